@@ -1,0 +1,248 @@
+"""Seeded synthetic inputs: regular GF(2^m) LDPC codes, interleavers, codewords, y.
+
+This module is shared by the test suite, the benchmark and the CPU oracle's
+callers as the single source of inputs.  It holds none of the decoder's
+arithmetic: it builds parity-check matrices (appendix "Q-ary LDPC code",
+paragraph "Construction of H": random nonzero positions, i.i.d. coefficients
+uniform on F_Q^x), an encoder (Gaussian elimination over GF(2^m), used only to
+draw uniform codewords) and the K-user PAM-sum channel output
+
+    y_t = sum_k (2 c_{k, pi_k^{-1}(t)} - (Q-1)) + w_t,   w_t ~ N(0, sigma2),
+    sigma2 = E_s 10^(-SNR/10),  E_s = (Q^2 - 1)/3 (mean energy of a uniform level).
+
+Random numbers come from NumPy's PCG64 with explicit seeds.  Its GF(2^m)
+arithmetic is its own (exp/log tables from the same primitive polynomials the
+decoder uses: x^2+x+1, x^4+x+1, x^6+x+1, ...), independent of the oracle's and
+of the CUDA library's.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+PRIM_POLY = {1: 0x3, 2: 0x7, 3: 0xB, 4: 0x13, 5: 0x25, 6: 0x43, 7: 0x89, 8: 0x11D}
+
+
+def code_seed(n: int, q: int) -> int:
+    """Default seed of the (n, q) code: 2605e6 + q*1e4 + n."""
+    return 2605 * 10**6 + q * 10**4 + n
+
+
+def log2_exact(q: int) -> int:
+    m = int(q).bit_length() - 1
+    if q < 2 or (1 << m) != q or m > 8:
+        raise ValueError("q must be 2^m with 1 <= m <= 8, got %r" % (q,))
+    return m
+
+
+class _GF:
+    """GF(2^m) by exp/log tables (for the encoder only)."""
+
+    def __init__(self, m: int):
+        self.m, self.q = m, 1 << m
+        q = self.q
+        exp = np.zeros(2 * q, dtype=np.int64)
+        log = np.zeros(q, dtype=np.int64)
+        x = 1
+        for i in range(q - 1):
+            exp[i] = x
+            log[x] = i
+            x <<= 1
+            if x & q:
+                x ^= PRIM_POLY[m]
+        for i in range(q - 1, 2 * q):
+            exp[i] = exp[i - (q - 1)]
+        a = np.arange(q)[:, None]
+        b = np.arange(q)[None, :]
+        mul = exp[(log[a] + log[b]) % (q - 1)]
+        mul[(a == 0) | (b == 0)] = 0
+        self.mul = mul.astype(np.int64)
+        self.inv = np.zeros(q, dtype=np.int64)
+        for v in range(1, q):
+            self.inv[v] = exp[(q - 1 - log[v]) % (q - 1)]
+
+
+def _four_cycle_edges(chk_var: np.ndarray, P: int, dc: int) -> np.ndarray:
+    """Edges that sit on a double edge or a 4-cycle of the Tanner graph."""
+    rows = chk_var.reshape(P, dc)
+    bad = np.zeros(P * dc, dtype=bool)
+    for j in range(P):
+        vals, counts = np.unique(rows[j], return_counts=True)
+        for v in vals[counts > 1]:
+            bad[j * dc + np.nonzero(rows[j] == v)[0]] = True
+    var_checks: dict[int, list[int]] = {}
+    for e, v in enumerate(chk_var.tolist()):
+        var_checks.setdefault(v, []).append(e // dc)
+    seen: dict[tuple[int, int], int] = {}
+    for v, cs in var_checks.items():
+        cs = sorted(set(cs))
+        for a in range(len(cs)):
+            for b in range(a + 1, len(cs)):
+                key = (cs[a], cs[b])
+                if key in seen:
+                    for vv in (v, seen[key]):
+                        for j in key:
+                            bad[j * dc + np.nonzero(rows[j] == vv)[0]] = True
+                else:
+                    seen[key] = v
+    return np.nonzero(bad)[0]
+
+
+def make_code(n: int, q: int, dv: int = 2, dc: int = 4, seed: int | None = None) -> dict:
+    """Regular (dv, dc) GF(q) LDPC code with no double edges and no 4-cycles.
+
+    Socket model: the n*dv variable sockets are placed on the P*dc check sockets
+    by a seeded random permutation (check-major: check j owns edges j*dc..j*dc+dc-1);
+    offending edges are then swapped with random edges until the graph has no
+    repeated variable in a check and no two variables sharing two checks.
+    Coefficients are i.i.d. uniform on {1, ..., q-1}.
+    """
+    m = log2_exact(q)
+    if (n * dv) % dc:
+        raise ValueError("n*dv must be a multiple of dc")
+    P = n * dv // dc
+    rng = np.random.Generator(np.random.PCG64(code_seed(n, q) if seed is None else seed))
+    sockets = np.repeat(np.arange(n, dtype=np.int64), dv)
+    chk_var = sockets[rng.permutation(n * dv)]
+    for _ in range(100000):
+        bad = _four_cycle_edges(chk_var, P, dc)
+        if bad.size == 0:
+            break
+        e1 = int(rng.choice(bad))
+        e2 = int(rng.integers(0, n * dv))
+        chk_var[e1], chk_var[e2] = chk_var[e2], chk_var[e1]
+    else:
+        raise RuntimeError("could not remove 4-cycles")
+    chk_coef = rng.integers(1, q, size=P * dc)
+    code = {"n": n, "P": P, "q": q, "m": m, "dv": dv, "dc": dc,
+            "chk_var": chk_var.astype(np.int32), "chk_coef": chk_coef.astype(np.uint8)}
+    code.update(_encoder(code))
+    return code
+
+
+def code_from_edges(n: int, q: int, dc: int, chk_var, chk_coef) -> dict:
+    """Wrap an explicit check-major edge list (any variable degrees)."""
+    chk_var = np.asarray(chk_var, dtype=np.int32).reshape(-1)
+    chk_coef = np.asarray(chk_coef, dtype=np.uint8).reshape(-1)
+    if chk_var.size % dc:
+        raise ValueError("edge count must be a multiple of dc")
+    code = {"n": n, "P": chk_var.size // dc, "q": q, "m": log2_exact(q), "dv": None, "dc": dc,
+            "chk_var": chk_var, "chk_coef": chk_coef}
+    code.update(_encoder(code))
+    return code
+
+
+def _encoder(code: dict) -> dict:
+    """Systematic encoder from Gaussian elimination of H over GF(q).
+
+    Returns the information positions (non-pivot columns), rank(H) and a binary
+    generator that maps information bits to codeword bits (multiplication by a
+    fixed field element is GF(2)-linear, so encoding is a 0/1 matrix product).
+    """
+    n, P, q, m, dc = code["n"], code["P"], code["q"], code["m"], code["dc"]
+    gf = _GF(m)
+    H = np.zeros((P, n), dtype=np.int64)
+    for e in range(P * dc):
+        H[e // dc, int(code["chk_var"][e])] = int(code["chk_coef"][e])
+    pivots = []
+    r = 0
+    for c in range(n):
+        if r == P:
+            break
+        nz = np.nonzero(H[r:, c])[0]
+        if nz.size == 0:
+            continue
+        p = r + int(nz[0])
+        if p != r:
+            H[[r, p]] = H[[p, r]]
+        H[r] = gf.mul[gf.inv[H[r, c]], H[r]]
+        rows = np.nonzero(H[:, c])[0]
+        rows = rows[rows != r]
+        if rows.size:
+            H[rows] ^= gf.mul[H[rows, c][:, None], H[r][None, :]]
+        pivots.append(c)
+        r += 1
+    rank = r
+    piv = np.array(pivots, dtype=np.int64)
+    info = np.array(sorted(set(range(n)) - set(pivots)), dtype=np.int64)
+    k = info.size
+    # generator over GF(2): bit b of info symbol f -> bits of every codeword symbol
+    G = np.zeros((k * m, n * m), dtype=np.float32)
+    for fi, col in enumerate(info):
+        for b in range(m):
+            G[fi * m + b, col * m + b] = 1.0
+    for row in range(rank):
+        for fi, col in enumerate(info):
+            h = int(H[row, col])
+            if h == 0:
+                continue
+            for b in range(m):
+                prod = int(gf.mul[h, 1 << b])
+                for b2 in range(m):
+                    if (prod >> b2) & 1:
+                        G[fi * m + b, piv[row] * m + b2] = 1.0
+    return {"rank": rank, "k": k, "info_pos": info.astype(np.int32), "gen_bits": G}
+
+
+def encode(code: dict, info: np.ndarray) -> np.ndarray:
+    """Codewords [..., n] (uint8) for information symbols [..., k]."""
+    m, n, k = code["m"], code["n"], code["k"]
+    shape = info.shape[:-1]
+    flat = np.asarray(info, dtype=np.int64).reshape(-1, k)
+    bits = ((flat[:, :, None] >> np.arange(m)[None, None, :]) & 1).astype(np.float32).reshape(-1, k * m)
+    out = np.empty((flat.shape[0], n), dtype=np.uint8)
+    weights = (1 << np.arange(m)).astype(np.int64)
+    G = code["gen_bits"]
+    step = 16384
+    for s in range(0, flat.shape[0], step):
+        cb = (bits[s:s + step] @ G).astype(np.int64) & 1   # exact: 0/1 sums < 2^24
+        out[s:s + step] = (cb.reshape(-1, n, m) * weights).sum(-1).astype(np.uint8)
+    return out.reshape(*shape, n)
+
+
+def make_interleavers(n: int, K: int, seed: int, interleave: bool = True) -> np.ndarray:
+    """pi[k, i] = channel use of user k's symbol i; pi_0 = identity."""
+    pi = np.tile(np.arange(n, dtype=np.int32), (K, 1))
+    if interleave:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        for k in range(1, K):
+            pi[k] = rng.permutation(n).astype(np.int32)
+    return pi
+
+
+def es(q: int) -> float:
+    """Mean energy of the uniform PAM levels 2a-(q-1): (q^2-1)/3."""
+    return (q * q - 1) / 3.0
+
+
+def sigma2_from_snr(q: int, snr_db: float) -> float:
+    return es(q) * 10.0 ** (-snr_db / 10.0)
+
+
+def make_frames(code: dict, K: int, snr_db: float, F: int, seed: int, interleave: bool = True,
+                noiseless: bool = False, perm_seed: int | None = None) -> dict:
+    """F frames of K users: uniform info symbols, codewords, channel output y (float32)."""
+    q, n = code["q"], code["n"]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    info = rng.integers(0, q, size=(F, K, code["k"]), dtype=np.int64)
+    c = encode(code, info)                                   # [F, K, n]
+    pi = make_interleavers(n, K, seed if perm_seed is None else perm_seed, interleave)
+    sigma2 = sigma2_from_snr(q, snr_db)
+    levels = 2.0 * c.astype(np.float64) - (q - 1)            # [F, K, n]
+    y = np.zeros((F, n), dtype=np.float64)
+    for k in range(K):
+        y[:, pi[k]] += levels[:, k, :]
+    if not noiseless:
+        y += rng.standard_normal((F, n)) * math.sqrt(sigma2)
+    return {"c": c, "y": y.astype(np.float32), "sigma2": sigma2, "perm": pi, "snr_db": snr_db,
+            "K": K, "info": info.astype(np.int32)}
+
+
+def random_log_messages(rng: np.random.Generator, shape, q: int, spread: float = 8.0,
+                        log_floor: float = math.log(1e-12)) -> np.ndarray:
+    """Random max-normalised log-messages [..., q] for single-step tests: Gaussian
+    logits scaled by `spread`, shifted to max 0 and clipped at log_floor."""
+    x = rng.standard_normal(tuple(shape) + (q,)) * spread
+    x -= x.max(axis=-1, keepdims=True)
+    return np.maximum(x, log_floor)

@@ -1,0 +1,76 @@
+"""Seeded input generator: code structure, encoder, interleavers, channel output."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2605_26580_gb300 import inputs as I
+
+
+@pytest.mark.parametrize("n,q", [(64, 4), (256, 16), (512, 64), (128, 2)])
+def test_regular_code_structure(n, q):
+    code = I.make_code(n, q)
+    P, dc = code["P"], code["dc"]
+    assert P == n // 2 and code["chk_var"].size == P * dc
+    counts = np.bincount(code["chk_var"], minlength=n)
+    assert (counts == 2).all()                              # dv = 2 regular
+    rows = code["chk_var"].reshape(P, dc)
+    assert all(len(set(r)) == dc for r in rows.tolist())    # no double edges
+    pairs = set()
+    for i in range(n):                                      # no 4-cycles: no two vars share two checks
+        cs = tuple(sorted(set(np.nonzero((rows == i).any(1))[0].tolist())))
+        assert cs not in pairs
+        pairs.add(cs)
+    assert ((code["chk_coef"] >= 1) & (code["chk_coef"] < q)).all()
+    assert code["k"] == n - code["rank"] and code["k"] >= n // 2
+
+
+def test_code_is_reproducible():
+    a, b = I.make_code(128, 16), I.make_code(128, 16)
+    assert (a["chk_var"] == b["chk_var"]).all() and (a["chk_coef"] == b["chk_coef"]).all()
+    c = I.make_code(128, 16, seed=1)
+    assert not (a["chk_var"] == c["chk_var"]).all()
+
+
+def test_encoder_is_systematic_and_linear():
+    code = I.make_code(64, 16)
+    rng = np.random.default_rng(0)
+    info = rng.integers(0, 16, size=(10, code["k"]))
+    c = I.encode(code, info)
+    assert (c[:, code["info_pos"]] == info).all()
+    # linearity over GF(2^m): c(u) xor c(v) = c(u xor v)
+    u, v = info[:5], info[5:]
+    assert (I.encode(code, u) ^ I.encode(code, v) == I.encode(code, u ^ v)).all()
+
+
+def test_interleavers():
+    pi = I.make_interleavers(100, 4, seed=3)
+    assert (pi[0] == np.arange(100)).all()
+    for k in range(4):
+        assert sorted(pi[k].tolist()) == list(range(100))
+    assert (I.make_interleavers(100, 4, seed=3, interleave=False) == np.arange(100)).all()
+
+
+def test_channel_output_noiseless_and_noise_variance():
+    code = I.make_code(64, 4)
+    fr = I.make_frames(code, 3, 10.0, 50, seed=1, noiseless=True)
+    pi = fr["perm"]
+    y = np.zeros((50, 64))
+    for k in range(3):
+        for i in range(64):
+            y[:, pi[k, i]] += 2.0 * fr["c"][:, k, i].astype(np.float64) - 3
+    assert np.array_equal(fr["y"], y.astype(np.float32))
+    noisy = I.make_frames(code, 3, 10.0, 2000, seed=1)
+    clean = np.zeros((2000, 64))
+    for k in range(3):
+        clean[:, pi[k]] += 2.0 * noisy["c"][:, k] - 3
+    w = noisy["y"] - clean
+    assert abs(w.var() / noisy["sigma2"] - 1) < 0.05
+    assert math.isclose(noisy["sigma2"], 5.0 * 10 ** -1.0)   # E_s = (q^2-1)/3 = 5 at q = 4
+
+
+def test_random_messages_are_max_normalised():
+    rng = np.random.default_rng(0)
+    m = I.random_log_messages(rng, (7, 3), 16)
+    assert m.shape == (7, 3, 16)
+    assert np.allclose(m.max(-1), 0.0) and m.min() >= math.log(1e-12)
