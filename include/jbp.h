@@ -1,0 +1,209 @@
+/*
+ * jbp.h -- C ABI of the GB300 joint FFT belief-propagation decoder.
+ *
+ * The library decodes frames of K users who share one regular GF(q) LDPC code
+ * (q = 2^m, m = 1..6) and whose PAM levels add on a real AWGN channel:
+ *
+ *     y_t = sum_k (2 c_{k, pi_k^{-1}(t)} - (q-1)) + w_t,   w_t ~ N(0, sigma2).
+ *
+ * Each decoding iteration is sum-product belief propagation on the joint
+ * factor graph, run as hand-written sm_103a CUDA kernels:
+ *   (a) channel node: each user's extrinsic q-ary message from the other users'
+ *       distributions (prefix/suffix convolution over the integer symbol sum,
+ *       no division) scored against y_t;
+ *   (b) check node (FFT-QSPA): the variable-to-check rule of the paper's
+ *       appendix "Q-ary LDPC code", eq. (app_ldpc_v2c), then eq. (app_ldpc_c2v)
+ *       evaluated in the Walsh-Hadamard domain (appendix "Complexity
+ *       derivation", paragraph FFT-BP): permute by the edge coefficient, WHT,
+ *       leave-one-out product, inverse WHT, inverse permutation;
+ *   (c) variable node: the marginal of eq. (app_ldpc_marginal);
+ *   (d) hard decision, syndrome check (eq. app_ldpc_check_eq) and per-frame
+ *       early exit on convergence (Table 1 caption: at most 50 iterations
+ *       with early exit).
+ *
+ * Messages are FP32 log-probabilities shifted to a maximum of 0.  A c2v
+ * message is floored at 1e-12 of its maximum; a channel message is clipped at
+ * ln(1e-12).  The schedule is flooding: per iteration all channel nodes, then
+ * all checks, then the decisions.
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns a jbp_status.  On failure jbp_last_error() returns a
+ *     thread-local message describing the most recent failure of this thread.
+ *     No C++ exception crosses this interface.
+ *   - Field: GF(2^m) with the primitive polynomials x+1, x^2+x+1, x^3+x+1,
+ *     x^4+x+1, x^5+x^2+1, x^6+x+1; symbol index bits are the polynomial
+ *     coefficients (bit i = coefficient of x^i).
+ *   - Layouts are row-major and frame-major.  Check-major edges: edge
+ *     e = j*dc + d is the d-th nonzero of row j of H.
+ *   - "device pointer" means memory of the handle's GPU (cudaMalloc or any
+ *     allocator of that device); "host pointer" means pageable or pinned host
+ *     memory.  The library never frees memory it did not allocate.
+ */
+#ifndef JBP_H
+#define JBP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    JBP_OK = 0,
+    JBP_EINVAL = 1,    /* invalid argument (NULL handle, bad size, unsupported shape)   */
+    JBP_ENOMEM = 2,    /* device or host allocation failed, or the memory budget is hit */
+    JBP_ECUDA = 3,     /* a CUDA runtime call failed (message has the CUDA error)       */
+    JBP_EAGAIN = 4,    /* jbp_poll: the request is not finished yet                     */
+    JBP_ETIMEOUT = 5,  /* a bounded device-side wait expired                            */
+    JBP_ECLOSED = 6    /* the context is shutting down / ticket unknown or consumed     */
+} jbp_status;
+
+/* Check-node transform precision.  FP32: Walsh-Hadamard butterflies in FP32 on
+ * the CUDA cores.  The others run the transform as a dense +-1 matrix product on
+ * the tensor cores with BF16 operands and FP32 accumulation: BF16X3 splits each
+ * FP32 operand into three BF16 terms (about FP32 accuracy), BF16X2 into two
+ * (hi/lo), BF16 uses one. */
+typedef enum { JBP_PREC_FP32 = 0, JBP_PREC_BF16X2 = 1, JBP_PREC_BF16 = 2, JBP_PREC_BF16X3 = 3 } jbp_precision;
+
+/* Launch form of jbp_decode.  AUTO picks FUSED when one frame's message state
+ * fits in one SM's shared memory, else STEP.  FUSED: one persistent kernel runs
+ * every iteration of a group of frames with all messages in shared memory.
+ * STEP: one kernel per node type per iteration, messages resident in HBM.
+ * PLAIN: the STEP kernels launched for one frame at a time (the per-frame
+ * reference form used for comparison). */
+typedef enum { JBP_FORM_AUTO = 0, JBP_FORM_FUSED = 1, JBP_FORM_STEP = 2, JBP_FORM_PLAIN = 3 } jbp_form;
+
+typedef struct jbp_ctx jbp_ctx;  /* one GPU, its streams, memory budget and serving loop */
+typedef struct jbp_h jbp_h;      /* one (code, K, q, channel) decoder bound to a context  */
+
+/* Parity-check matrix H (P x n over GF(q)), regular: every check has dc edges,
+ * every variable dv edges.  chk_var [P*dc]: variable index of each edge;
+ * chk_coef [P*dc]: nonzero coefficient H_{j,l} in 1..q-1.  Host pointers,
+ * copied by jbp_create; the caller keeps ownership. */
+typedef struct {
+    int32_t n, P, q, dv, dc;
+    const int32_t *chk_var;
+    const uint8_t *chk_coef;
+} jbp_code;
+
+/* Channel.  sigma2 > 0: noise variance.  interleave = 1: perm [K*n] gives
+ * pi_k(i), the channel use that carries user k's symbol i (each row a
+ * permutation of 0..n-1).  interleave = 0: every pi_k is the identity and perm
+ * may be NULL.  Host pointer, copied by jbp_create. */
+typedef struct {
+    double sigma2;
+    int32_t interleave;
+    const int32_t *perm;
+} jbp_channel;
+
+/* Context options.  iters: maximum iterations T (>= 1).  early_stop: 1 stops a
+ * frame at the first iteration after which all K syndromes are zero.
+ * precision: jbp_precision of the check-node transform.  mem_budget_bytes:
+ * cap on the device memory the context allocates (0 = 90% of free memory at
+ * creation).  device: CUDA device ordinal.  block_iters: iterations per
+ * serving block (0 = 5). */
+typedef struct {
+    int32_t iters;
+    int32_t early_stop;
+    int32_t precision;
+    int32_t device;
+    int64_t mem_budget_bytes;
+    int32_t block_iters;
+    int32_t reserved[7];
+} jbp_options;
+
+/* One decode call.  F >= 0 frames.  y [F*n] FP32 channel outputs.  Outputs:
+ * hat [F*K*n] decided symbols; iters [F] iterations run (the stopping
+ * iteration, or T); ok [F*K] 1 where user k's syndrome is zero after the last
+ * iteration run; logpost [F*K*n*q] optional (may be NULL) max-normalised
+ * log-posterior of the last iteration run.
+ * on_device = 0: host pointers; the call copies in and out and returns when
+ * the outputs are written.  on_device = 1: device pointers; the work is
+ * enqueued on `stream` (a cudaStream_t, NULL = the handle's own stream) and the
+ * call returns without waiting; outputs are valid once that stream reaches
+ * this point.  form: jbp_form.  Buffers must not overlap. */
+typedef struct {
+    int32_t F;
+    const float *y;
+    uint8_t *hat;
+    int32_t *iters;
+    uint8_t *ok;
+    float *logpost;
+    int32_t on_device;
+    int32_t form;
+    void *stream;
+} jbp_batch;
+
+/* Create a context on opt->device.  Fails with JBP_EINVAL on bad options,
+ * JBP_ECUDA if the device cannot be used.  *out owns streams and a serving
+ * thread (started on the first jbp_submit). */
+int jbp_context_create(const jbp_options *opt, jbp_ctx **out);
+
+/* Stop the serving thread, wait for in-flight work, free everything the
+ * context owns.  Handles of this context must be destroyed first. */
+int jbp_context_destroy(jbp_ctx *ctx);
+
+/* Bind a decoder for `code`, K >= 1 users (K <= 16) and GF(q) (q = code->q)
+ * to the context; copies the code and interleavers to the device and builds
+ * the GF tables.  Supported shapes: q in {2,4,8,16,32,64}, dc = 4, dv >= 1
+ * regular, n >= 1.  Others give JBP_EINVAL. */
+int jbp_create(jbp_ctx *ctx, const jbp_code *code, int32_t K, int32_t q,
+               const jbp_channel *chan, jbp_h **out);
+
+/* Free the handle's device memory.  Its pending submitted requests are
+ * cancelled (their tickets poll JBP_ECLOSED). */
+int jbp_destroy(jbp_h *h);
+
+/* Decode one batch (see jbp_batch). */
+int jbp_decode(jbp_h *h, jbp_batch *batch);
+
+/* Serving: queue one frame (y_frame [n] host pointer, copied before return)
+ * for continuous batching on the context's device.  *ticket identifies it. */
+int jbp_submit(jbp_h *h, const float *y_frame, uint64_t *ticket);
+
+/* Serving: JBP_EAGAIN while the request runs; JBP_OK once finished, with
+ * hat [K*n], iters [1] and ok [K] written (host pointers; any may be NULL).
+ * A finished ticket is consumed by the successful poll; polling it again
+ * gives JBP_ECLOSED. */
+int jbp_poll(jbp_ctx *ctx, uint64_t ticket, uint8_t *hat, int32_t *iters, uint8_t *ok);
+
+/* Serving statistics since context creation: completed requests, and the
+ * p50 / p99 submit-to-finish latency in microseconds (0 when nothing ran). */
+int jbp_serving_stats(jbp_ctx *ctx, uint64_t *completed, double *p50_us, double *p99_us);
+
+/* Thread-local message of the last failure on this thread ("" if none). */
+const char *jbp_last_error(void);
+
+/* ---- single steps on device buffers (one kernel launch each, enqueued on
+ * `stream`, NULL = the handle's stream).  They expose the per-iteration kernels
+ * for testing and for callers that schedule iterations themselves.
+ * Layouts: msg [F*K*E*q] holds, per edge, the check-to-variable message
+ * (before jbp_step_channel, after jbp_step_check) or the variable-to-check
+ * message (after jbp_step_channel); ch2v and post [F*K*n*q]; hat [F*K*n];
+ * ok [F*K]; E = P*dc. ---- */
+
+/* (a) channel node for every channel use of F frames: reads the c2v messages in
+ * msg and y [F*n]; writes ch2v and replaces each c2v in msg by the v2c message
+ * of the same edge (eq. app_ldpc_v2c with the channel message as local belief). */
+int jbp_step_channel(jbp_h *h, int32_t F, const float *y, float *msg, float *ch2v, void *stream);
+
+/* (b) check node for every check: replaces the v2c messages in msg by the new
+ * c2v messages (eq. app_ldpc_c2v in the WHT domain); precision: jbp_precision. */
+int jbp_step_check(jbp_h *h, int32_t F, float *msg, int32_t precision, void *stream);
+
+/* (c) variable node: post = ch2v + sum of the variable's c2v (max-normalised;
+ * post may be NULL) and the hard decision hat (ties -> lowest symbol). */
+int jbp_step_var(jbp_h *h, int32_t F, const float *ch2v, const float *msg, float *post,
+                 uint8_t *hat, void *stream);
+
+/* (d) syndrome: ok[f*K+k] = 1 iff every check of user k is satisfied by hat. */
+int jbp_step_syndrome(jbp_h *h, int32_t F, const uint8_t *hat, uint8_t *ok, void *stream);
+
+/* Shape information of a handle (host pointers, any may be NULL): edges E,
+ * per-frame device state bytes, and whether one frame fits the fused form. */
+int jbp_query(jbp_h *h, int32_t *E, int64_t *state_bytes_per_frame, int32_t *fused_ok);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,56 @@
+// jbp_internal.h -- host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "jbp_device.cuh"
+
+namespace jbp {
+
+// Per-frame control words of the step form (device memory, F entries each).
+struct StepCtl {
+    uint8_t* active;   // 1 while the frame iterates
+    uint8_t* unsat;    // [F*K] 1 if some check of user k is unsatisfied
+    int32_t* iters;    // iterations run
+    uint8_t* ok;       // [F*K]
+};
+
+struct DeviceInfo {
+    int sm_count;
+    int smem_optin;   // max dynamic shared memory per block (bytes)
+};
+
+// Step kernels (jbp_step.cu).  active may be null (all frames active).
+cudaError_t launch_channel(const Graph& g, const DeviceInfo& di, int F, const float* y, float* msg,
+                           float* ch2v, const uint8_t* active, cudaStream_t s);
+cudaError_t launch_check(const Graph& g, const DeviceInfo& di, int F, float* msg,
+                         const uint8_t* active, int precision, cudaStream_t s);
+cudaError_t launch_var(const Graph& g, const DeviceInfo& di, int F, const float* ch2v,
+                       const float* msg, float* post, uint8_t* hat, const uint8_t* active,
+                       cudaStream_t s);
+cudaError_t launch_syndrome(const Graph& g, const DeviceInfo& di, int F, const uint8_t* hat,
+                            uint8_t* unsat, const uint8_t* active, cudaStream_t s);
+cudaError_t launch_finalize(int F, int K, int t, int early_stop, StepCtl ctl, cudaStream_t s);
+cudaError_t launch_ok_from_unsat(int F, int K, const uint8_t* unsat, uint8_t* ok, cudaStream_t s);
+
+// Fused shared-memory form (jbp_fused.cu).
+struct FusedPlan {
+    int frames_per_cta;   // frames resident in one CTA
+    int threads;          // threads per CTA
+    int smem_bytes;       // dynamic shared memory per CTA
+    int grid;             // CTAs launched (persistent)
+};
+bool fused_plan(const Graph& g, const DeviceInfo& di, int F, int threads_hint, int fpc_hint,
+                FusedPlan* plan);
+cudaError_t launch_fused(const Graph& g, const FusedPlan& plan, int F, const float* y, int T,
+                         int early_stop, uint8_t* hat, int32_t* iters, uint8_t* ok, float* post,
+                         cudaStream_t s);
+
+// Bytes of message state of one frame in either form: msg [K*E*Q] + ch2v [K*n*Q] floats.
+inline int64_t state_bytes(const Graph& g)
+{
+    return 4ll * g.K * (int64_t)(g.E + g.n) * g.Q;
+}
+
+}  // namespace jbp

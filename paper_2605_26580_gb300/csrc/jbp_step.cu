@@ -1,0 +1,258 @@
+// jbp_step.cu -- step form: one kernel per node type per iteration, message
+// state resident in HBM.
+//
+// HBM layout per frame f (frame-major, q contiguous):
+//   msg  [K][E][q]  FP32 log-messages on check-major edges (c2v, or v2c between
+//                   the channel and check steps: updated in place, no double buffer)
+//   ch2v [K][n][q]  FP32 channel messages
+// Each kernel is a persistent grid-stride loop over units with grids sized to
+// fill every SM at the occupancy the block shape allows.
+#include <algorithm>
+
+#include "jbp_internal.h"
+
+namespace jbp {
+namespace {
+
+constexpr int kStepThreads = 256;
+
+template <class Kern>
+int persistent_grid(Kern kern, int threads, size_t smem, const DeviceInfo& di, long units_per_block,
+                    long units)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess || occ < 1) occ = 1;
+    long need = (units + units_per_block - 1) / units_per_block;
+    long cap = (long)di.sm_count * occ;
+    return (int)std::max(1L, std::min(need, cap));
+}
+
+// Copy the GF tables to shared memory (Q*Q bytes each).
+template <int Q>
+__device__ __forceinline__ void load_gf(const Graph& g, uint8_t* smul, uint8_t* sdiv)
+{
+    for (int i = threadIdx.x; i < Q * Q; i += blockDim.x) {
+        smul[i] = g.gf_mul[i];
+        sdiv[i] = g.gf_div[i];
+    }
+    __syncthreads();
+}
+
+// (a) channel node + in-place v2c.  Team per (frame, channel use).
+template <int Q>
+__global__ void __launch_bounds__(kStepThreads) k_channel(Graph g, int F, const float* __restrict__ y,
+                                                          float* msg, float* ch2v,
+                                                          const uint8_t* __restrict__ active, int sc_floats)
+{
+    constexpr int T = Shape<Q>::T;
+    extern __shared__ float smem[];
+    const int teams = blockDim.x / T, team = threadIdx.x / T;
+    float* sc = smem + (size_t)team * sc_floats;
+    float* res = sc + sc_floats - g.K * Q;
+    const TeamLane L = team_lane<T>();
+    const long total = (long)F * g.n;
+    const size_t fs = (size_t)g.K * g.E * Q, vs = (size_t)g.K * g.n * Q;
+    for (long unit = (long)blockIdx.x * teams + team; unit < total; unit += (long)gridDim.x * teams) {
+        const int f = (int)(unit / g.n), u = (int)(unit % g.n);
+        if (active && !active[f]) continue;
+        float* msg_f = msg + f * fs;
+        const float yv = y[(size_t)f * g.n + u];
+        if (chan_trellis<Q, LinSR>(g, msg_f, yv, u, sc, res, L))
+            chan_trellis<Q, LogSR>(g, msg_f, yv, u, sc, res, L);
+        chan_write<Q>(g, msg_f, ch2v + f * vs, res, u, L);
+    }
+}
+
+// (b) check node, FP32 butterflies.  Team per (frame, user, check).
+template <int Q, int DC>
+__global__ void __launch_bounds__(kStepThreads) k_check_fp32(Graph g, int F, float* msg,
+                                                             const uint8_t* __restrict__ active)
+{
+    constexpr int T = Shape<Q>::T;
+    __shared__ uint8_t smul[Q * Q], sdiv[Q * Q];
+    load_gf<Q>(g, smul, sdiv);
+    const int teams = blockDim.x / T, team = threadIdx.x / T;
+    const TeamLane L = team_lane<T>();
+    const long per_frame = (long)g.K * g.P, total = (long)F * per_frame;
+    for (long unit = (long)blockIdx.x * teams + team; unit < total; unit += (long)gridDim.x * teams) {
+        const int f = (int)(unit / per_frame);
+        if (active && !active[f]) continue;
+        const int rem = (int)(unit % per_frame), k = rem / g.P, j = rem % g.P;
+        float* msg_fk = msg + ((size_t)f * g.K + k) * g.E * Q;
+        check_unit_fp32<Q, DC>(g, msg_fk, j, smul, sdiv, L);
+    }
+}
+
+// (c) posterior and decision.  Team per (frame, user, variable).
+template <int Q>
+__global__ void __launch_bounds__(kStepThreads) k_var(Graph g, int F, const float* __restrict__ ch2v,
+                                                      const float* __restrict__ msg, float* post,
+                                                      uint8_t* hat, const uint8_t* __restrict__ active)
+{
+    constexpr int T = Shape<Q>::T;
+    const int teams = blockDim.x / T, team = threadIdx.x / T;
+    const TeamLane L = team_lane<T>();
+    const long per_frame = (long)g.K * g.n, total = (long)F * per_frame;
+    for (long unit = (long)blockIdx.x * teams + team; unit < total; unit += (long)gridDim.x * teams) {
+        const int f = (int)(unit / per_frame);
+        if (active && !active[f]) continue;
+        const int rem = (int)(unit % per_frame), k = rem / g.n, i = rem % g.n;
+        const size_t fk = (size_t)f * g.K + k;
+        var_unit<Q>(g, ch2v + fk * g.n * Q, msg + fk * g.E * Q, i, post ? post + fk * g.n * Q : nullptr,
+                    hat + fk * g.n, L);
+    }
+}
+
+// (d) syndrome: unsat[f*K+k] = 1 if a check of user k is unsatisfied.
+template <int Q>
+__global__ void __launch_bounds__(kStepThreads) k_syndrome(Graph g, int F, const uint8_t* __restrict__ hat,
+                                                           uint8_t* unsat, const uint8_t* __restrict__ active)
+{
+    __shared__ uint8_t smul[Q * Q], sdiv[Q * Q];
+    load_gf<Q>(g, smul, sdiv);
+    const long per_frame = (long)g.K * g.P, total = (long)F * per_frame;
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int f = (int)(t / per_frame);
+        if (active && !active[f]) continue;
+        const int rem = (int)(t % per_frame), k = rem / g.P, j = rem % g.P;
+        const size_t fk = (size_t)f * g.K + k;
+        if (!check_satisfied(g, hat + fk * g.n, j, smul)) unsat[fk] = 1;
+    }
+}
+
+// After iteration t: record iterations and ok flags, stop converged frames.
+__global__ void k_finalize(int F, int K, int t, int early_stop, StepCtl c)
+{
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < F; f += gridDim.x * blockDim.x) {
+        if (!c.active[f]) continue;
+        bool all = true;
+        for (int k = 0; k < K; ++k) {
+            const bool okk = c.unsat[(size_t)f * K + k] == 0;
+            c.ok[(size_t)f * K + k] = okk ? 1 : 0;
+            c.unsat[(size_t)f * K + k] = 0;
+            all = all && okk;
+        }
+        c.iters[f] = t;
+        if (early_stop && all) c.active[f] = 0;
+    }
+}
+
+__global__ void k_ok_from_unsat(int n, const uint8_t* unsat, uint8_t* ok)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        ok[i] = unsat[i] ? 0 : 1;
+}
+
+template <int Q>
+cudaError_t channel_q(const Graph& g, const DeviceInfo& di, int F, const float* y, float* msg, float* ch2v,
+                      const uint8_t* active, cudaStream_t s)
+{
+    constexpr int T = Shape<Q>::T;
+    const int scf = chan_scratch_floats(g.K, Q);
+    const size_t per_team = (size_t)scf * sizeof(float);
+    // as many warps as fit in the opt-in shared memory, at most kStepThreads threads
+    int threads = kStepThreads;
+    while (threads > 32 && (size_t)(threads / T) * per_team > (size_t)di.smem_optin) threads -= 32;
+    const size_t smem = (size_t)(threads / T) * per_team;
+    if (smem > (size_t)di.smem_optin) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(k_channel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long units = (long)F * g.n;
+    const int grid = persistent_grid(k_channel<Q>, threads, smem, di, threads / T, units);
+    k_channel<Q><<<grid, threads, smem, s>>>(g, F, y, msg, ch2v, active, scf);
+    return cudaGetLastError();
+}
+
+template <int Q>
+cudaError_t check_q(const Graph& g, const DeviceInfo& di, int F, float* msg, const uint8_t* active,
+                    cudaStream_t s)
+{
+    constexpr int T = Shape<Q>::T;
+    if (g.dc != 4) return cudaErrorInvalidValue;
+    const long units = (long)F * g.K * g.P;
+    const int grid = persistent_grid(k_check_fp32<Q, 4>, kStepThreads, 0, di, kStepThreads / T, units);
+    k_check_fp32<Q, 4><<<grid, kStepThreads, 0, s>>>(g, F, msg, active);
+    return cudaGetLastError();
+}
+
+template <int Q>
+cudaError_t var_q(const Graph& g, const DeviceInfo& di, int F, const float* ch2v, const float* msg,
+                  float* post, uint8_t* hat, const uint8_t* active, cudaStream_t s)
+{
+    constexpr int T = Shape<Q>::T;
+    const long units = (long)F * g.K * g.n;
+    const int grid = persistent_grid(k_var<Q>, kStepThreads, 0, di, kStepThreads / T, units);
+    k_var<Q><<<grid, kStepThreads, 0, s>>>(g, F, ch2v, msg, post, hat, active);
+    return cudaGetLastError();
+}
+
+template <int Q>
+cudaError_t syndrome_q(const Graph& g, const DeviceInfo& di, int F, const uint8_t* hat, uint8_t* unsat,
+                       const uint8_t* active, cudaStream_t s)
+{
+    const long units = (long)F * g.K * g.P;
+    const int grid = persistent_grid(k_syndrome<Q>, kStepThreads, 0, di, kStepThreads, units);
+    k_syndrome<Q><<<grid, kStepThreads, 0, s>>>(g, F, hat, unsat, active);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+#define JBP_DISPATCH_Q(QV, CALL)                      \
+    switch (QV) {                                     \
+        case 2: { constexpr int Qc = 2; return CALL; }   \
+        case 4: { constexpr int Qc = 4; return CALL; }   \
+        case 8: { constexpr int Qc = 8; return CALL; }   \
+        case 16: { constexpr int Qc = 16; return CALL; } \
+        case 32: { constexpr int Qc = 32; return CALL; } \
+        case 64: { constexpr int Qc = 64; return CALL; } \
+        default: return cudaErrorInvalidValue;        \
+    }
+
+cudaError_t launch_channel(const Graph& g, const DeviceInfo& di, int F, const float* y, float* msg,
+                           float* ch2v, const uint8_t* active, cudaStream_t s)
+{
+    if (F <= 0) return cudaSuccess;
+    JBP_DISPATCH_Q(g.Q, (channel_q<Qc>(g, di, F, y, msg, ch2v, active, s)));
+}
+
+cudaError_t launch_check(const Graph& g, const DeviceInfo& di, int F, float* msg, const uint8_t* active,
+                         int precision, cudaStream_t s)
+{
+    (void)precision;
+    if (F <= 0) return cudaSuccess;
+    JBP_DISPATCH_Q(g.Q, (check_q<Qc>(g, di, F, msg, active, s)));
+}
+
+cudaError_t launch_var(const Graph& g, const DeviceInfo& di, int F, const float* ch2v, const float* msg,
+                       float* post, uint8_t* hat, const uint8_t* active, cudaStream_t s)
+{
+    if (F <= 0) return cudaSuccess;
+    JBP_DISPATCH_Q(g.Q, (var_q<Qc>(g, di, F, ch2v, msg, post, hat, active, s)));
+}
+
+cudaError_t launch_syndrome(const Graph& g, const DeviceInfo& di, int F, const uint8_t* hat, uint8_t* unsat,
+                            const uint8_t* active, cudaStream_t s)
+{
+    if (F <= 0) return cudaSuccess;
+    JBP_DISPATCH_Q(g.Q, (syndrome_q<Qc>(g, di, F, hat, unsat, active, s)));
+}
+
+cudaError_t launch_finalize(int F, int K, int t, int early_stop, StepCtl ctl, cudaStream_t s)
+{
+    if (F <= 0) return cudaSuccess;
+    const int threads = 256, grid = std::min((F + threads - 1) / threads, 4096);
+    k_finalize<<<grid, threads, 0, s>>>(F, K, t, early_stop, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ok_from_unsat(int F, int K, const uint8_t* unsat, uint8_t* ok, cudaStream_t s)
+{
+    const int n = F * K;
+    if (n <= 0) return cudaSuccess;
+    const int threads = 256, grid = std::min((n + threads - 1) / threads, 4096);
+    k_ok_from_unsat<<<grid, threads, 0, s>>>(n, unsat, ok);
+    return cudaGetLastError();
+}
+
+}  // namespace jbp

@@ -220,23 +220,34 @@ def sigma2_from_snr(q: int, snr_db: float) -> float:
     return es(q) * 10.0 ** (-snr_db / 10.0)
 
 
+def channel_output(q: int, c: np.ndarray, perm: np.ndarray, snr_db: float, seed: int,
+                   noiseless: bool = False) -> tuple[np.ndarray, float]:
+    """y [F, n] float32 of codewords c [F, K, n] through the PAM-sum channel."""
+    F, K, n = c.shape
+    sigma2 = sigma2_from_snr(q, snr_db)
+    y = np.zeros((F, n), dtype=np.float64)
+    for k in range(K):
+        y[:, perm[k]] += 2.0 * c[:, k, :].astype(np.float64) - (q - 1)
+    if not noiseless:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        y += rng.standard_normal((F, n)) * math.sqrt(sigma2)
+    return y.astype(np.float32), sigma2
+
+
 def make_frames(code: dict, K: int, snr_db: float, F: int, seed: int, interleave: bool = True,
                 noiseless: bool = False, perm_seed: int | None = None) -> dict:
-    """F frames of K users: uniform info symbols, codewords, channel output y (float32)."""
+    """F frames of K users: uniform info symbols, codewords, channel output y (float32).
+
+    Streams: info symbols from PCG64(seed), interleavers from PCG64(perm_seed or
+    seed), noise from PCG64(seed + 1)."""
     q, n = code["q"], code["n"]
     rng = np.random.Generator(np.random.PCG64(seed))
     info = rng.integers(0, q, size=(F, K, code["k"]), dtype=np.int64)
     c = encode(code, info)                                   # [F, K, n]
     pi = make_interleavers(n, K, seed if perm_seed is None else perm_seed, interleave)
-    sigma2 = sigma2_from_snr(q, snr_db)
-    levels = 2.0 * c.astype(np.float64) - (q - 1)            # [F, K, n]
-    y = np.zeros((F, n), dtype=np.float64)
-    for k in range(K):
-        y[:, pi[k]] += levels[:, k, :]
-    if not noiseless:
-        y += rng.standard_normal((F, n)) * math.sqrt(sigma2)
-    return {"c": c, "y": y.astype(np.float32), "sigma2": sigma2, "perm": pi, "snr_db": snr_db,
-            "K": K, "info": info.astype(np.int32)}
+    y, sigma2 = channel_output(q, c, pi, snr_db, seed + 1, noiseless)
+    return {"c": c, "y": y, "sigma2": sigma2, "perm": pi, "snr_db": snr_db, "K": K,
+            "info": info.astype(np.int32)}
 
 
 def random_log_messages(rng: np.random.Generator, shape, q: int, spread: float = 8.0,

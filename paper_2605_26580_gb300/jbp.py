@@ -1,0 +1,213 @@
+"""Thin ctypes binding of the C ABI in ``include/jbp.h`` (argument marshalling only).
+
+Every step of the decoder runs inside ``libjbp.so``; this module only converts
+numpy arrays / torch CUDA tensors to pointers and status codes to exceptions.
+If the library is missing or cannot load, every call raises: there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libjbp.so")
+
+OK, EINVAL, ENOMEM, ECUDA, EAGAIN, ETIMEOUT, ECLOSED = range(7)
+PREC_FP32, PREC_BF16X2, PREC_BF16, PREC_BF16X3 = 0, 1, 2, 3
+FORM_AUTO, FORM_FUSED, FORM_STEP, FORM_PLAIN = 0, 1, 2, 3
+
+EXPORTS = [
+    "jbp_context_create", "jbp_context_destroy", "jbp_create", "jbp_destroy", "jbp_decode",
+    "jbp_submit", "jbp_poll", "jbp_serving_stats", "jbp_last_error", "jbp_step_channel",
+    "jbp_step_check", "jbp_step_var", "jbp_step_syndrome", "jbp_query",
+]
+
+
+class JBPError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("jbp error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Code(C.Structure):
+    _fields_ = [("n", C.c_int32), ("P", C.c_int32), ("q", C.c_int32), ("dv", C.c_int32), ("dc", C.c_int32),
+                ("chk_var", C.POINTER(C.c_int32)), ("chk_coef", C.POINTER(C.c_uint8))]
+
+
+class Channel(C.Structure):
+    _fields_ = [("sigma2", C.c_double), ("interleave", C.c_int32), ("perm", C.POINTER(C.c_int32))]
+
+
+class Options(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("early_stop", C.c_int32), ("precision", C.c_int32), ("device", C.c_int32),
+                ("mem_budget_bytes", C.c_int64), ("block_iters", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class Batch(C.Structure):
+    _fields_ = [("F", C.c_int32), ("y", C.c_void_p), ("hat", C.c_void_p), ("iters", C.c_void_p),
+                ("ok", C.c_void_p), ("logpost", C.c_void_p), ("on_device", C.c_int32), ("form", C.c_int32),
+                ("stream", C.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libjbp.so (raises if it is missing: there is no CPU path)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libjbp.so is not built; run __graft_entry__.build() "
+                                   "(paper_2605_26580_gb300.build.build())")
+            L = C.CDLL(LIB_PATH)
+            vp, i32, i64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+            L.jbp_context_create.argtypes = [C.POINTER(Options), C.POINTER(vp)]
+            L.jbp_context_destroy.argtypes = [vp]
+            L.jbp_create.argtypes = [vp, C.POINTER(Code), i32, i32, C.POINTER(Channel), C.POINTER(vp)]
+            L.jbp_destroy.argtypes = [vp]
+            L.jbp_decode.argtypes = [vp, C.POINTER(Batch)]
+            L.jbp_submit.argtypes = [vp, vp, C.POINTER(u64)]
+            L.jbp_poll.argtypes = [vp, u64, vp, vp, vp]
+            L.jbp_serving_stats.argtypes = [vp, C.POINTER(u64), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            L.jbp_last_error.restype = C.c_char_p
+            L.jbp_step_channel.argtypes = [vp, i32, vp, vp, vp, vp]
+            L.jbp_step_check.argtypes = [vp, i32, vp, i32, vp]
+            L.jbp_step_var.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+            L.jbp_step_syndrome.argtypes = [vp, i32, vp, vp, vp]
+            L.jbp_query.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]
+            for name in EXPORTS:
+                if name != "jbp_last_error":
+                    getattr(L, name).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def check(rc: int) -> int:
+    if rc not in (OK,):
+        raise JBPError(rc, lib().jbp_last_error().decode())
+    return rc
+
+
+def _addr(x):
+    """Pointer of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    assert x.is_contiguous()
+    return x.data_ptr()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Context:
+    def __init__(self, iters: int = 50, early_stop: bool = True, precision: int = PREC_FP32, device: int = 0,
+                 mem_budget_bytes: int = 0, block_iters: int = 0):
+        self.opt = Options(int(iters), int(bool(early_stop)), int(precision), int(device), int(mem_budget_bytes),
+                           int(block_iters))
+        h = C.c_void_p()
+        check(lib().jbp_context_create(C.byref(self.opt), C.byref(h)))
+        self.ptr = h
+
+    def close(self):
+        if self.ptr:
+            check(lib().jbp_context_destroy(self.ptr))
+            self.ptr = None
+
+    def poll(self, ticket: int, n: int, K: int):
+        hat = np.empty((K, n), dtype=np.uint8)
+        ok = np.empty((K,), dtype=np.uint8)
+        it = np.empty((1,), dtype=np.int32)
+        rc = lib().jbp_poll(self.ptr, ticket, _addr(hat), _addr(it), _addr(ok))
+        if rc == EAGAIN:
+            return None
+        check(rc)
+        return {"hat": hat, "iters": int(it[0]), "ok": ok}
+
+    def serving_stats(self):
+        c = C.c_uint64()
+        a, b = C.c_double(), C.c_double()
+        check(lib().jbp_serving_stats(self.ptr, C.byref(c), C.byref(a), C.byref(b)))
+        return {"completed": c.value, "p50_us": a.value, "p99_us": b.value}
+
+
+class Decoder:
+    """One (code, K, q, channel) decoder bound to a Context."""
+
+    def __init__(self, ctx: Context, code: dict, K: int, sigma2: float, perm=None, interleave: bool = True):
+        self.ctx = ctx
+        self.K, self.n, self.q = int(K), int(code["n"]), int(code["q"])
+        self._chk_var = np.ascontiguousarray(code["chk_var"], dtype=np.int32)
+        self._chk_coef = np.ascontiguousarray(code["chk_coef"], dtype=np.uint8)
+        dv = code.get("dv") or int(self._chk_var.size // self.n)
+        c = Code(self.n, int(code["P"]), self.q, int(dv), int(code["dc"]),
+                 self._chk_var.ctypes.data_as(C.POINTER(C.c_int32)),
+                 self._chk_coef.ctypes.data_as(C.POINTER(C.c_uint8)))
+        self._perm = None if perm is None else np.ascontiguousarray(perm, dtype=np.int32).reshape(-1)
+        ch = Channel(float(sigma2), int(bool(interleave and self._perm is not None)),
+                     None if self._perm is None else self._perm.ctypes.data_as(C.POINTER(C.c_int32)))
+        h = C.c_void_p()
+        check(lib().jbp_create(ctx.ptr, C.byref(c), self.K, self.q, C.byref(ch), C.byref(h)))
+        self.ptr = h
+        E = C.c_int32()
+        sb = C.c_int64()
+        fz = C.c_int32()
+        check(lib().jbp_query(h, C.byref(E), C.byref(sb), C.byref(fz)))
+        self.E, self.state_bytes, self.fused_ok = E.value, sb.value, bool(fz.value)
+
+    def close(self):
+        if self.ptr:
+            check(lib().jbp_destroy(self.ptr))
+            self.ptr = None
+
+    # -- whole decodes --------------------------------------------------------
+    def decode(self, y, form: int = FORM_AUTO, want_post: bool = False):
+        """Host decode: y numpy [F, n] float32 -> dict of numpy outputs."""
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        F = y.shape[0]
+        out = {"hat": np.empty((F, self.K, self.n), dtype=np.uint8), "iters": np.empty((F,), dtype=np.int32),
+               "ok": np.empty((F, self.K), dtype=np.uint8)}
+        if want_post:
+            out["post"] = np.empty((F, self.K, self.n, self.q), dtype=np.float32)
+        b = Batch(F, _addr(y), _addr(out["hat"]), _addr(out["iters"]), _addr(out["ok"]), _addr(out.get("post")),
+                  0, int(form), None)
+        check(lib().jbp_decode(self.ptr, C.byref(b)))
+        return out
+
+    def decode_device(self, y, hat, iters, ok, post=None, form: int = FORM_AUTO, stream=None):
+        """Enqueue a decode on device tensors (returns without waiting)."""
+        b = Batch(int(y.shape[0]), _addr(y), _addr(hat), _addr(iters), _addr(ok), _addr(post), 1, int(form),
+                  _stream_ptr(stream))
+        check(lib().jbp_decode(self.ptr, C.byref(b)))
+
+    # -- serving --------------------------------------------------------------
+    def submit(self, y_frame) -> int:
+        y = np.ascontiguousarray(y_frame, dtype=np.float32).reshape(-1)
+        t = C.c_uint64()
+        check(lib().jbp_submit(self.ptr, _addr(y), C.byref(t)))
+        return t.value
+
+    # -- single steps on device tensors ---------------------------------------
+    def step_channel(self, y, msg, ch2v, stream=None):
+        check(lib().jbp_step_channel(self.ptr, int(y.shape[0]), _addr(y), _addr(msg), _addr(ch2v), _stream_ptr(stream)))
+
+    def step_check(self, msg, precision: int = PREC_FP32, stream=None):
+        check(lib().jbp_step_check(self.ptr, int(msg.shape[0]), _addr(msg), int(precision), _stream_ptr(stream)))
+
+    def step_var(self, ch2v, msg, post, hat, stream=None):
+        check(lib().jbp_step_var(self.ptr, int(ch2v.shape[0]), _addr(ch2v), _addr(msg), _addr(post), _addr(hat),
+                                 _stream_ptr(stream)))
+
+    def step_syndrome(self, hat, ok, stream=None):
+        check(lib().jbp_step_syndrome(self.ptr, int(hat.shape[0]), _addr(hat), _addr(ok), _stream_ptr(stream)))

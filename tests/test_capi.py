@@ -1,0 +1,62 @@
+"""The C-ABI library loads and exports every entry point declared in include/jbp.h;
+host-side argument checks work without a GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    with open(os.path.join(ROOT, "include", "jbp.h")) as f:
+        for m in re.finditer(r"^\s*(?:int|const char \*)\s*(jbp_\w+)\s*\(", f.read(), re.M):
+            names.append(m.group(1))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = set(_declared())
+    for required in ["jbp_context_create", "jbp_create", "jbp_decode", "jbp_submit", "jbp_poll",
+                     "jbp_destroy", "jbp_context_destroy", "jbp_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(jbp_lib):
+    lib = C.CDLL(jbp_lib.LIB_PATH)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(_declared()) <= set(jbp_lib.EXPORTS) | {"jbp_last_error"}
+
+
+def test_null_arguments_are_rejected(jbp_lib):
+    lib = jbp_lib.lib()
+    assert lib.jbp_context_create(None, None) == jbp_lib.EINVAL
+    assert b"NULL" in lib.jbp_last_error()
+    assert lib.jbp_decode(None, None) == jbp_lib.EINVAL
+    assert lib.jbp_destroy(None) == jbp_lib.EINVAL
+    assert lib.jbp_poll(None, 1, None, None, None) == jbp_lib.EINVAL
+    assert lib.jbp_step_check(None, 1, None, 0, None) == jbp_lib.EINVAL
+
+
+def test_bad_options_are_rejected_before_touching_the_gpu(jbp_lib):
+    opt = jbp_lib.Options(0, 1, 0, 0, 0, 0)          # iters = 0
+    h = C.c_void_p()
+    assert jbp_lib.lib().jbp_context_create(C.byref(opt), C.byref(h)) == jbp_lib.EINVAL
+    opt = jbp_lib.Options(10, 1, 9, 0, 0, 0)         # precision 9
+    assert jbp_lib.lib().jbp_context_create(C.byref(opt), C.byref(h)) == jbp_lib.EINVAL
+
+
+def test_no_gpu_fails_loudly(jbp_lib):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    with pytest.raises(jbp_lib.JBPError) as ei:
+        jbp_lib.Context(iters=5)
+    assert ei.value.code in (jbp_lib.ECUDA, jbp_lib.EINVAL)

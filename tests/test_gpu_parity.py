@@ -1,0 +1,253 @@
+"""GPU parity: every kernel of the decoder against the FP64 oracle on the same
+seeded inputs, through the C ABI.
+
+Tolerances (derived in the design notes, "Parity bar"):
+  * channel, v2c and posterior log-messages: |gpu - oracle| <= 1e-4 wherever the
+    oracle entry is >= ln(1e-4) (FP32 trellis and sums have no cancellation);
+    below that both must be < ln(1e-4) + 1e-4;
+  * check-node c2v (FP32 Walsh-Hadamard butterflies): in the linear domain
+    |exp(gpu) - exp(oracle)| <= B_q = q (4 log2 q + 2) 2^-24 (forward transform,
+    product and inverse transform error relative to the largest entry); in the
+    log domain, for every entry with oracle probability rho >= 1e-4 (relative
+    to the max), |gpu - oracle| <= 1e-4 + 2 B_q / rho (a linear error B_q is a
+    relative error B_q / rho at that entry; the cancellation of the transform
+    makes small entries less accurate than large ones);
+  * hard decisions bit-exact wherever the FP64 posterior margin p(1) - p(2) > 1e-6;
+  * syndromes bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2605_26580_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+LN_1E4 = math.log(1e-4)
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def wht_bound(q):
+    return q * (4 * math.log2(q) + 2) * 2.0 ** -24
+
+
+def masked_log_err(gpu, ref, thresh=LN_1E4):
+    gpu = np.asarray(gpu, dtype=np.float64)
+    mask = ref >= thresh
+    err_in = np.abs(gpu - ref)[mask].max() if mask.any() else 0.0
+    # outside the mask both must be small
+    outside_ok = bool(np.all(gpu[~mask] < thresh + 1e-4)) if (~mask).any() else True
+    return err_in, outside_ok
+
+
+@pytest.fixture(scope="module")
+def env(jbp_lib, oracle):
+    torch = _torch()
+    return jbp_lib, oracle, torch
+
+
+def _decoder(jbp, code, K, sigma2, perm, iters=20, early_stop=True, precision=0):
+    ctx = jbp.Context(iters=iters, early_stop=early_stop, precision=precision)
+    dec = jbp.Decoder(ctx, code, K, sigma2, perm)
+    return ctx, dec
+
+
+STEP_CASES = [  # (K, q, n)
+    (2, 4, 64), (4, 16, 256), (3, 8, 64), (1, 16, 64), (4, 64, 128), (8, 16, 64), (16, 4, 32), (2, 2, 24),
+    (5, 32, 40),
+]
+
+
+@pytest.mark.parametrize("K,q,n", STEP_CASES)
+def test_step_channel_matches_oracle(env, K, q, n):
+    jbp, O, torch = env
+    code = I.make_code(n, q)
+    fr = I.make_frames(code, K, 12.0, 7, seed=K * 1000 + q + n)
+    rng = np.random.default_rng(n + q)
+    E = code["P"] * code["dc"]
+    c2v = I.random_log_messages(rng, (7, K, E), q, spread=3.0).astype(np.float32)
+    ctx, dec = _decoder(jbp, code, K, fr["sigma2"], fr["perm"])
+    try:
+        y_d = torch.from_numpy(fr["y"]).cuda()
+        msg_d = torch.from_numpy(c2v).cuda()
+        ch_d = torch.empty((7, K, n, q), dtype=torch.float32, device="cuda")
+        dec.step_channel(y_d, msg_d, ch_d)
+        torch.cuda.synchronize()
+        ch_g, v2c_g = ch_d.cpu().numpy(), msg_d.cpu().numpy()
+    finally:
+        dec.close()
+        ctx.close()
+    ch_o = O.step_channel(code, K, fr["sigma2"], fr["perm"], fr["y"], c2v.astype(np.float64))
+    v2c_o = O.step_v2c(code, K, ch_o, c2v.astype(np.float64))
+    e1, ok1 = masked_log_err(ch_g, ch_o)
+    e2, ok2 = masked_log_err(v2c_g, v2c_o)
+    print("channel K=%d q=%d n=%d: ch2v err %.2e, v2c err %.2e" % (K, q, n, e1, e2))
+    assert e1 <= 1e-4 and ok1
+    assert e2 <= 1e-4 and ok2
+
+
+@pytest.mark.parametrize("K,q,n", STEP_CASES)
+def test_step_check_matches_oracle(env, K, q, n):
+    jbp, O, torch = env
+    code = I.make_code(n, q)
+    rng = np.random.default_rng(3 * n + q)
+    E = code["P"] * code["dc"]
+    v2c = I.random_log_messages(rng, (5, K, E), q, spread=3.0).astype(np.float32)
+    ctx, dec = _decoder(jbp, code, K, 1.0, None)
+    try:
+        msg_d = torch.from_numpy(v2c).cuda()
+        dec.step_check(msg_d)
+        torch.cuda.synchronize()
+        c2v_g = msg_d.cpu().numpy().astype(np.float64)
+    finally:
+        dec.close()
+        ctx.close()
+    c2v_o = O.step_check_v2c(code, K, v2c.astype(np.float64))
+    B = wht_bound(q)
+    lin = np.abs(np.exp(c2v_g) - np.exp(c2v_o)).max()
+    rho = np.exp(c2v_o)
+    mask = rho >= 1e-4
+    ratio = (np.abs(c2v_g - c2v_o)[mask] / (1e-4 + 2 * B / rho[mask])).max()
+    e_log4, _ = masked_log_err(c2v_g, c2v_o)
+    e_big, _ = masked_log_err(c2v_g, c2v_o, thresh=math.log(0.5))
+    print("check K=%d q=%d: linear err %.2e (bound %.2e), log err %.2e (rho>=0.5), %.2e (rho>=1e-4), "
+          "err/allowed %.3f" % (K, q, lin, B, e_big, e_log4, ratio))
+    assert lin <= B
+    assert ratio <= 1.0
+    assert np.allclose(c2v_g.max(-1), 0.0, atol=1e-6)
+    assert c2v_g.min() >= math.log(1e-12) - 1e-3
+
+
+@pytest.mark.parametrize("K,q,n", [(2, 4, 64), (4, 16, 256), (3, 64, 64), (1, 2, 16)])
+def test_step_var_and_syndrome_match_oracle(env, K, q, n):
+    jbp, O, torch = env
+    code = I.make_code(n, q)
+    rng = np.random.default_rng(5 * n + q)
+    E = code["P"] * code["dc"]
+    ch2v = I.random_log_messages(rng, (6, K, n), q, spread=2.0).astype(np.float32)
+    c2v = I.random_log_messages(rng, (6, K, E), q, spread=2.0).astype(np.float32)
+    ctx, dec = _decoder(jbp, code, K, 1.0, None)
+    try:
+        ch_d, msg_d = torch.from_numpy(ch2v).cuda(), torch.from_numpy(c2v).cuda()
+        post_d = torch.empty_like(ch_d)
+        hat_d = torch.empty((6, K, n), dtype=torch.uint8, device="cuda")
+        dec.step_var(ch_d, msg_d, post_d, hat_d)
+        # syndromes of the decisions and of true codewords
+        cw = I.make_frames(code, K, 10.0, 6, seed=1)["c"]
+        cw_d = torch.from_numpy(cw).cuda()
+        ok_hat = torch.empty((6, K), dtype=torch.uint8, device="cuda")
+        ok_cw = torch.empty((6, K), dtype=torch.uint8, device="cuda")
+        dec.step_syndrome(hat_d, ok_hat)
+        dec.step_syndrome(cw_d, ok_cw)
+        torch.cuda.synchronize()
+        post_g, hat_g = post_d.cpu().numpy(), hat_d.cpu().numpy()
+        okh, okc = ok_hat.cpu().numpy(), ok_cw.cpu().numpy()
+    finally:
+        dec.close()
+        ctx.close()
+    post_o, hat_o = O.step_var(code, K, ch2v.astype(np.float64), c2v.astype(np.float64))
+    e, _ = masked_log_err(post_g, post_o)
+    assert e <= 1e-4
+    p = np.exp(post_o)
+    p /= p.sum(-1, keepdims=True)
+    ps = np.sort(p, -1)
+    sure = (ps[..., -1] - ps[..., -2]) > 1e-6
+    assert (hat_g[sure] == hat_o[sure]).all()
+    assert (okh == O.syndrome_ok(code, K, hat_g)).all()
+    assert okc.all()
+
+
+def _margin_mismatch(got, ref):
+    sure = ref["margin"] > 1e-6
+    return int(((got["hat"] != ref["hat"]) & sure).sum()), int(sure.sum())
+
+
+@pytest.mark.parametrize("form", ["fused", "step"])
+def test_decode_config1_matches_oracle(env, form):
+    """K=2, GF(4), n=64, SNR 10 dB, 20 flooding iterations, 1,000 frames."""
+    jbp, O, torch = env
+    code = I.make_code(64, 4)
+    fr = I.make_frames(code, 2, 10.0, 1000, seed=1_000_000_000)
+    ctx, dec = _decoder(jbp, code, 2, fr["sigma2"], fr["perm"], iters=20, early_stop=False)
+    try:
+        got = dec.decode(fr["y"], form=jbp.FORM_FUSED if form == "fused" else jbp.FORM_STEP)
+    finally:
+        dec.close()
+        ctx.close()
+    ref = O.decode(code, 2, fr["sigma2"], fr["perm"], fr["y"], 20, early_stop=False, want_margin=True)
+    bad, total = _margin_mismatch(got, ref)
+    frames_bad = int(((got["hat"] != ref["hat"]) & (ref["margin"] > 1e-6)).any((1, 2)).sum())
+    ser_g = (got["hat"] != fr["c"]).mean()
+    ser_o = (ref["hat"] != fr["c"]).mean()
+    print("config1 %s: %d/%d confident decisions differ (%d frames); SER gpu %.5f oracle %.5f"
+          % (form, bad, total, frames_bad, ser_g, ser_o))
+    assert (got["iters"] == 20).all()
+    assert bad == 0
+    assert (got["ok"] == ref["ok"]).all()
+
+
+def test_forms_are_bit_identical(env):
+    jbp, O, torch = env
+    code = I.make_code(64, 16)
+    fr = I.make_frames(code, 3, 12.0, 37, seed=77)
+    ctx, dec = _decoder(jbp, code, 3, fr["sigma2"], fr["perm"], iters=15, early_stop=True)
+    try:
+        a = dec.decode(fr["y"], form=jbp.FORM_FUSED, want_post=True)
+        b = dec.decode(fr["y"], form=jbp.FORM_STEP, want_post=True)
+        c = dec.decode(fr["y"][:5], form=jbp.FORM_PLAIN, want_post=True)
+    finally:
+        dec.close()
+        ctx.close()
+    for key in ("hat", "iters", "ok", "post"):
+        assert np.array_equal(a[key], b[key]), key
+        assert np.array_equal(a[key][:5], c[key]), key
+
+
+@pytest.mark.parametrize("K,q,n,F,T", [(1, 2, 12, 1, 3), (4, 16, 256, 153, 6), (16, 4, 32, 9, 4),
+                                       (3, 64, 64, 5, 3), (2, 8, 12, 40, 8), (6, 32, 48, 3, 3)])
+def test_decode_edge_shapes_match_oracle(env, K, q, n, F, T):
+    """Single frame, ragged batches, K = 1 and K = 16, q = 2 and q = 64, tiny n."""
+    jbp, O, torch = env
+    code = I.make_code(n, q)
+    fr = I.make_frames(code, K, 14.0, F, seed=F * 7 + K)
+    ctx, dec = _decoder(jbp, code, K, fr["sigma2"], fr["perm"], iters=T, early_stop=True)
+    try:
+        got = dec.decode(fr["y"])
+        empty = dec.decode(np.zeros((0, n), np.float32))
+    finally:
+        dec.close()
+        ctx.close()
+    ref = O.decode(code, K, fr["sigma2"], fr["perm"], fr["y"], T, early_stop=True, want_margin=True)
+    bad, _ = _margin_mismatch(got, ref)
+    assert bad == 0
+    assert (got["iters"] == ref["iters"]).all()
+    assert empty["hat"].shape == (0, K, n)
+
+
+def test_literal_channel_mode(env):
+    """interleave = 0 (every pi_k the identity): the users are exchangeable, so
+    their posteriors are identical and often nearly tied; decisions must agree
+    where the FP64 margin exceeds 1e-4 (FP32 rounding accumulated over the
+    iterations can flip a near-tie between 1e-6 and 1e-4; the count is printed)."""
+    jbp, O, torch = env
+    code = I.make_code(64, 4)
+    fr = I.make_frames(code, 2, 12.0, 50, seed=5, interleave=False)
+    ctx = jbp.Context(iters=10, early_stop=False)
+    dec = jbp.Decoder(ctx, code, 2, fr["sigma2"], None, interleave=False)
+    try:
+        got = dec.decode(fr["y"])
+    finally:
+        dec.close()
+        ctx.close()
+    ref = O.decode(code, 2, fr["sigma2"], None, fr["y"], 10, early_stop=False, want_margin=True)
+    diff = got["hat"] != ref["hat"]
+    print("literal mode: differing decisions at FP64 margins", np.sort(ref["margin"][diff])[:10])
+    assert not (diff & (ref["margin"] > 1e-4)).any()
+    assert (got["hat"][:, 0] == got["hat"][:, 1]).all()   # symmetric users, identical decisions
