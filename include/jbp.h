@@ -199,6 +199,29 @@ int jbp_step_var(jbp_h *h, int32_t F, const float *ch2v, const float *msg, float
 /* (d) syndrome: ok[f*K+k] = 1 iff every check of user k is satisfied by hat. */
 int jbp_step_syndrome(jbp_h *h, int32_t F, const uint8_t *hat, uint8_t *ok, void *stream);
 
+/* Decode without allocating memory.  For callers that may not allocate device
+ * memory themselves (code running inside another framework's memory pool or
+ * under a hard memory cap, or a process that may not call cudaMalloc): the
+ * paper has no counterpart; this is a deployment variant of the step-form
+ * decode (the same kernels as jbp_decode with JBP_FORM_STEP).  Its working
+ * memory -- code tables and message state -- lives in one fixed 16 MiB device
+ * array inside the library, which every GPU that loads the library holds until
+ * the process exits; no call allocates (no cudaMalloc/cudaFree, no allocating
+ * library routine).  code/chan: host pointers as for jbp_create (dc = 4,
+ * regular dv, q in 2..64, K in 1..16).  T >= 1 iterations, early_stop as in
+ * jbp_options.  y [F*n], hat [F*K*n], iters [F], ok [F*K]: device pointers of the
+ * current device.  The work is enqueued on `stream` (a cudaStream_t, NULL = the
+ * default stream) and the call returns without waiting.  Errors: JBP_EINVAL for
+ * bad arguments, and when F frames of this shape do not fit the fixed array (the
+ * message gives the maximum F); JBP_ECUDA for CUDA failures.  The first call on
+ * each device looks up the array's device address (set-up); make that first
+ * call before any stream capture.  All calls share the array and it keeps the
+ * previous call's contents (each call clears what must start at zero); calls
+ * whose work overlaps on the GPU race on it, so serialise them. */
+int jbp_decode_noalloc(const jbp_code *code, int32_t K, const jbp_channel *chan, int32_t T,
+                       int32_t early_stop, int32_t F, const float *y, uint8_t *hat, int32_t *iters,
+                       uint8_t *ok, void *stream);
+
 /* Shape information of a handle (host pointers, any may be NULL): edges E,
  * per-frame device state bytes, and whether one frame fits the fused form. */
 int jbp_query(jbp_h *h, int32_t *E, int64_t *state_bytes_per_frame, int32_t *fused_ok);

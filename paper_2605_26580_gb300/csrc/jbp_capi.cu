@@ -51,6 +51,8 @@ static int cuda_fail(cudaError_t e, const char* what)
 
 extern "C" const char* jbp_last_error(void) { return g_last_error.c_str(); }
 
+void jbp::set_last_error(const char* msg) { g_last_error = msg; }
+
 static double now_us()
 {
     return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now().time_since_epoch()).count();

@@ -47,6 +47,9 @@ cudaError_t launch_fused(const Graph& g, const FusedPlan& plan, int F, const flo
                          int early_stop, uint8_t* hat, int32_t* iters, uint8_t* ok, float* post,
                          cudaStream_t s);
 
+// Record the message returned by jbp_last_error() on this thread (jbp_capi.cu).
+void set_last_error(const char* msg);
+
 // Bytes of message state of one frame in either form: msg [K*E*Q] + ch2v [K*n*Q] floats.
 inline int64_t state_bytes(const Graph& g)
 {
