@@ -21,10 +21,11 @@
  *       early exit on convergence (Table 1 caption: at most 50 iterations
  *       with early exit).
  *
- * Messages are FP32 log-probabilities shifted to a maximum of 0.  A c2v
- * message is floored at 1e-12 of its maximum; a channel message is clipped at
- * ln(1e-12).  The schedule is flooding: per iteration all channel nodes, then
- * all checks, then the decisions.
+ * Messages are FP32 probability vectors scaled to a largest entry of 1 (their
+ * natural logs are the decoder's max-normalised log-messages).  A c2v message
+ * is floored at 1e-12 of its maximum; a channel message is floored at 1e-12.
+ * The schedule is flooding: per iteration all channel nodes, then all checks,
+ * then the decisions.
  *
  * Conventions shared by every entry point:
  *   - Every call returns a jbp_status.  On failure jbp_last_error() returns a
@@ -98,7 +99,8 @@ typedef struct {
 
 /* Context options.  iters: maximum iterations T (>= 1).  early_stop: 1 stops a
  * frame at the first iteration after which all K syndromes are zero.
- * precision: jbp_precision of the check-node transform.  mem_budget_bytes:
+ * precision: jbp_precision of the check-node transform (the tensor-core
+ * variants run in the step form; AUTO then picks STEP).  mem_budget_bytes:
  * cap on the device memory the context allocates (0 = 90% of free memory at
  * creation).  device: CUDA device ordinal.  block_iters: iterations per
  * serving block (0 = 5). */
@@ -179,8 +181,9 @@ const char *jbp_last_error(void);
  * for testing and for callers that schedule iterations themselves.
  * Layouts: msg [F*K*E*q] holds, per edge, the check-to-variable message
  * (before jbp_step_channel, after jbp_step_check) or the variable-to-check
- * message (after jbp_step_channel); ch2v and post [F*K*n*q]; hat [F*K*n];
- * ok [F*K]; E = P*dc. ---- */
+ * message (after jbp_step_channel), as probabilities scaled to max 1 (the
+ * uniform start is all ones); ch2v [F*K*n*q] likewise; post [F*K*n*q]
+ * max-normalised log-posterior; hat [F*K*n]; ok [F*K]; E = P*dc. ---- */
 
 /* (a) channel node for every channel use of F frames: reads the c2v messages in
  * msg and y [F*n]; writes ch2v and replaces each c2v in msg by the v2c message
@@ -221,6 +224,11 @@ int jbp_step_syndrome(jbp_h *h, int32_t F, const uint8_t *hat, uint8_t *ok, void
 int jbp_decode_noalloc(const jbp_code *code, int32_t K, const jbp_channel *chan, int32_t T,
                        int32_t early_stop, int32_t F, const float *y, uint8_t *hat, int32_t *iters,
                        uint8_t *ok, void *stream);
+
+/* Counters of a handle since creation (host pointers, may be NULL):
+ * log_fallbacks = channel messages whose linear-domain computation underflowed
+ * and were recomputed in log space.  Synchronises the device. */
+int jbp_stats(jbp_h *h, uint64_t *log_fallbacks);
 
 /* Shape information of a handle (host pointers, any may be NULL): edges E,
  * per-frame device state bytes, and whether one frame fits the fused form. */

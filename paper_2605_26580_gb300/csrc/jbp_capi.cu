@@ -176,6 +176,7 @@ struct jbp_h {
     int32_t* d_use_pos = nullptr;
     uint8_t* d_gf_mul = nullptr;
     uint8_t* d_gf_div = nullptr;
+    unsigned long long* d_fallbacks = nullptr;
     int64_t table_bytes = 0;
     Workspace ws;
     std::mutex ws_mu;
@@ -188,6 +189,7 @@ struct jbp_h {
         g.inv_sigma2 = (float)(1.0 / sigma2);
         g.chk_var = d_chk_var; g.chk_coef = d_chk_coef; g.var_edge = d_var_edge;
         g.use_pos = d_use_pos; g.gf_mul = d_gf_mul; g.gf_div = d_gf_div;
+        g.log_fallbacks = d_fallbacks;
         return g;
     }
 };
@@ -299,7 +301,7 @@ static int run_step_iters(jbp_h* h, Workspace& w, int F, const float* y, uint8_t
     jbp_ctx* ctx = h->ctx;
     const Graph g = h->graph();
     const size_t fs = (size_t)h->K * h->E * h->Q;
-    JBP_CU(cudaMemsetAsync(w.msg, 0, sizeof(float) * fs * F, s), "memset msg");
+    JBP_CU(launch_fill(w.msg, fs * F, 1.0f, s), "init msg");
     JBP_CU(cudaMemsetAsync(w.active, 1, (size_t)F, s), "memset active");
     JBP_CU(cudaMemsetAsync(w.unsat, 0, (size_t)F * h->K, s), "memset unsat");
     StepCtl c{w.active, w.unsat, iters, ok};
@@ -319,7 +321,12 @@ static int decode_device(jbp_h* h, Workspace& w, int form, int F, const float* y
 {
     if (F == 0) return JBP_OK;
     jbp_ctx* ctx = h->ctx;
-    if (form == JBP_FORM_AUTO) form = h->fused_ok ? JBP_FORM_FUSED : JBP_FORM_STEP;
+    // the fused kernel runs the FP32 butterfly check node; the tensor-core
+    // precision variants run in the step form
+    if (form == JBP_FORM_AUTO) form = (h->fused_ok && ctx->opt.precision == JBP_PREC_FP32) ? JBP_FORM_FUSED : JBP_FORM_STEP;
+    if (form == JBP_FORM_FUSED && ctx->opt.precision != JBP_PREC_FP32)
+        return fail(JBP_EINVAL, "the fused form runs the FP32 check node; use the step form for precision %d",
+                    ctx->opt.precision);
     if (form == JBP_FORM_FUSED) {
         if (!h->fused_ok) return fail(JBP_EINVAL, "one frame does not fit the fused form (shared memory)");
         FusedPlan plan;
@@ -471,7 +478,8 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
         (rc = dev_alloc(ctx, &h->d_var_edge, (size_t)n * dv, &h->table_bytes)) ||
         (rc = dev_alloc(ctx, &h->d_use_pos, (size_t)K * n, &h->table_bytes)) ||
         (rc = dev_alloc(ctx, &h->d_gf_mul, (size_t)q * q, &h->table_bytes)) ||
-        (rc = dev_alloc(ctx, &h->d_gf_div, (size_t)q * q, &h->table_bytes))) {
+        (rc = dev_alloc(ctx, &h->d_gf_div, (size_t)q * q, &h->table_bytes)) ||
+        (rc = dev_alloc(ctx, &h->d_fallbacks, (size_t)1, &h->table_bytes))) {
         jbp_destroy(h);
         return rc;
     }
@@ -481,7 +489,8 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
         (e = cudaMemcpy(h->d_var_edge, var_edge.data(), sizeof(int32_t) * var_edge.size(), cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(h->d_use_pos, use_pos.data(), sizeof(int32_t) * use_pos.size(), cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(h->d_gf_mul, gmul.data(), gmul.size(), cudaMemcpyHostToDevice)) ||
-        (e = cudaMemcpy(h->d_gf_div, gdiv.data(), gdiv.size(), cudaMemcpyHostToDevice))) {
+        (e = cudaMemcpy(h->d_gf_div, gdiv.data(), gdiv.size(), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemset(h->d_fallbacks, 0, sizeof(unsigned long long)))) {
         jbp_destroy(h);
         return cuda_fail(e, "jbp_create: copy tables");
     }
@@ -533,6 +542,7 @@ extern "C" int jbp_destroy(jbp_h* h)
     dev_free(ctx, h->d_use_pos, sizeof(int32_t) * (size_t)h->K * h->n);
     dev_free(ctx, h->d_gf_mul, (size_t)h->Q * h->Q);
     dev_free(ctx, h->d_gf_div, (size_t)h->Q * h->Q);
+    dev_free(ctx, h->d_fallbacks, sizeof(unsigned long long));
     delete h;
     return JBP_OK;
 }
@@ -543,6 +553,17 @@ extern "C" int jbp_query(jbp_h* h, int32_t* E, int64_t* state_bytes_per_frame, i
     if (E) *E = h->E;
     if (state_bytes_per_frame) *state_bytes_per_frame = state_bytes(h->graph());
     if (fused) *fused = h->fused_ok ? 1 : 0;
+    return JBP_OK;
+}
+
+extern "C" int jbp_stats(jbp_h* h, uint64_t* log_fallbacks)
+{
+    if (!h) return fail(JBP_EINVAL, "jbp_stats: NULL handle");
+    JBP_CU(cudaSetDevice(h->ctx->device), "cudaSetDevice");
+    unsigned long long v = 0;
+    JBP_CU(cudaDeviceSynchronize(), "jbp_stats");
+    JBP_CU(cudaMemcpy(&v, h->d_fallbacks, sizeof v, cudaMemcpyDeviceToHost), "jbp_stats: copy");
+    if (log_fallbacks) *log_fallbacks = v;
     return JBP_OK;
 }
 

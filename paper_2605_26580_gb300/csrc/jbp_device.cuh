@@ -1,15 +1,22 @@
 // jbp_device.cuh -- per-node device routines of joint FFT belief propagation.
 //
-// Every routine works on one "unit" (a channel use, a check of one user, a
-// variable of one user) with a team of T = min(q, 32) lanes of one warp; lane
-// tl owns the symbols a = v*T + tl, v < V = q/T.  Teams synchronise only with
-// their own lanes (team masks), so teams of one warp may diverge.  Pointers are
-// generic: the same routines run on HBM-resident state (step kernels) and on
-// shared-memory state (fused kernel).
+// Message format: every stored message is an FP32 probability vector over the q
+// symbols scaled so that its largest entry is 1 (the log-message of the decoder
+// is its natural log).  A c2v message is floored at kRelFloor of its maximum
+// (after the inverse transform); a channel message is floored at kRelFloor.
+// Storing probabilities rather than logs keeps the hot loops free of exp/log;
+// the relative precision of a stored entry is 2^-24 at every magnitude.
 //
-// Message convention: FP32 log-probabilities with maximum 0.  A stored c2v
-// message is floored at kRelFloor of its maximum (in the linear domain after
-// the inverse transform); a channel message is clipped at kLogFloor.
+// Message block of one (frame, user): the check-major edges e = 4j + d, edge e
+// at blk + j*cbs + d*q (cbs = 4q in HBM, 4q + 4 in shared memory to spread
+// banks).  Channel messages: ch2v[(k*n + i)*q + a], dense.
+//
+// Two execution shapes per node type:
+//   thread: one thread owns a unit (channel use, check of one user, variable of
+//           one user) with all its q-vectors in registers (q <= 16);
+//   team:   T = min(q, 32) lanes of one warp own a unit, lane tl holding
+//           symbols a = v*T + tl (q = 32, 64, and the channel for K > 4).
+// Teams synchronise only their own lanes (team masks), so teams may diverge.
 #pragma once
 
 #include <cstdint>
@@ -18,10 +25,10 @@
 namespace jbp {
 
 constexpr float kRelFloor = 1e-12f;
-constexpr float kLogFloor = -27.631021115928547f;  // ln(1e-12)
-constexpr float kFallbackMax = 1e-30f;             // linear trellis underflow guard
+constexpr float kFallbackMax = 1e-30f;   // linear channel output below this: redo in log space
 constexpr int kMaxDv = 8;
 constexpr int kMaxK = 16;
+constexpr int kDC = 4;                   // check degree of the kernels
 constexpr float kNegInf = -__builtin_inff();
 
 // Device view of one decoder: code, interleavers, channel and GF tables.
@@ -34,7 +41,17 @@ struct Graph {
     const int32_t* use_pos;   // [K*n]   use_pos[k*n+t] = pi_k^{-1}(t)
     const uint8_t* gf_mul;    // [Q*Q]   gf_mul[h*Q+x] = h*x
     const uint8_t* gf_div;    // [Q*Q]   gf_div[h*Q+x] = h^{-1}*x
+    unsigned long long* log_fallbacks;   // counts channel messages redone in log space (may be null)
 };
+
+__device__ __forceinline__ float* edge_ptr(float* blk, int e, int cbs, int Q)
+{
+    return blk + (e >> 2) * cbs + (e & 3) * Q;
+}
+__device__ __forceinline__ const float* edge_ptr(const float* blk, int e, int cbs, int Q)
+{
+    return blk + (e >> 2) * cbs + (e & 3) * Q;
+}
 
 template <int Q>
 struct Shape {
@@ -67,28 +84,339 @@ __device__ __forceinline__ float team_max(float v, unsigned mask)
     return v;
 }
 
-template <int T>
-__device__ __forceinline__ bool team_any(bool p, unsigned mask)
+// ---------------------------------------------------------------------------
+// register vector helpers (thread shape)
+// ---------------------------------------------------------------------------
+
+template <int Q>
+__device__ __forceinline__ void vload(const float* p, float (&v)[Q])
 {
-    int v = p ? 1 : 0;
+    if constexpr (Q % 4 == 0) {
 #pragma unroll
-    for (int o = T / 2; o > 0; o >>= 1) v |= __shfl_xor_sync(mask, v, o, T);
-    return v != 0;
+        for (int i = 0; i < Q / 4; ++i) {
+            const float4 t = reinterpret_cast<const float4*>(p)[i];
+            v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q / 2; ++i) {
+            const float2 t = reinterpret_cast<const float2*>(p)[i];
+            v[2 * i] = t.x; v[2 * i + 1] = t.y;
+        }
+    }
+}
+
+template <int Q>
+__device__ __forceinline__ void vstore(float* p, const float (&v)[Q])
+{
+    if constexpr (Q % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < Q / 4; ++i)
+            reinterpret_cast<float4*>(p)[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q / 2; ++i) reinterpret_cast<float2*>(p)[i] = make_float2(v[2 * i], v[2 * i + 1]);
+    }
+}
+
+template <int N>
+__device__ __forceinline__ float vmax(const float (&v)[N])
+{
+    float m = v[0];
+#pragma unroll
+    for (int i = 1; i < N; ++i) m = fmaxf(m, v[i]);
+    return m;
 }
 
 // ---------------------------------------------------------------------------
 // Channel node
 // ---------------------------------------------------------------------------
+//
+// With a_k the symbol of user k and s = sum_k a_k, the likelihood of y is
+// G(s) = exp(-(y - (2s - K(q-1)))^2 / (2 sigma2)), and the message to user k is
+//   ch2v_k(a) ~ sum over the other users' symbols of G(a + sum_{j!=k} a_j) prod mu_j(a_j),
+// a leave-one-out combination of the K incoming messages mu_j.  The exponent is
+// taken relative to the nearest symbol sum s*: with r = y - (2s* - K(q-1)) and
+// d = s* - s, -(y - L_s)^2/(2 sigma2) + (y - L_s*)^2/(2 sigma2) = -2 d (r + d)/sigma2,
+// which keeps its relative accuracy for every entry that matters.
 
-// Sum-product arithmetic of the trellis: linear domain (fast path) or log
-// domain (taken when the linear pass underflows).
+struct GaussTerm {
+    int ss;          // nearest symbol sum s*
+    float r;         // y - (2 s* - K(q-1))
+    float inv_s2;    // 1 / sigma2
+    __device__ __forceinline__ float expo(int s) const
+    {
+        const float d = (float)(ss - s);
+        return -2.0f * d * (r + d) * inv_s2;
+    }
+};
+
+__device__ __forceinline__ GaussTerm gauss_term(float y, int K, int Q, float inv_s2)
+{
+    const int KD = K * (Q - 1);
+    float sf = rintf((y + (float)KD) * 0.5f);
+    sf = fminf(fmaxf(sf, 0.0f), (float)KD);
+    GaussTerm t;
+    t.ss = (int)sf;
+    t.r = y - (float)(2 * t.ss - KD);
+    t.inv_s2 = inv_s2;
+    return t;
+}
+
+// -- thread shape: K <= 4, q <= 16, every array in registers -----------------
+//
+// Leave-one-out without division by a balanced split of the users (for K = 4:
+// {0,1} | {2,3}): with P23 = mu_2 (*) mu_3 (integer convolution) and the scored
+// suffix H23(v) = sum_s P23(s) G(v + s), the messages to users 0 and 1 are
+// sum_b mu_1(b) H23(a + b) and sum_b mu_0(b) H23(a + b); users 2 and 3 use the
+// mirror quantities.  K = 3 uses the prefix F_2 = mu_0 (*) mu_1 and the suffix
+// B_2(v) = sum_b mu_2(b) G(v + b).  G is streamed (one exp per sum value per pass).
+
+template <int NA, int NB>
+__device__ __forceinline__ void rconv(const float (&A)[NA], const float (&B)[NB], float (&C)[NA + NB - 1])
+{
+#pragma unroll
+    for (int i = 0; i < NA + NB - 1; ++i) C[i] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NA; ++i)
+#pragma unroll
+        for (int j = 0; j < NB; ++j) C[i + j] = fmaf(A[i], B[j], C[i + j]);
+}
+
+// H(v) = sum_s P(s) X(v + s), v in [0, NX - NP]
+template <int NP, int NX>
+__device__ __forceinline__ void rcorr(const float (&P)[NP], const float (&X)[NX], float (&H)[NX - NP + 1])
+{
+#pragma unroll
+    for (int v = 0; v < NX - NP + 1; ++v) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int s = 0; s < NP; ++s) acc = fmaf(P[s], X[v + s], acc);
+        H[v] = acc;
+    }
+}
+
+// H1(v) = sum_s P1(s) G(v + s), H2 likewise, one pass over G(w), w in [0, W)
+template <int NP1, int NH1, int NP2, int NH2>
+__device__ __forceinline__ void rcorr_g2(const float (&P1)[NP1], float (&H1)[NH1], const float (&P2)[NP2],
+                                        float (&H2)[NH2], const GaussTerm& gt)
+{
+    constexpr int W1 = NH1 + NP1 - 1, W2 = NH2 + NP2 - 1, W = W1 > W2 ? W1 : W2;
+#pragma unroll
+    for (int v = 0; v < NH1; ++v) H1[v] = 0.0f;
+#pragma unroll
+    for (int v = 0; v < NH2; ++v) H2[v] = 0.0f;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const float g = __expf(gt.expo(w));
+#pragma unroll
+        for (int v = 0; v < NH1; ++v)
+            if (w - v >= 0 && w - v < NP1) H1[v] = fmaf(P1[w - v], g, H1[v]);
+#pragma unroll
+        for (int v = 0; v < NH2; ++v)
+            if (w - v >= 0 && w - v < NP2) H2[v] = fmaf(P2[w - v], g, H2[v]);
+    }
+}
+
+template <int NP, int NH>
+__device__ __forceinline__ void rcorr_g(const float (&P)[NP], float (&H)[NH], const GaussTerm& gt)
+{
+#pragma unroll
+    for (int v = 0; v < NH; ++v) H[v] = 0.0f;
+#pragma unroll
+    for (int w = 0; w < NH + NP - 1; ++w) {
+        const float g = __expf(gt.expo(w));
+#pragma unroll
+        for (int v = 0; v < NH; ++v)
+            if (w - v >= 0 && w - v < NP) H[v] = fmaf(P[w - v], g, H[v]);
+    }
+}
+
+// Log-space recomputation of user k's message (rare: taken when the linear pass
+// of that user underflows).  mu: the linear incoming messages (> 0 or 0).
+template <int K, int Q>
+__device__ __noinline__ void chan_user_log(const float (&mu)[K][Q], int k, const GaussTerm& gt, float (&out)[Q])
+{
+    constexpr int D = Q - 1, S = (K - 1) * D + 1;
+    float F[S], Fn[S];
+#pragma unroll 1
+    for (int s = 0; s < S; ++s) F[s] = kNegInf;
+    F[0] = 0.0f;
+    int len = 1;
+#pragma unroll 1
+    for (int j = 0; j < K; ++j) {
+        if (j == k) continue;
+#pragma unroll 1
+        for (int s = 0; s < len + D; ++s) {
+            float acc = kNegInf;
+#pragma unroll 1
+            for (int b = 0; b <= D; ++b) {
+                if (s - b < 0 || s - b >= len) continue;
+                const float t = F[s - b] + __logf(mu[j][b]);
+                const float hi = fmaxf(acc, t), lo = fminf(acc, t);
+                acc = (lo == kNegInf) ? hi : hi + log1pf(__expf(lo - hi));
+            }
+            Fn[s] = acc;
+        }
+        len += D;
+#pragma unroll 1
+        for (int s = 0; s < len; ++s) F[s] = Fn[s];
+    }
+    float mx = kNegInf;
+#pragma unroll 1
+    for (int a = 0; a < Q; ++a) {
+        float acc = kNegInf;
+#pragma unroll 1
+        for (int s = 0; s < len; ++s) {
+            const float t = F[s] + gt.expo(s + a);
+            const float hi = fmaxf(acc, t), lo = fminf(acc, t);
+            acc = (lo == kNegInf) ? hi : hi + log1pf(__expf(lo - hi));
+        }
+        out[a] = acc;
+        mx = fmaxf(mx, acc);
+    }
+#pragma unroll 1
+    for (int a = 0; a < Q; ++a) out[a] = fmaxf(__expf(out[a] - mx), kRelFloor);
+}
+
+// Normalise a linear channel output to max 1 and floor it; rerun in log space
+// if it underflowed.
+template <int K, int Q>
+__device__ __forceinline__ void chan_finish(const float (&mu)[K][Q], int k, const GaussTerm& gt, float (&o)[Q],
+                                            unsigned long long* fallbacks)
+{
+    const float mx = vmax(o);
+    if (!(mx >= kFallbackMax)) {
+        if (fallbacks) atomicAdd(fallbacks, 1ull);
+        chan_user_log<K, Q>(mu, k, gt, o);
+        return;
+    }
+    const float inv = 1.0f / mx;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) o[a] = fmaxf(o[a] * inv, kRelFloor);
+}
+
+// Extrinsic messages of one channel use; calls emit(k, out_k) per user as soon
+// as its message is final (max 1, floored).
+template <int K, int Q, class Emit>
+__device__ __forceinline__ void chan_reg(const float (&mu)[K][Q], const GaussTerm& gt, unsigned long long* fb,
+                                         Emit emit)
+{
+    constexpr int D = Q - 1;
+    if constexpr (K == 1) {
+        float o[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) o[a] = __expf(gt.expo(a));
+        chan_finish<K, Q>(mu, 0, gt, o, fb);
+        emit(0, o);
+    } else if constexpr (K == 2) {
+        float o0[Q], o1[Q];
+        rcorr_g2<Q, Q, Q, Q>(mu[1], o0, mu[0], o1, gt);
+        chan_finish<K, Q>(mu, 0, gt, o0, fb);
+        emit(0, o0);
+        chan_finish<K, Q>(mu, 1, gt, o1, fb);
+        emit(1, o1);
+    } else if constexpr (K == 3) {
+        float F2[2 * D + 1];
+        rconv(mu[0], mu[1], F2);
+        float o2[Q], B2[2 * D + 1];
+        rcorr_g2<2 * D + 1, Q, Q, 2 * D + 1>(F2, o2, mu[2], B2, gt);
+        chan_finish<K, Q>(mu, 2, gt, o2, fb);
+        emit(2, o2);
+        float o[Q];
+        rcorr(mu[0], B2, o);
+        chan_finish<K, Q>(mu, 1, gt, o, fb);
+        emit(1, o);
+        rcorr(mu[1], B2, o);
+        chan_finish<K, Q>(mu, 0, gt, o, fb);
+        emit(0, o);
+    } else {
+        static_assert(K == 4, "thread-shape channel node is built for K <= 4");
+        float o[Q];
+        {
+            float P23[2 * D + 1], H23[2 * D + 1];
+            rconv(mu[2], mu[3], P23);
+            rcorr_g<2 * D + 1, 2 * D + 1>(P23, H23, gt);
+            rcorr(mu[1], H23, o);
+            chan_finish<K, Q>(mu, 0, gt, o, fb);
+            emit(0, o);
+            rcorr(mu[0], H23, o);
+            chan_finish<K, Q>(mu, 1, gt, o, fb);
+            emit(1, o);
+        }
+        {
+            float P01[2 * D + 1], H01[2 * D + 1];
+            rconv(mu[0], mu[1], P01);
+            rcorr_g<2 * D + 1, 2 * D + 1>(P01, H01, gt);
+            rcorr(mu[3], H01, o);
+            chan_finish<K, Q>(mu, 2, gt, o, fb);
+            emit(2, o);
+            rcorr(mu[2], H01, o);
+            chan_finish<K, Q>(mu, 3, gt, o, fb);
+            emit(3, o);
+        }
+    }
+}
+
+// One channel use u of one frame, thread shape (variable degree 2).  msg_f:
+// the frame's message blocks (user k at msg_f + k*ustride); ch2v_f: the frame's
+// channel messages.  Reads the c2v of the K variables on this use, writes their
+// channel messages and replaces each of their two c2v by the v2c message of the
+// same edge (eq. app_ldpc_v2c with the channel message as the local belief:
+// v2c_0 = ch2v * c2v_1, v2c_1 = ch2v * c2v_0, each rescaled to max 1).
+template <int K, int Q>
+__device__ __forceinline__ void chan_thread(const Graph& g, float* msg_f, size_t ustride, int cbs, float* ch2v_f,
+                                            float y, int u)
+{
+    float mu[K][Q];
+    int var[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        var[k] = g.use_pos[k * g.n + u];
+        const float* blk = msg_f + k * ustride;
+        float a0[Q], a1[Q];
+        vload<Q>(edge_ptr(blk, g.var_edge[2 * var[k]], cbs, Q), a0);
+        vload<Q>(edge_ptr(blk, g.var_edge[2 * var[k] + 1], cbs, Q), a1);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) a0[a] *= a1[a];
+        const float inv = 1.0f / vmax(a0);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) mu[k][a] = a0[a] * inv;
+    }
+    const GaussTerm gt = gauss_term(y, K, Q, g.inv_sigma2);
+    chan_reg<K, Q>(mu, gt, g.log_fallbacks, [&](int k, const float (&o)[Q]) {
+        const int i = var[k];
+        float* blk = msg_f + k * ustride;
+        vstore<Q>(ch2v_f + ((size_t)k * g.n + i) * Q, o);
+        float* p0 = edge_ptr(blk, g.var_edge[2 * i], cbs, Q);
+        float* p1 = edge_ptr(blk, g.var_edge[2 * i + 1], cbs, Q);
+        float c0[Q], c1[Q];
+        vload<Q>(p0, c0);
+        vload<Q>(p1, c1);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const float t = c0[a];
+            c0[a] = o[a] * c1[a];
+            c1[a] = o[a] * t;
+        }
+        const float i0 = 1.0f / vmax(c0), i1 = 1.0f / vmax(c1);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            c0[a] *= i0;
+            c1[a] *= i1;
+        }
+        vstore<Q>(p0, c0);
+        vstore<Q>(p1, c1);
+    });
+}
+
+// -- team shape: any K <= 16, q <= 64 (linear trellis, log-space on underflow)
+
 struct LinSR {
     static constexpr bool kLog = false;
     __device__ static __forceinline__ float zero() { return 0.0f; }
     __device__ static __forceinline__ float mac(float acc, float a, float b) { return fmaf(a, b, acc); }
-    __device__ static __forceinline__ float from_log(float l) { return __expf(l); }
     __device__ static __forceinline__ float rescale(float x, float mx) { return mx > 0.0f ? x * (1.0f / mx) : x; }
-    __device__ static __forceinline__ float to_log(float x, float mx) { return __logf(x) - __logf(mx); }
 };
 
 struct LogSR {
@@ -100,9 +428,7 @@ struct LogSR {
         const float hi = fmaxf(acc, t), lo = fminf(acc, t);
         return (lo == kNegInf) ? hi : hi + log1pf(__expf(lo - hi));
     }
-    __device__ static __forceinline__ float from_log(float l) { return l; }
     __device__ static __forceinline__ float rescale(float x, float mx) { return x - mx; }
-    __device__ static __forceinline__ float to_log(float x, float mx) { return x - mx; }
 };
 
 // Offset of the prefix array F_k (k >= 2) inside the prefix buffer; F_1 is mu_0.
@@ -118,23 +444,14 @@ __host__ __device__ __forceinline__ int chan_scratch_floats(int K, int Q)
     return 2 * K * Q + prefix_offset(K, D) + 2 * (S + 1);
 }
 
-// Extrinsic channel messages of channel use u of one frame.
-//
-// With a_k the symbol of user k and s = sum_k a_k, the likelihood of y_u is
-// G(s) = exp(-(y_u - (2s - K(q-1)))^2 / (2 sigma2)).  The message to user k is
-//   ch2v_k(a) ~ sum_s F_k(s) B_{k+1}(s + a),
-// with prefixes F_0 = delta_0, F_{j+1} = F_j (*) mu_j (integer convolution) and
-// scored suffixes B_K = G, B_j(v) = sum_b mu_j(b) B_{j+1}(v + b).  Nothing is
-// divided out.  Every prefix and suffix is rescaled to a maximum of 1.  The
-// exponent uses the nearest symbol sum s*: with r = y - (2s* - K(q-1)) and
-// d = s* - s, -(y - L_s)^2/(2 sigma2) + (y - L_s*)^2/(2 sigma2) = -2 d (r + d)/sigma2.
-//
-// msg_f: the frame's message block [K][E][Q] (c2v).  res [K*Q] receives the
-// max-normalised, clipped log messages.  Returns true (team-uniform) if the
-// linear pass lost a message to underflow; the caller then reruns in LogSR.
+// Team-shape channel messages of use u: prefixes F_0 = delta_0, F_{j+1} = F_j (*) mu_j,
+// scored suffixes B_K = G, B_j(v) = sum_b mu_j(b) B_{j+1}(v + b), messages
+// ch2v_k(a) ~ sum_s F_k(s) B_{k+1}(s + a); every prefix and suffix rescaled to max 1.
+// res [K*Q] receives the final messages (max 1, floored).  Returns true
+// (team-uniform) if the linear pass underflowed; the caller reruns in LogSR.
 template <int Q, class SR>
-__device__ bool chan_trellis(const Graph& g, const float* msg_f, float y, int u, float* sc,
-                             float* res, TeamLane L)
+__device__ bool chan_trellis(const Graph& g, const float* msg_f, size_t ustride, int cbs, float y, int u,
+                             float* sc, float* res, TeamLane L)
 {
     constexpr int T = Shape<Q>::T, V = Shape<Q>::V, D = Q - 1;
     const int K = g.K, S = K * D;
@@ -144,41 +461,31 @@ __device__ bool chan_trellis(const Graph& g, const float* msg_f, float y, int u,
     float* Bn = B + S + 1;
     bool bad = false;
 
-    // messages of the K variables into this channel node: product of all c2v
     for (int k = 0; k < K; ++k) {
         const int i = g.use_pos[k * g.n + u];
-        const float* mk = msg_f + (size_t)k * g.E * Q;
+        const float* blk = msg_f + k * ustride;
         float l[V];
 #pragma unroll
-        for (int v = 0; v < V; ++v) l[v] = 0.0f;
+        for (int v = 0; v < V; ++v) l[v] = SR::kLog ? 0.0f : 1.0f;
         for (int d = 0; d < g.dv; ++d) {
-            const float* m = mk + (size_t)g.var_edge[i * g.dv + d] * Q;
+            const float* m = edge_ptr(blk, g.var_edge[i * g.dv + d], cbs, Q);
 #pragma unroll
-            for (int v = 0; v < V; ++v) l[v] += m[v * T + L.tl];
+            for (int v = 0; v < V; ++v) {
+                const float x = m[v * T + L.tl];
+                l[v] = SR::kLog ? l[v] + __logf(x) : l[v] * x;
+            }
         }
         float mx = l[0];
 #pragma unroll
         for (int v = 1; v < V; ++v) mx = fmaxf(mx, l[v]);
         mx = team_max<T>(mx, L.mask);
 #pragma unroll
-        for (int v = 0; v < V; ++v) mu[k * Q + v * T + L.tl] = SR::from_log(l[v] - mx);
+        for (int v = 0; v < V; ++v) mu[k * Q + v * T + L.tl] = SR::rescale(l[v], mx);
     }
 
-    // likelihood over the symbol sum
-    {
-        const int KD = K * D;
-        float sf = rintf((y + (float)KD) * 0.5f);
-        sf = fminf(fmaxf(sf, 0.0f), (float)KD);
-        const int ss = (int)sf;
-        const float r = y - (float)(2 * ss - KD);
-        for (int s = L.tl; s <= S; s += T) {
-            const float dl = (float)(ss - s);
-            const float e = -2.0f * dl * (r + dl) * g.inv_sigma2;
-            B[s] = SR::kLog ? e : __expf(e);
-        }
-    }
+    const GaussTerm gt = gauss_term(y, K, Q, g.inv_sigma2);
+    for (int s = L.tl; s <= S; s += T) B[s] = SR::kLog ? gt.expo(s) : __expf(gt.expo(s));
 
-    // prefixes F_2 .. F_{K-1}
     for (int j = 1; j + 1 < K; ++j) {
         __syncwarp(L.mask);
         const float* Fj = (j == 1) ? mu : Fb + prefix_offset(j, D);
@@ -197,7 +504,6 @@ __device__ bool chan_trellis(const Graph& g, const float* msg_f, float y, int u,
         for (int s = L.tl; s < len; s += T) Fn[s] = SR::rescale(Fn[s], mx);
     }
 
-    // scored suffixes and the extrinsic outputs, last user first
     for (int k = K - 1; k >= 0; --k) {
         __syncwarp(L.mask);
         const float* Fk = (k == 1) ? mu : Fb + prefix_offset(k, D);
@@ -219,7 +525,10 @@ __device__ bool chan_trellis(const Graph& g, const float* msg_f, float y, int u,
         const float mx = team_max<T>(lmx, L.mask);
         if (!SR::kLog && !(mx >= kFallbackMax)) bad = true;
 #pragma unroll
-        for (int v = 0; v < V; ++v) res[k * Q + v * T + L.tl] = fmaxf(SR::to_log(o[v], mx), kLogFloor);
+        for (int v = 0; v < V; ++v) {
+            const float r = SR::kLog ? __expf(o[v] - mx) : o[v] * (1.0f / mx);
+            res[k * Q + v * T + L.tl] = fmaxf(r, kRelFloor);
+        }
         if (k > 0) {
             const int len = k * D + 1;
             float lm2 = kNegInf;
@@ -242,18 +551,16 @@ __device__ bool chan_trellis(const Graph& g, const float* msg_f, float y, int u,
     return bad;
 }
 
-// Store the channel messages of use u and turn the c2v messages of the K
-// variables on this use into v2c messages in place (eq. app_ldpc_v2c with the
-// channel message as the local belief): v2c_e = ch2v + sum of the other edges'
-// c2v, max-normalised.  Only this team touches these edges in this step.
+// Team shape: store the channel messages res of use u and turn the c2v of the
+// K variables on this use into v2c in place.
 template <int Q>
-__device__ void chan_write(const Graph& g, float* msg_f, float* ch2v_f, const float* res, int u,
-                           TeamLane L)
+__device__ void chan_write_team(const Graph& g, float* msg_f, size_t ustride, int cbs, float* ch2v_f,
+                                const float* res, int u, TeamLane L)
 {
     constexpr int T = Shape<Q>::T, V = Shape<Q>::V;
     for (int k = 0; k < g.K; ++k) {
         const int i = g.use_pos[k * g.n + u];
-        float* mk = msg_f + (size_t)k * g.E * Q;
+        float* blk = msg_f + k * ustride;
         float ch[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
@@ -261,17 +568,15 @@ __device__ void chan_write(const Graph& g, float* msg_f, float* ch2v_f, const fl
             ch2v_f[((size_t)k * g.n + i) * Q + v * T + L.tl] = ch[v];
         }
         float cv[kMaxDv][V];
-        int eidx[kMaxDv];
 #pragma unroll
-        for (int d = 0; d < kMaxDv; ++d) {
+        for (int d = 0; d < kMaxDv; ++d)
             if (d < g.dv) {
-                eidx[d] = g.var_edge[i * g.dv + d];
+                const float* m = edge_ptr(blk, g.var_edge[i * g.dv + d], cbs, Q);
 #pragma unroll
-                for (int v = 0; v < V; ++v) cv[d][v] = mk[(size_t)eidx[d] * Q + v * T + L.tl];
+                for (int v = 0; v < V; ++v) cv[d][v] = m[v * T + L.tl];
             }
-        }
 #pragma unroll
-        for (int d = 0; d < kMaxDv; ++d) {
+        for (int d = 0; d < kMaxDv; ++d)
             if (d < g.dv) {
                 float l[V];
                 float lmx = kNegInf;
@@ -280,26 +585,80 @@ __device__ void chan_write(const Graph& g, float* msg_f, float* ch2v_f, const fl
                     float s = ch[v];
 #pragma unroll
                     for (int d2 = 0; d2 < kMaxDv; ++d2)
-                        if (d2 < g.dv && d2 != d) s += cv[d2][v];
+                        if (d2 < g.dv && d2 != d) s *= cv[d2][v];
                     l[v] = s;
                     lmx = fmaxf(lmx, s);
                 }
-                const float mx = team_max<T>(lmx, L.mask);
+                const float inv = 1.0f / team_max<T>(lmx, L.mask);
+                float* m = edge_ptr(blk, g.var_edge[i * g.dv + d], cbs, Q);
 #pragma unroll
-                for (int v = 0; v < V; ++v) mk[(size_t)eidx[d] * Q + v * T + L.tl] = l[v] - mx;
+                for (int v = 0; v < V; ++v) m[v * T + L.tl] = l[v] * inv;
             }
-        }
     }
 }
 
 // ---------------------------------------------------------------------------
-// Check node (FFT-QSPA, FP32 butterflies)
+// Check node (FFT-QSPA, FP32 Walsh-Hadamard butterflies)
 // ---------------------------------------------------------------------------
+//
+// For check j of one user, in place (v2c in, c2v out), edges d = 0..3 with
+// coefficient h_d: the edge carries x = h_d a, so p~_d(x) = v2c_d(h_d^{-1} x);
+// P_d = WHT(p~_d) with P(w) = sum_x p(x) (-1)^{popcount(x & w)}; Q_d = prod of the
+// other three P (prefix/suffix, no division); r_d = WHT(Q_d) (the 1/q factor
+// cancels in the normalisation); c2v_d(a) = max(r_d(h_d a), kRelFloor max r_d) / max r_d.
 
-// In-team Walsh-Hadamard transform in natural (Sylvester) order over the index
-// x = v*T + tl: P(w) = sum_x p(x) (-1)^{popcount(x & w)}.
 template <int Q>
-__device__ __forceinline__ void wht(float (&p)[Shape<Q>::V], TeamLane L)
+__device__ __forceinline__ void wht_reg(float (&p)[Q])
+{
+#pragma unroll
+    for (int s = 1; s < Q; s <<= 1)
+#pragma unroll
+        for (int x = 0; x < Q; ++x)
+            if (!(x & s)) {
+                const float a = p[x], b = p[x | s];
+                p[x] = a + b;
+                p[x | s] = a - b;
+            }
+}
+
+// Thread shape (q <= 16).  blk: check j's four edge vectors (blk + d*Q).
+template <int Q>
+__device__ __forceinline__ void check_thread(float* blk, const uint8_t* coef, const uint8_t* gdiv)
+{
+    float P[kDC][Q];
+    int h[kDC];
+#pragma unroll
+    for (int d = 0; d < kDC; ++d) {
+        h[d] = coef[d];
+        const uint8_t* dv = gdiv + h[d] * Q;
+#pragma unroll
+        for (int x = 0; x < Q; ++x) P[d][x] = blk[d * Q + dv[x]];
+    }
+#pragma unroll
+    for (int d = 0; d < kDC; ++d) wht_reg<Q>(P[d]);
+    float R[kDC][Q];
+#pragma unroll
+    for (int x = 0; x < Q; ++x) {
+        const float l01 = P[0][x] * P[1][x], r23 = P[2][x] * P[3][x];
+        R[0][x] = P[1][x] * r23;
+        R[1][x] = P[0][x] * r23;
+        R[2][x] = l01 * P[3][x];
+        R[3][x] = l01 * P[2][x];
+    }
+#pragma unroll
+    for (int d = 0; d < kDC; ++d) {
+        wht_reg<Q>(R[d]);
+        const float mx = vmax(R[d]);
+        const float fl = kRelFloor * mx, inv = 1.0f / mx;
+        const uint8_t* dv = gdiv + h[d] * Q;
+#pragma unroll
+        for (int x = 0; x < Q; ++x) blk[d * Q + dv[x]] = fmaxf(R[d][x], fl) * inv;
+    }
+}
+
+// In-team Walsh-Hadamard transform over the index x = v*T + tl.
+template <int Q>
+__device__ __forceinline__ void wht_team(float (&p)[Shape<Q>::V], TeamLane L)
 {
     constexpr int T = Shape<Q>::T, V = Shape<Q>::V;
 #pragma unroll
@@ -338,69 +697,44 @@ __device__ __forceinline__ float team_gather(const float (&r)[Shape<Q>::V], int 
     return out;
 }
 
-// Check-node update of check j of one user (msg_fk: that user's [E][Q] block),
-// in place: v2c of the DC edges in, c2v out.
-//   x_e = h_e a_e carries the edge; p~_e(x) = v2c_e(h_e^{-1} x);
-//   P_e = WHT(p~_e); Q_e = prod_{e' != e} P_e' (prefix/suffix, no division);
-//   r_e = WHT(Q_e) (the 1/q factor cancels in the normalisation);
-//   c2v_e(a) = log max(r_e(h_e a), kRelFloor * max r_e) - log max r_e.
-template <int Q, int DC>
-__device__ void check_unit_fp32(const Graph& g, float* msg_fk, int j, const uint8_t* gmul,
-                                const uint8_t* gdiv, TeamLane L)
+// Team shape (any q).  blk: check j's four edge vectors.
+template <int Q>
+__device__ void check_team(float* blk, const uint8_t* coef, const uint8_t* gmul, const uint8_t* gdiv, TeamLane L)
 {
     constexpr int T = Shape<Q>::T, V = Shape<Q>::V;
-    float P[DC][V];
-    int h[DC];
+    float P[kDC][V];
+    int h[kDC];
 #pragma unroll
-    for (int d = 0; d < DC; ++d) {
-        const int e = j * DC + d;
-        h[d] = g.chk_coef[e];
-        const float* m = msg_fk + (size_t)e * Q;
+    for (int d = 0; d < kDC; ++d) {
+        h[d] = coef[d];
 #pragma unroll
-        for (int v = 0; v < V; ++v) P[d][v] = __expf(m[gdiv[h[d] * Q + v * T + L.tl]]);
+        for (int v = 0; v < V; ++v) P[d][v] = blk[d * Q + gdiv[h[d] * Q + v * T + L.tl]];
     }
 #pragma unroll
-    for (int d = 0; d < DC; ++d) wht<Q>(P[d], L);
-
-    float R[DC][V];
-    {
-        float pre[V];
+    for (int d = 0; d < kDC; ++d) wht_team<Q>(P[d], L);
+    float R[kDC][V];
 #pragma unroll
-        for (int v = 0; v < V; ++v) pre[v] = 1.0f;
-#pragma unroll
-        for (int d = 0; d < DC; ++d) {
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                R[d][v] = pre[v];
-                pre[v] *= P[d][v];
-            }
-        }
-#pragma unroll
-        for (int v = 0; v < V; ++v) pre[v] = 1.0f;
-#pragma unroll
-        for (int d = DC - 1; d >= 0; --d) {
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                R[d][v] *= pre[v];
-                pre[v] *= P[d][v];
-            }
-        }
+    for (int v = 0; v < V; ++v) {
+        const float l01 = P[0][v] * P[1][v], r23 = P[2][v] * P[3][v];
+        R[0][v] = P[1][v] * r23;
+        R[1][v] = P[0][v] * r23;
+        R[2][v] = l01 * P[3][v];
+        R[3][v] = l01 * P[2][v];
     }
     __syncwarp(L.mask);
 #pragma unroll
-    for (int d = 0; d < DC; ++d) {
-        wht<Q>(R[d], L);
+    for (int d = 0; d < kDC; ++d) {
+        wht_team<Q>(R[d], L);
         float lmx = R[d][0];
 #pragma unroll
         for (int v = 1; v < V; ++v) lmx = fmaxf(lmx, R[d][v]);
         const float mx = team_max<T>(lmx, L.mask);
-        const float lgmx = __logf(mx);
-        float* m = msg_fk + (size_t)(j * DC + d) * Q;
+        const float fl = kRelFloor * mx, inv = 1.0f / mx;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const int a = v * T + L.tl;
             const float r = team_gather<Q>(R[d], gmul[h[d] * Q + a], L);
-            m[a] = __logf(fmaxf(r, kRelFloor * mx)) - lgmx;
+            blk[d * Q + a] = fmaxf(r, fl) * inv;
         }
     }
 }
@@ -409,20 +743,50 @@ __device__ void check_unit_fp32(const Graph& g, float* msg_fk, int j, const uint
 // Variable node, decision, syndrome
 // ---------------------------------------------------------------------------
 
-// Marginal eq. (app_ldpc_marginal) of variable i of one user and its hard
-// decision (ties -> lowest symbol).  post_fk may be null.
+// Marginal eq. (app_ldpc_marginal) of variable i of one user, its hard decision
+// (ties -> lowest symbol) and optionally the max-normalised log-posterior.
 template <int Q>
-__device__ void var_unit(const Graph& g, const float* ch2v_fk, const float* msg_fk, int i,
-                         float* post_fk, uint8_t* hat_fk, TeamLane L)
+__device__ __forceinline__ void var_thread(const Graph& g, const float* ch2v_fk, const float* blk, int cbs, int i,
+                                           float* logpost_fk, uint8_t* hat_fk)
+{
+    float b[Q];
+    vload<Q>(ch2v_fk + (size_t)i * Q, b);
+    for (int d = 0; d < g.dv; ++d) {
+        float t[Q];
+        vload<Q>(edge_ptr(blk, g.var_edge[i * g.dv + d], cbs, Q), t);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) b[a] *= t[a];
+    }
+    float bv = b[0];
+    int bi = 0;
+#pragma unroll
+    for (int a = 1; a < Q; ++a)
+        if (b[a] > bv) {
+            bv = b[a];
+            bi = a;
+        }
+    hat_fk[i] = (uint8_t)bi;
+    if (logpost_fk) {
+        const float l = __logf(bv);
+        float o[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) o[a] = __logf(b[a]) - l;
+        vstore<Q>(logpost_fk + (size_t)i * Q, o);
+    }
+}
+
+template <int Q>
+__device__ void var_team(const Graph& g, const float* ch2v_fk, const float* blk, int cbs, int i, float* logpost_fk,
+                         uint8_t* hat_fk, TeamLane L)
 {
     constexpr int T = Shape<Q>::T, V = Shape<Q>::V;
     float b[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) b[v] = ch2v_fk[(size_t)i * Q + v * T + L.tl];
     for (int d = 0; d < g.dv; ++d) {
-        const float* m = msg_fk + (size_t)g.var_edge[i * g.dv + d] * Q;
+        const float* m = edge_ptr(blk, g.var_edge[i * g.dv + d], cbs, Q);
 #pragma unroll
-        for (int v = 0; v < V; ++v) b[v] += m[v * T + L.tl];
+        for (int v = 0; v < V; ++v) b[v] *= m[v * T + L.tl];
     }
     float bv = b[0];
     int bi = L.tl;
@@ -442,15 +806,15 @@ __device__ void var_unit(const Graph& g, const float* ch2v_fk, const float* msg_
         }
     }
     if (L.tl == 0) hat_fk[i] = (uint8_t)bi;
-    if (post_fk) {
+    if (logpost_fk) {
+        const float l = __logf(bv);
 #pragma unroll
-        for (int v = 0; v < V; ++v) post_fk[(size_t)i * Q + v * T + L.tl] = b[v] - bv;
+        for (int v = 0; v < V; ++v) logpost_fk[(size_t)i * Q + v * T + L.tl] = __logf(b[v]) - l;
     }
 }
 
 // eq. (app_ldpc_check_eq) for check j of one user's decisions.
-__device__ __forceinline__ bool check_satisfied(const Graph& g, const uint8_t* hat_fk, int j,
-                                                const uint8_t* gmul)
+__device__ __forceinline__ bool check_satisfied(const Graph& g, const uint8_t* hat_fk, int j, const uint8_t* gmul)
 {
     int s = 0;
     for (int d = 0; d < g.dc; ++d) {

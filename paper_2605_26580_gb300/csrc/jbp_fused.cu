@@ -2,14 +2,19 @@
 // group of frames with the whole message state in shared memory.
 //
 // A CTA owns G frames at a time.  Shared memory (per CTA):
-//   msg  [G][K][E][q] f32   c2v / v2c on check-major edges (updated in place)
-//   ch2v [G][K][n][q] f32   channel messages
-//   y    [G][n]       f32
-//   scratch [teams][chan_scratch_floats] f32   channel trellis per team
+//   msg  [G][K][P][cbs] f32   c2v / v2c (max 1) per check block, cbs = 4q + 4
+//                             (the 16-byte pad spreads thread-shape accesses
+//                             over the banks); updated in place
+//   ch2v [G][K][n][q]   f32   channel messages
+//   y    [G][n]         f32
+//   scratch [teams][chan_scratch_floats] f32   (team-shape channel only)
 //   hat  [G][K][n] u8, unsat [G][K] u8, active [G] u8, gf mul/div [q*q] u8
 // Per iteration: (A) channel nodes + in-place v2c, (B) check nodes,
 // (C) decisions, (D) syndromes, (E) per-frame stop; __syncthreads between.
-// Global memory sees only y in and hat/iters/ok (and the optional posterior) out.
+// Global memory sees only y in and hat/iters/ok (and the optional log-posterior) out.
+//
+// Thread shape (q <= 16; channel also K <= 4 and variable degree 2): one thread
+// per unit, vectors in registers.  Team shape otherwise.
 #include <algorithm>
 
 #include "jbp_internal.h"
@@ -17,7 +22,7 @@
 namespace jbp {
 namespace {
 
-constexpr int kFusedMaxThreads = 512;
+constexpr int kFusedMaxThreads = 256;
 constexpr size_t kStaticSmemMargin = 256;   // static __shared__ words of k_fused
 
 struct FusedLayout {
@@ -26,11 +31,13 @@ struct FusedLayout {
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
+__host__ __device__ inline int fused_cbs(int Q) { return 4 * Q + 4; }
+
 __host__ __device__ inline FusedLayout fused_layout(const Graph& g, int G, int teams, int scf)
 {
     FusedLayout L;
     size_t o = 0;
-    L.msg = o;     o = align16(o + sizeof(float) * (size_t)G * g.K * g.E * g.Q);
+    L.msg = o;     o = align16(o + sizeof(float) * (size_t)G * g.K * g.P * fused_cbs(g.Q));
     L.ch2v = o;    o = align16(o + sizeof(float) * (size_t)G * g.K * g.n * g.Q);
     L.y = o;       o = align16(o + sizeof(float) * (size_t)G * g.n);
     L.scratch = o; o = align16(o + sizeof(float) * (size_t)teams * scf);
@@ -43,15 +50,18 @@ __host__ __device__ inline FusedLayout fused_layout(const Graph& g, int G, int t
     return L;
 }
 
-template <int Q, int DC>
+// KC > 0: thread-shape channel with KC users; KC == 0: team-shape channel.
+template <int Q, int KC>
 __global__ void __launch_bounds__(kFusedMaxThreads) k_fused(Graph g, int F, int G, const float* __restrict__ y,
                                                             int T_it, int early_stop, uint8_t* hat,
-                                                            int32_t* iters, uint8_t* ok, float* post, int scf)
+                                                            int32_t* iters, uint8_t* ok, float* logpost, int scf)
 {
     constexpr int T = Shape<Q>::T;
+    constexpr bool kThreadCheck = Q <= 16;
     extern __shared__ __align__(16) unsigned char sm[];
     const int teams = blockDim.x / T, team = threadIdx.x / T;
-    const FusedLayout lay = fused_layout(g, G, teams, scf);
+    const FusedLayout lay = fused_layout(g, G, KC > 0 ? 0 : teams, scf);
+    const int cbs = fused_cbs(Q);
     float* s_msg = reinterpret_cast<float*>(sm + lay.msg);
     float* s_ch2v = reinterpret_cast<float*>(sm + lay.ch2v);
     float* s_y = reinterpret_cast<float*>(sm + lay.y);
@@ -65,8 +75,8 @@ __global__ void __launch_bounds__(kFusedMaxThreads) k_fused(Graph g, int F, int 
     __shared__ int s_nactive;
 
     const TeamLane L = team_lane<T>();
-    const int K = g.K, n = g.n, E = g.E, P = g.P;
-    const size_t fs = (size_t)K * E * Q, vs = (size_t)K * n * Q;
+    const int K = g.K, n = g.n, P = g.P;
+    const size_t us = (size_t)P * cbs, fs = (size_t)K * us, vs = (size_t)K * n * Q;
 
     for (int i = threadIdx.x; i < Q * Q; i += blockDim.x) {
         s_mul[i] = g.gf_mul[i];
@@ -76,8 +86,8 @@ __global__ void __launch_bounds__(kFusedMaxThreads) k_fused(Graph g, int F, int 
     const int groups = (F + G - 1) / G;
     for (int grp = blockIdx.x; grp < groups; grp += gridDim.x) {
         const int f0 = grp * G, gc = min(G, F - f0);
-        // uniform c2v (log 1 = 0), y, control words
-        for (size_t i = threadIdx.x; i < (size_t)gc * fs; i += blockDim.x) s_msg[i] = 0.0f;
+        // uniform c2v messages (all ones), y, control words
+        for (size_t i = threadIdx.x; i < (size_t)gc * fs; i += blockDim.x) s_msg[i] = 1.0f;
         for (int i = threadIdx.x; i < gc * n; i += blockDim.x) s_y[i] = y[(size_t)f0 * n + i];
         for (int i = threadIdx.x; i < gc * K; i += blockDim.x) s_unsat[i] = 0;
         for (int i = threadIdx.x; i < G; i += blockDim.x) s_active[i] = i < gc ? 1 : 0;
@@ -85,30 +95,58 @@ __global__ void __launch_bounds__(kFusedMaxThreads) k_fused(Graph g, int F, int 
 
         for (int t = 1; t <= T_it; ++t) {
             // (A) channel nodes, v2c in place
-            for (int unit = team; unit < gc * n; unit += teams) {
-                const int gi = unit / n, u = unit % n;
-                if (!s_active[gi]) continue;
-                float* msg_f = s_msg + gi * fs;
-                const float yv = s_y[gi * n + u];
-                if (chan_trellis<Q, LinSR>(g, msg_f, yv, u, sc, res, L))
-                    chan_trellis<Q, LogSR>(g, msg_f, yv, u, sc, res, L);
-                chan_write<Q>(g, msg_f, s_ch2v + gi * vs, res, u, L);
+            if constexpr (KC > 0) {
+                for (int unit = threadIdx.x; unit < gc * n; unit += blockDim.x) {
+                    const int gi = unit / n, u = unit % n;
+                    if (!s_active[gi]) continue;
+                    chan_thread<KC, Q>(g, s_msg + gi * fs, us, cbs, s_ch2v + gi * vs, s_y[gi * n + u], u);
+                }
+            } else {
+                for (int unit = team; unit < gc * n; unit += teams) {
+                    const int gi = unit / n, u = unit % n;
+                    if (!s_active[gi]) continue;
+                    float* msg_f = s_msg + gi * fs;
+                    const float yv = s_y[gi * n + u];
+                    if (chan_trellis<Q, LinSR>(g, msg_f, us, cbs, yv, u, sc, res, L)) {
+                        if (g.log_fallbacks && L.tl == 0) atomicAdd(g.log_fallbacks, 1ull);
+                        chan_trellis<Q, LogSR>(g, msg_f, us, cbs, yv, u, sc, res, L);
+                    }
+                    chan_write_team<Q>(g, msg_f, us, cbs, s_ch2v + gi * vs, res, u, L);
+                }
             }
             __syncthreads();
             // (B) check nodes
-            for (int unit = team; unit < gc * K * P; unit += teams) {
-                const int gi = unit / (K * P), rem = unit % (K * P), k = rem / P, j = rem % P;
-                if (!s_active[gi]) continue;
-                check_unit_fp32<Q, DC>(g, s_msg + gi * fs + (size_t)k * E * Q, j, s_mul, s_div, L);
+            if constexpr (kThreadCheck) {
+                for (int unit = threadIdx.x; unit < gc * K * P; unit += blockDim.x) {
+                    const int gi = unit / (K * P), j = unit % P;
+                    if (!s_active[gi]) continue;
+                    check_thread<Q>(s_msg + (size_t)unit * cbs, g.chk_coef + 4 * j, s_div);
+                }
+            } else {
+                for (int unit = team; unit < gc * K * P; unit += teams) {
+                    const int gi = unit / (K * P), j = unit % P;
+                    if (!s_active[gi]) continue;
+                    check_team<Q>(s_msg + (size_t)unit * cbs, g.chk_coef + 4 * j, s_mul, s_div, L);
+                }
             }
             __syncthreads();
             // (C) posterior and decisions
-            for (int unit = team; unit < gc * K * n; unit += teams) {
-                const int gi = unit / (K * n), rem = unit % (K * n), k = rem / n, i = rem % n;
-                if (!s_active[gi]) continue;
-                const size_t fk = (size_t)gi * K + k;
-                float* pst = post ? post + ((size_t)(f0 + gi) * K + k) * n * Q : nullptr;
-                var_unit<Q>(g, s_ch2v + fk * n * Q, s_msg + fk * E * Q, i, pst, s_hat + fk * n, L);
+            if constexpr (kThreadCheck) {
+                for (int unit = threadIdx.x; unit < gc * K * n; unit += blockDim.x) {
+                    const int gi = unit / (K * n), rem = unit % (K * n), k = rem / n, i = rem % n;
+                    if (!s_active[gi]) continue;
+                    const size_t fk = (size_t)gi * K + k;
+                    float* lp = logpost ? logpost + ((size_t)(f0 + gi) * K + k) * n * Q : nullptr;
+                    var_thread<Q>(g, s_ch2v + fk * n * Q, s_msg + fk * us, cbs, i, lp, s_hat + fk * n);
+                }
+            } else {
+                for (int unit = team; unit < gc * K * n; unit += teams) {
+                    const int gi = unit / (K * n), rem = unit % (K * n), k = rem / n, i = rem % n;
+                    if (!s_active[gi]) continue;
+                    const size_t fk = (size_t)gi * K + k;
+                    float* lp = logpost ? logpost + ((size_t)(f0 + gi) * K + k) * n * Q : nullptr;
+                    var_team<Q>(g, s_ch2v + fk * n * Q, s_msg + fk * us, cbs, i, lp, s_hat + fk * n, L);
+                }
             }
             __syncthreads();
             // (D) syndromes
@@ -141,16 +179,15 @@ __global__ void __launch_bounds__(kFusedMaxThreads) k_fused(Graph g, int F, int 
     }
 }
 
-template <int Q>
-bool plan_q(const Graph& g, const DeviceInfo& di, int F, int threads_hint, int fpc_hint, FusedPlan* plan)
+template <int Q, int KC>
+bool plan_qk(const Graph& g, const DeviceInfo& di, int F, int threads_hint, int fpc_hint, FusedPlan* plan)
 {
     constexpr int T = Shape<Q>::T;
-    if (g.dc != 4 || F <= 0) return false;
     const int scf = chan_scratch_floats(g.K, Q);
     int threads = threads_hint > 0 ? threads_hint : 256;
     threads = std::max(32, std::min(kFusedMaxThreads, threads / 32 * 32));
     for (; threads >= 32; threads -= 32) {
-        const int teams = threads / T;
+        const int teams = KC > 0 ? 0 : threads / T;
         int Gmax = 0;
         for (int G = 1; G <= 4096; ++G) {
             if (fused_layout(g, G, teams, scf).total + kStaticSmemMargin > (size_t)di.smem_optin) break;
@@ -165,9 +202,9 @@ bool plan_q(const Graph& g, const DeviceInfo& di, int F, int threads_hint, int f
         plan->smem_bytes = (int)fused_layout(g, G, teams, scf).total;
         const int groups = (F + G - 1) / G;
         int occ = 0;
-        if (cudaFuncSetAttribute(k_fused<Q, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem_bytes) !=
+        if (cudaFuncSetAttribute(k_fused<Q, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem_bytes) !=
                 cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused<Q, 4>, threads, plan->smem_bytes) !=
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused<Q, KC>, threads, plan->smem_bytes) !=
                 cudaSuccess ||
             occ < 1)
             return false;
@@ -177,45 +214,65 @@ bool plan_q(const Graph& g, const DeviceInfo& di, int F, int threads_hint, int f
     return false;
 }
 
-template <int Q>
-cudaError_t fused_q(const Graph& g, const FusedPlan& p, int F, const float* y, int T_it, int early_stop,
-                    uint8_t* hat, int32_t* iters, uint8_t* ok, float* post, cudaStream_t s)
+template <int Q, int KC>
+cudaError_t fused_qk(const Graph& g, const FusedPlan& p, int F, const float* y, int T_it, int early_stop, uint8_t* hat,
+                     int32_t* iters, uint8_t* ok, float* post, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_fused<Q, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem_bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_fused<Q, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem_bytes);
     if (e != cudaSuccess) return e;
-    k_fused<Q, 4><<<p.grid, p.threads, p.smem_bytes, s>>>(g, F, p.frames_per_cta, y, T_it, early_stop, hat, iters,
-                                                           ok, post, chan_scratch_floats(g.K, Q));
+    k_fused<Q, KC><<<p.grid, p.threads, p.smem_bytes, s>>>(g, F, p.frames_per_cta, y, T_it, early_stop, hat, iters,
+                                                            ok, post, chan_scratch_floats(g.K, Q));
     return cudaGetLastError();
 }
 
+// Which k_fused<Q, KC> instance serves this graph.
+inline int fused_kc(const Graph& g) { return (g.Q <= 16 && g.dv == 2 && g.K <= 4) ? g.K : 0; }
+
 }  // namespace
+
+#define JBP_FUSED_DISPATCH(FN, ...)                                                  \
+    do {                                                                             \
+        const int kc = fused_kc(g);                                                  \
+        switch (g.Q * 8 + kc) {                                                      \
+            case 2 * 8 + 0: return FN<2, 0>(__VA_ARGS__);                            \
+            case 2 * 8 + 1: return FN<2, 1>(__VA_ARGS__);                            \
+            case 2 * 8 + 2: return FN<2, 2>(__VA_ARGS__);                            \
+            case 2 * 8 + 3: return FN<2, 3>(__VA_ARGS__);                            \
+            case 2 * 8 + 4: return FN<2, 4>(__VA_ARGS__);                            \
+            case 4 * 8 + 0: return FN<4, 0>(__VA_ARGS__);                            \
+            case 4 * 8 + 1: return FN<4, 1>(__VA_ARGS__);                            \
+            case 4 * 8 + 2: return FN<4, 2>(__VA_ARGS__);                            \
+            case 4 * 8 + 3: return FN<4, 3>(__VA_ARGS__);                            \
+            case 4 * 8 + 4: return FN<4, 4>(__VA_ARGS__);                            \
+            case 8 * 8 + 0: return FN<8, 0>(__VA_ARGS__);                            \
+            case 8 * 8 + 1: return FN<8, 1>(__VA_ARGS__);                            \
+            case 8 * 8 + 2: return FN<8, 2>(__VA_ARGS__);                            \
+            case 8 * 8 + 3: return FN<8, 3>(__VA_ARGS__);                            \
+            case 8 * 8 + 4: return FN<8, 4>(__VA_ARGS__);                            \
+            case 16 * 8 + 0: return FN<16, 0>(__VA_ARGS__);                          \
+            case 16 * 8 + 1: return FN<16, 1>(__VA_ARGS__);                          \
+            case 16 * 8 + 2: return FN<16, 2>(__VA_ARGS__);                          \
+            case 16 * 8 + 3: return FN<16, 3>(__VA_ARGS__);                          \
+            case 16 * 8 + 4: return FN<16, 4>(__VA_ARGS__);                          \
+            case 32 * 8 + 0: return FN<32, 0>(__VA_ARGS__);                          \
+            case 64 * 8 + 0: return FN<64, 0>(__VA_ARGS__);                          \
+            default: break;                                                          \
+        }                                                                            \
+    } while (0)
 
 bool fused_plan(const Graph& g, const DeviceInfo& di, int F, int threads_hint, int fpc_hint, FusedPlan* plan)
 {
-    switch (g.Q) {
-        case 2: return plan_q<2>(g, di, F, threads_hint, fpc_hint, plan);
-        case 4: return plan_q<4>(g, di, F, threads_hint, fpc_hint, plan);
-        case 8: return plan_q<8>(g, di, F, threads_hint, fpc_hint, plan);
-        case 16: return plan_q<16>(g, di, F, threads_hint, fpc_hint, plan);
-        case 32: return plan_q<32>(g, di, F, threads_hint, fpc_hint, plan);
-        case 64: return plan_q<64>(g, di, F, threads_hint, fpc_hint, plan);
-        default: return false;
-    }
+    if (g.dc != kDC || F <= 0) return false;
+    JBP_FUSED_DISPATCH(plan_qk, g, di, F, threads_hint, fpc_hint, plan);
+    return false;
 }
 
 cudaError_t launch_fused(const Graph& g, const FusedPlan& plan, int F, const float* y, int T_it, int early_stop,
                          uint8_t* hat, int32_t* iters, uint8_t* ok, float* post, cudaStream_t s)
 {
     if (F <= 0) return cudaSuccess;
-    switch (g.Q) {
-        case 2: return fused_q<2>(g, plan, F, y, T_it, early_stop, hat, iters, ok, post, s);
-        case 4: return fused_q<4>(g, plan, F, y, T_it, early_stop, hat, iters, ok, post, s);
-        case 8: return fused_q<8>(g, plan, F, y, T_it, early_stop, hat, iters, ok, post, s);
-        case 16: return fused_q<16>(g, plan, F, y, T_it, early_stop, hat, iters, ok, post, s);
-        case 32: return fused_q<32>(g, plan, F, y, T_it, early_stop, hat, iters, ok, post, s);
-        case 64: return fused_q<64>(g, plan, F, y, T_it, early_stop, hat, iters, ok, post, s);
-        default: return cudaErrorInvalidValue;
-    }
+    JBP_FUSED_DISPATCH(fused_qk, g, plan, F, y, T_it, early_stop, hat, iters, ok, post, s);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace jbp

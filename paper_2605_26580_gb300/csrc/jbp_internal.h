@@ -32,6 +32,13 @@ cudaError_t launch_var(const Graph& g, const DeviceInfo& di, int F, const float*
 cudaError_t launch_syndrome(const Graph& g, const DeviceInfo& di, int F, const uint8_t* hat,
                             uint8_t* unsat, const uint8_t* active, cudaStream_t s);
 cudaError_t launch_finalize(int F, int K, int t, int early_stop, StepCtl ctl, cudaStream_t s);
+cudaError_t launch_fill(float* p, size_t count, float value, cudaStream_t s);
+
+// Check node on the tensor cores (jbp_check_tc.cu): the Walsh-Hadamard
+// transforms as +-1 matrix products with BF16 operands split into `precision`
+// terms (JBP_PREC_BF16X2 / BF16 / BF16X3) and FP32 accumulation.
+cudaError_t launch_check_tc(const Graph& g, const DeviceInfo& di, int F, float* msg, const uint8_t* active,
+                            int precision, cudaStream_t s);
 cudaError_t launch_ok_from_unsat(int F, int K, const uint8_t* unsat, uint8_t* ok, cudaStream_t s);
 
 // Fused shared-memory form (jbp_fused.cu).

@@ -167,7 +167,7 @@ extern "C" int jbp_decode_noalloc(const jbp_code* code, int32_t K, const jbp_cha
     unsigned char* D = ds.base;
     cudaError_t e;
     if ((e = cudaMemcpyAsync(D, H, tables_end, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(D + o_msg, 0, fs * F, s)) != cudaSuccess ||
+        (e = jbp::launch_fill(reinterpret_cast<float*>(D + o_msg), fs / 4 * F, 1.0f, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(D + o_act, 1, (size_t)F, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(D + o_unsat, 0, (size_t)F * K, s)) != cudaSuccess)
         return nfail(JBP_ECUDA, cudaGetErrorString(e));
@@ -180,6 +180,7 @@ extern "C" int jbp_decode_noalloc(const jbp_code* code, int32_t K, const jbp_cha
     g.use_pos = reinterpret_cast<const int32_t*>(D + o_use);
     g.gf_mul = D + o_mul;
     g.gf_div = D + o_div;
+    g.log_fallbacks = nullptr;
     float* msg = reinterpret_cast<float*>(D + o_msg);
     float* ch2v = reinterpret_cast<float*>(D + o_ch2v);
     uint8_t* active = D + o_act;

@@ -23,7 +23,7 @@ FORM_AUTO, FORM_FUSED, FORM_STEP, FORM_PLAIN = 0, 1, 2, 3
 EXPORTS = [
     "jbp_context_create", "jbp_context_destroy", "jbp_create", "jbp_destroy", "jbp_decode",
     "jbp_submit", "jbp_poll", "jbp_serving_stats", "jbp_last_error", "jbp_step_channel",
-    "jbp_step_check", "jbp_step_var", "jbp_step_syndrome", "jbp_query", "jbp_decode_noalloc",
+    "jbp_step_check", "jbp_step_var", "jbp_step_syndrome", "jbp_query", "jbp_decode_noalloc", "jbp_stats",
 ]
 
 
@@ -81,6 +81,7 @@ def lib():
             L.jbp_step_var.argtypes = [vp, i32, vp, vp, vp, vp, vp]
             L.jbp_step_syndrome.argtypes = [vp, i32, vp, vp, vp]
             L.jbp_query.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]
+            L.jbp_stats.argtypes = [vp, C.POINTER(u64)]
             L.jbp_decode_noalloc.argtypes = [C.POINTER(Code), i32, C.POINTER(Channel), i32, i32, i32, vp, vp, vp,
                                              vp, vp]
             for name in EXPORTS:
@@ -172,6 +173,11 @@ class Decoder:
         if self.ptr:
             check(lib().jbp_destroy(self.ptr))
             self.ptr = None
+
+    def log_fallbacks(self) -> int:
+        v = C.c_uint64()
+        check(lib().jbp_stats(self.ptr, C.byref(v)))
+        return v.value
 
     # -- whole decodes --------------------------------------------------------
     def decode(self, y, form: int = FORM_AUTO, want_post: bool = False):
