@@ -177,6 +177,9 @@ struct jbp_h {
     uint8_t* d_gf_mul = nullptr;
     uint8_t* d_gf_div = nullptr;
     unsigned long long* d_fallbacks = nullptr;
+    int32_t* d_pos_of = nullptr;
+    int* d_tc_error = nullptr;
+    uint16_t* d_slot = nullptr;
     int64_t table_bytes = 0;
     Workspace ws;
     std::mutex ws_mu;
@@ -190,6 +193,9 @@ struct jbp_h {
         g.chk_var = d_chk_var; g.chk_coef = d_chk_coef; g.var_edge = d_var_edge;
         g.use_pos = d_use_pos; g.gf_mul = d_gf_mul; g.gf_div = d_gf_div;
         g.log_fallbacks = d_fallbacks;
+        g.pos_of = d_pos_of;
+        g.slot = d_slot;
+        g.tc_error = d_tc_error;
         return g;
     }
 };
@@ -452,6 +458,20 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
                 return fail(JBP_EINVAL, "perm row %d is not a permutation of 0..n-1", k);
             use_pos[(size_t)k * n + t] = i;
         }
+    // position-major tables of the fused form: pi_k(i) and, per user and edge,
+    // pi_k(var)*2 + (rank of the edge among its variable's edges)
+    std::vector<int32_t> pos_of((size_t)K * n);
+    for (int k = 0; k < K; ++k)
+        for (int i = 0; i < n; ++i) pos_of[(size_t)k * n + i] = chan->interleave ? chan->perm[(size_t)k * n + i] : i;
+    const bool want_slot = dv == 2 && n <= 32767;
+    std::vector<uint16_t> slot(want_slot ? (size_t)K * E : 0);
+    if (want_slot)
+        for (int k = 0; k < K; ++k)
+            for (int e = 0; e < E; ++e) {
+                const int i = code->chk_var[e];
+                const int rank = var_edge[(size_t)i * dv] == e ? 0 : 1;
+                slot[(size_t)k * E + e] = (uint16_t)(pos_of[(size_t)k * n + i] * 2 + rank);
+            }
     std::vector<uint8_t> gmul((size_t)q * q), gdiv((size_t)q * q);
     std::vector<int> inv(q, 0);
     for (int a = 1; a < q; ++a)
@@ -479,7 +499,10 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
         (rc = dev_alloc(ctx, &h->d_use_pos, (size_t)K * n, &h->table_bytes)) ||
         (rc = dev_alloc(ctx, &h->d_gf_mul, (size_t)q * q, &h->table_bytes)) ||
         (rc = dev_alloc(ctx, &h->d_gf_div, (size_t)q * q, &h->table_bytes)) ||
-        (rc = dev_alloc(ctx, &h->d_fallbacks, (size_t)1, &h->table_bytes))) {
+        (rc = dev_alloc(ctx, &h->d_fallbacks, (size_t)1, &h->table_bytes)) ||
+        (rc = dev_alloc(ctx, &h->d_pos_of, (size_t)K * n, &h->table_bytes)) ||
+        (rc = dev_alloc(ctx, &h->d_tc_error, (size_t)1, &h->table_bytes)) ||
+        (want_slot && (rc = dev_alloc(ctx, &h->d_slot, (size_t)K * E, &h->table_bytes)))) {
         jbp_destroy(h);
         return rc;
     }
@@ -490,7 +513,11 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
         (e = cudaMemcpy(h->d_use_pos, use_pos.data(), sizeof(int32_t) * use_pos.size(), cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(h->d_gf_mul, gmul.data(), gmul.size(), cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(h->d_gf_div, gdiv.data(), gdiv.size(), cudaMemcpyHostToDevice)) ||
-        (e = cudaMemset(h->d_fallbacks, 0, sizeof(unsigned long long)))) {
+        (e = cudaMemset(h->d_fallbacks, 0, sizeof(unsigned long long))) ||
+        (e = cudaMemset(h->d_tc_error, 0, sizeof(int))) ||
+        (e = cudaMemcpy(h->d_pos_of, pos_of.data(), sizeof(int32_t) * pos_of.size(), cudaMemcpyHostToDevice)) ||
+        (want_slot &&
+         (e = cudaMemcpy(h->d_slot, slot.data(), sizeof(uint16_t) * slot.size(), cudaMemcpyHostToDevice)))) {
         jbp_destroy(h);
         return cuda_fail(e, "jbp_create: copy tables");
     }
@@ -543,6 +570,9 @@ extern "C" int jbp_destroy(jbp_h* h)
     dev_free(ctx, h->d_gf_mul, (size_t)h->Q * h->Q);
     dev_free(ctx, h->d_gf_div, (size_t)h->Q * h->Q);
     dev_free(ctx, h->d_fallbacks, sizeof(unsigned long long));
+    dev_free(ctx, h->d_pos_of, sizeof(int32_t) * (size_t)h->K * h->n);
+    dev_free(ctx, h->d_tc_error, sizeof(int));
+    if (h->d_slot) dev_free(ctx, h->d_slot, sizeof(uint16_t) * (size_t)h->K * h->E);
     delete h;
     return JBP_OK;
 }
@@ -556,14 +586,17 @@ extern "C" int jbp_query(jbp_h* h, int32_t* E, int64_t* state_bytes_per_frame, i
     return JBP_OK;
 }
 
-extern "C" int jbp_stats(jbp_h* h, uint64_t* log_fallbacks)
+extern "C" int jbp_stats(jbp_h* h, uint64_t* log_fallbacks, int32_t* tc_timeouts)
 {
     if (!h) return fail(JBP_EINVAL, "jbp_stats: NULL handle");
     JBP_CU(cudaSetDevice(h->ctx->device), "cudaSetDevice");
     unsigned long long v = 0;
+    int err = 0;
     JBP_CU(cudaDeviceSynchronize(), "jbp_stats");
     JBP_CU(cudaMemcpy(&v, h->d_fallbacks, sizeof v, cudaMemcpyDeviceToHost), "jbp_stats: copy");
+    JBP_CU(cudaMemcpy(&err, h->d_tc_error, sizeof err, cudaMemcpyDeviceToHost), "jbp_stats: copy");
     if (log_fallbacks) *log_fallbacks = v;
+    if (tc_timeouts) *tc_timeouts = err;
     return JBP_OK;
 }
 
@@ -601,6 +634,11 @@ extern "C" int jbp_decode(jbp_h* h, jbp_batch* b)
     if (b->logpost)
         JBP_CU(cudaMemcpyAsync(b->logpost, w.post, sizeof(float) * vs * F, cudaMemcpyDeviceToHost, s), "copy post");
     JBP_CU(cudaStreamSynchronize(s), "jbp_decode");
+    if (ctx->opt.precision != JBP_PREC_FP32) {
+        int err = 0;
+        JBP_CU(cudaMemcpy(&err, h->d_tc_error, sizeof err, cudaMemcpyDeviceToHost), "jbp_decode: status");
+        if (err) return fail(JBP_ETIMEOUT, "a tensor-core completion wait expired");
+    }
     return JBP_OK;
 }
 

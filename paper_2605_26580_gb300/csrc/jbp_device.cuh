@@ -42,6 +42,9 @@ struct Graph {
     const uint8_t* gf_mul;    // [Q*Q]   gf_mul[h*Q+x] = h*x
     const uint8_t* gf_div;    // [Q*Q]   gf_div[h*Q+x] = h^{-1}*x
     unsigned long long* log_fallbacks;   // counts channel messages redone in log space (may be null)
+    const int32_t* pos_of;    // [K*n]   pos_of[k*n+i] = pi_k(i)                 (fused layout)
+    const uint16_t* slot;     // [K*E]   pi_k(var of e)*2 + (e's rank in its var) (fused layout)
+    int* tc_error;            // set to 1 if a tensor-core wait expired (may be null: FP32 only)
 };
 
 __device__ __forceinline__ float* edge_ptr(float* blk, int e, int cbs, int Q)
@@ -811,6 +814,203 @@ __device__ void var_team(const Graph& g, const float* ch2v_fk, const float* blk,
 #pragma unroll
         for (int v = 0; v < V; ++v) logpost_fk[(size_t)i * Q + v * T + L.tl] = __logf(b[v]) - l;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Position-major transposed layout (fused kernel, thread shape, dv = 2)
+// ---------------------------------------------------------------------------
+//
+// User k's variable i is stored at its channel-use position p = pi_k(i), so the
+// channel node of use p finds every user's variable at the same position.  32
+// consecutive positions are interleaved in chunks of W symbols (W = 1: chunks of
+// 4 halve the load instructions of the channel and variable phases but cost the
+// check phase's permuted gathers more address arithmetic and bank conflicts;
+// measured 5% slower on K=4, q=16):
+// symbol a of the q-vector at position p of row r lives at
+//   ((r * q/W + a/W) * 32 + p % 32) * W + a % W,
+// so a thread reads its vector as q/W aligned W-float loads and the 32 threads
+// of a warp on consecutive positions cover consecutive banks.  Rows: ch2v row =
+// k*NB + p/32; msg row = (k*NB + p/32)*2 + d for the variable's d-th edge
+// (ascending edge id).
+
+constexpr int kLanes = 32;
+
+template <int Q>
+struct PosW {
+    static constexpr int W = 1;
+};
+
+template <int Q>
+__device__ __forceinline__ int pos_vec(int row, int p)
+{
+    return row * Q * kLanes + (p & (kLanes - 1)) * PosW<Q>::W;
+}
+
+// offset of symbol a inside a position vector
+template <int Q>
+__device__ __forceinline__ int pos_sym(int a)
+{
+    constexpr int W = PosW<Q>::W;
+    return (a / W) * (kLanes * W) + (a % W);
+}
+
+template <int Q>
+__device__ __forceinline__ void sload(const float* base, float (&v)[Q])
+{
+    constexpr int W = PosW<Q>::W;
+#pragma unroll
+    for (int c = 0; c < Q / W; ++c) {
+        if constexpr (W == 4) {
+            const float4 t = *reinterpret_cast<const float4*>(base + c * kLanes * W);
+            v[4 * c] = t.x; v[4 * c + 1] = t.y; v[4 * c + 2] = t.z; v[4 * c + 3] = t.w;
+        } else if constexpr (W == 1) {
+            v[c] = base[c * kLanes];
+        } else {
+            const float2 t = *reinterpret_cast<const float2*>(base + c * kLanes * W);
+            v[2 * c] = t.x; v[2 * c + 1] = t.y;
+        }
+    }
+}
+
+template <int Q>
+__device__ __forceinline__ void sstore(float* base, const float (&v)[Q])
+{
+    constexpr int W = PosW<Q>::W;
+#pragma unroll
+    for (int c = 0; c < Q / W; ++c) {
+        if constexpr (W == 4)
+            *reinterpret_cast<float4*>(base + c * kLanes * W) = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+        else if constexpr (W == 1)
+            base[c * kLanes] = v[c];
+        else
+            *reinterpret_cast<float2*>(base + c * kLanes * W) = make_float2(v[2 * c], v[2 * c + 1]);
+    }
+}
+
+// Channel node of use p, thread shape, position-major layout.  msg_f / ch2v_f:
+// the frame's blocks; NB = ceil(n / 32).
+template <int K, int Q>
+__device__ __forceinline__ void chan_thread_pos(const Graph& g, float* msg_f, float* ch2v_f, int NB, float y, int p)
+{
+    float mu[K][Q];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int row = (k * NB + (p >> 5)) * 2;
+        float a0[Q], a1[Q];
+        sload<Q>(msg_f + pos_vec<Q>(row, p), a0);
+        sload<Q>(msg_f + pos_vec<Q>(row + 1, p), a1);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) a0[a] *= a1[a];
+        const float inv = 1.0f / vmax(a0);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) mu[k][a] = a0[a] * inv;
+    }
+    const GaussTerm gt = gauss_term(y, K, Q, g.inv_sigma2);
+    chan_reg<K, Q>(mu, gt, g.log_fallbacks, [&](int k, const float (&o)[Q]) {
+        const int row = (k * NB + (p >> 5)) * 2;
+        sstore<Q>(ch2v_f + pos_vec<Q>(k * NB + (p >> 5), p), o);
+        float* p0 = msg_f + pos_vec<Q>(row, p);
+        float* p1 = msg_f + pos_vec<Q>(row + 1, p);
+        float c0[Q], c1[Q];
+        sload<Q>(p0, c0);
+        sload<Q>(p1, c1);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const float t = c0[a];
+            c0[a] = o[a] * c1[a];
+            c1[a] = o[a] * t;
+        }
+        const float i0 = 1.0f / vmax(c0), i1 = 1.0f / vmax(c1);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            c0[a] *= i0;
+            c1[a] *= i1;
+        }
+        sstore<Q>(p0, c0);
+        sstore<Q>(p1, c1);
+    });
+}
+
+// Index h^{-1} x for every x from the images of the basis vectors: multiplying
+// by a fixed field element is GF(2)-linear, so h^{-1} x is the XOR of
+// h^{-1} 2^b over the set bits b of x.
+template <int Q>
+__device__ __forceinline__ int gf_lin(const int (&basis)[6], int x)
+{
+    int r = 0;
+#pragma unroll
+    for (int b = 0; (1 << b) < Q; ++b)
+        if (x & (1 << b)) r ^= basis[b];
+    return r;
+}
+
+// Check node of check j of user k, thread shape, position-major layout.
+// slot_k: [E] (position*2 + d) of each edge; coef: [E] coefficients.
+template <int Q>
+__device__ __forceinline__ void check_thread_pos(float* msg_f, int NB, int k, int j, const uint16_t* slot_k,
+                                                 const uint8_t* coef, const uint8_t* gdiv)
+{
+    float P[kDC][Q];
+    int base[kDC], basis[kDC][6];
+#pragma unroll
+    for (int d = 0; d < kDC; ++d) {
+        const int e = 4 * j + d, sl = slot_k[e], pp = sl >> 1;
+        base[d] = pos_vec<Q>((k * NB + (pp >> 5)) * 2 + (sl & 1), pp);
+        const uint8_t* dv = gdiv + coef[e] * Q;
+#pragma unroll
+        for (int b = 0; b < 6; ++b) basis[d][b] = ((1 << b) < Q) ? dv[1 << b] : 0;
+#pragma unroll
+        for (int x = 0; x < Q; ++x) P[d][x] = msg_f[base[d] + pos_sym<Q>(gf_lin<Q>(basis[d], x))];
+    }
+#pragma unroll
+    for (int d = 0; d < kDC; ++d) wht_reg<Q>(P[d]);
+#pragma unroll
+    for (int x = 0; x < Q; ++x) {
+        const float p0 = P[0][x], p1 = P[1][x], p2 = P[2][x], p3 = P[3][x];
+        const float l01 = p0 * p1, r23 = p2 * p3;
+        P[0][x] = p1 * r23;
+        P[1][x] = p0 * r23;
+        P[2][x] = l01 * p3;
+        P[3][x] = l01 * p2;
+    }
+#pragma unroll
+    for (int d = 0; d < kDC; ++d) {
+        wht_reg<Q>(P[d]);
+        const float mx = vmax(P[d]);
+        const float fl = kRelFloor * mx, inv = 1.0f / mx;
+#pragma unroll
+        for (int x = 0; x < Q; ++x) msg_f[base[d] + pos_sym<Q>(gf_lin<Q>(basis[d], x))] = fmaxf(P[d][x], fl) * inv;
+    }
+}
+
+// Posterior and decision of the variable at position p of user k.
+template <int Q>
+__device__ __forceinline__ int var_thread_pos(const float* msg_f, const float* ch2v_f, int NB, int k, int p,
+                                              float* logpost_ki)
+{
+    float b[Q], c0[Q], c1[Q];
+    const int row = k * NB + (p >> 5);
+    sload<Q>(ch2v_f + pos_vec<Q>(row, p), b);
+    sload<Q>(msg_f + pos_vec<Q>(2 * row, p), c0);
+    sload<Q>(msg_f + pos_vec<Q>(2 * row + 1, p), c1);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) b[a] *= c0[a] * c1[a];
+    float bv = b[0];
+    int bi = 0;
+#pragma unroll
+    for (int a = 1; a < Q; ++a)
+        if (b[a] > bv) {
+            bv = b[a];
+            bi = a;
+        }
+    if (logpost_ki) {
+        const float l = __logf(bv);
+        float o[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) o[a] = __logf(b[a]) - l;
+        vstore<Q>(logpost_ki, o);
+    }
+    return bi;
 }
 
 // eq. (app_ldpc_check_eq) for check j of one user's decisions.

@@ -179,6 +179,184 @@ __global__ void __launch_bounds__(kFusedMaxThreads) k_fused(Graph g, int F, int 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Position-major fused kernel (thread shape: q <= 16, K <= 4, dv = 2)
+// ---------------------------------------------------------------------------
+//
+// Shared memory per CTA (NB = ceil(n/32), every q-vector interleaved over 32
+// positions, see jbp_device.cuh):
+//   msg  [G][K*NB*2][q][32] f32   c2v / v2c of each variable's two edges, in place
+//   ch2v [G][K*NB][q][32]   f32
+//   y    [G][NB*32] f32, hat [G][K][NB*32] u8 (position order), unsat [G][K], active [G]
+//   slot [K][E] u16, coef [E] u8, gf mul/div [q*q] u8 (shared by the G frames)
+// Phase A reads and writes consecutive banks; phase B gathers each check's
+// four edges through slot (the only irregular access of an iteration).
+
+struct PosLayout {
+    size_t msg, ch2v, y, hat, unsat, active, slot, coef, gmul, gdiv, total;
+};
+
+__host__ __device__ inline PosLayout pos_layout(const Graph& g, int G)
+{
+    const size_t NB = (size_t)(g.n + 31) / 32;
+    PosLayout L;
+    size_t o = 0;
+    L.msg = o;    o = align16(o + sizeof(float) * (size_t)G * g.K * NB * 2 * g.Q * 32);
+    L.ch2v = o;   o = align16(o + sizeof(float) * (size_t)G * g.K * NB * g.Q * 32);
+    L.y = o;      o = align16(o + sizeof(float) * (size_t)G * NB * 32);
+    L.hat = o;    o = align16(o + (size_t)G * g.K * NB * 32);
+    L.unsat = o;  o = align16(o + (size_t)G * g.K);
+    L.active = o; o = align16(o + (size_t)G);
+    L.slot = o;   o = align16(o + sizeof(uint16_t) * (size_t)g.K * g.E);
+    L.coef = o;   o = align16(o + (size_t)g.E);
+    L.gmul = o;   o = align16(o + (size_t)g.Q * g.Q);
+    L.gdiv = o;   o = align16(o + (size_t)g.Q * g.Q);
+    L.total = o;
+    return L;
+}
+
+template <int Q, int KC>
+__global__ void __launch_bounds__(kFusedMaxThreads) k_fused_pos(Graph g, int F, int G, const float* __restrict__ y,
+                                                                int T_it, int early_stop, uint8_t* hat,
+                                                                int32_t* iters, uint8_t* ok, float* logpost)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    const PosLayout lay = pos_layout(g, G);
+    const int n = g.n, P = g.P, E = g.E, NB = (n + 31) / 32;
+    constexpr int K = KC;
+    float* s_msg = reinterpret_cast<float*>(sm + lay.msg);
+    float* s_ch2v = reinterpret_cast<float*>(sm + lay.ch2v);
+    float* s_y = reinterpret_cast<float*>(sm + lay.y);
+    uint8_t* s_hat = sm + lay.hat;
+    uint8_t* s_unsat = sm + lay.unsat;
+    uint8_t* s_active = sm + lay.active;
+    uint16_t* s_slot = reinterpret_cast<uint16_t*>(sm + lay.slot);
+    uint8_t* s_coef = sm + lay.coef;
+    uint8_t* s_mul = sm + lay.gmul;
+    uint8_t* s_div = sm + lay.gdiv;
+    __shared__ int s_nactive;
+
+    const size_t fs = (size_t)K * NB * 2 * Q * 32, vs = (size_t)K * NB * Q * 32, hs = (size_t)K * NB * 32;
+    for (int i = threadIdx.x; i < Q * Q; i += blockDim.x) {
+        s_mul[i] = g.gf_mul[i];
+        s_div[i] = g.gf_div[i];
+    }
+    for (int i = threadIdx.x; i < K * E; i += blockDim.x) s_slot[i] = g.slot[i];
+    for (int i = threadIdx.x; i < E; i += blockDim.x) s_coef[i] = g.chk_coef[i];
+
+    const int groups = (F + G - 1) / G;
+    for (int grp = blockIdx.x; grp < groups; grp += gridDim.x) {
+        const int f0 = grp * G, gc = min(G, F - f0);
+        for (size_t i = threadIdx.x; i < (size_t)gc * fs; i += blockDim.x) s_msg[i] = 1.0f;
+        for (int i = threadIdx.x; i < gc * n; i += blockDim.x) s_y[(i / n) * NB * 32 + i % n] = y[(size_t)f0 * n + i];
+        for (int i = threadIdx.x; i < gc * K; i += blockDim.x) s_unsat[i] = 0;
+        for (int i = threadIdx.x; i < G; i += blockDim.x) s_active[i] = i < gc ? 1 : 0;
+        __syncthreads();
+
+        for (int t = 1; t <= T_it; ++t) {
+            // (A) channel nodes, v2c in place
+            for (int unit = threadIdx.x; unit < gc * n; unit += blockDim.x) {
+                const int gi = unit / n, p = unit % n;
+                if (!s_active[gi]) continue;
+                chan_thread_pos<K, Q>(g, s_msg + gi * fs, s_ch2v + gi * vs, NB, s_y[gi * NB * 32 + p], p);
+            }
+            __syncthreads();
+            // (B) check nodes
+            for (int unit = threadIdx.x; unit < gc * K * P; unit += blockDim.x) {
+                const int gi = unit / (K * P), rem = unit % (K * P), k = rem / P, j = rem % P;
+                if (!s_active[gi]) continue;
+                check_thread_pos<Q>(s_msg + gi * fs, NB, k, j, s_slot + k * E, s_coef, s_div);
+            }
+            __syncthreads();
+            // (C) posterior and decisions (position order)
+            for (int unit = threadIdx.x; unit < gc * K * n; unit += blockDim.x) {
+                const int gi = unit / (K * n), rem = unit % (K * n), k = rem / n, p = rem % n;
+                if (!s_active[gi]) continue;
+                float* lp = nullptr;
+                if (logpost) lp = logpost + (((size_t)(f0 + gi) * K + k) * n + g.use_pos[k * n + p]) * Q;
+                s_hat[gi * hs + k * NB * 32 + p] = (uint8_t)var_thread_pos<Q>(s_msg + gi * fs, s_ch2v + gi * vs,
+                                                                              NB, k, p, lp);
+            }
+            __syncthreads();
+            // (D) syndromes
+            for (int w = threadIdx.x; w < gc * K * P; w += blockDim.x) {
+                const int gi = w / (K * P), rem = w % (K * P), k = rem / P, j = rem % P;
+                if (!s_active[gi]) continue;
+                const uint8_t* hk = s_hat + gi * hs + k * NB * 32;
+                int sy = 0;
+#pragma unroll
+                for (int d = 0; d < kDC; ++d) {
+                    const int e = 4 * j + d;
+                    sy ^= s_mul[s_coef[e] * Q + hk[s_slot[k * E + e] >> 1]];
+                }
+                if (sy) s_unsat[gi * K + k] = 1;
+            }
+            if (threadIdx.x == 0) s_nactive = 0;
+            __syncthreads();
+            // (E) per-frame stop
+            for (int gi = threadIdx.x; gi < gc; gi += blockDim.x) {
+                if (!s_active[gi]) continue;
+                bool all = true;
+                for (int k = 0; k < K; ++k) {
+                    const bool okk = s_unsat[gi * K + k] == 0;
+                    ok[(size_t)(f0 + gi) * K + k] = okk ? 1 : 0;
+                    s_unsat[gi * K + k] = 0;
+                    all = all && okk;
+                }
+                iters[f0 + gi] = t;
+                if (early_stop && all) s_active[gi] = 0;
+                else atomicAdd(&s_nactive, 1);
+            }
+            __syncthreads();
+            if (s_nactive == 0) break;
+        }
+        // decisions back to variable order
+        for (int w = threadIdx.x; w < gc * K * n; w += blockDim.x) {
+            const int gi = w / (K * n), rem = w % (K * n), k = rem / n, i = rem % n;
+            hat[(size_t)f0 * K * n + w] = s_hat[gi * hs + k * NB * 32 + g.pos_of[k * n + i]];
+        }
+        __syncthreads();
+    }
+}
+
+template <int Q, int KC>
+bool plan_pos(const Graph& g, const DeviceInfo& di, int F, int threads_hint, int fpc_hint, FusedPlan* plan)
+{
+    int threads = threads_hint > 0 ? threads_hint : 256;
+    threads = std::max(32, std::min(kFusedMaxThreads, threads / 32 * 32));
+    int Gmax = 0;
+    for (int G = 1; G <= 4096; ++G) {
+        if (pos_layout(g, G).total + kStaticSmemMargin > (size_t)di.smem_optin) break;
+        Gmax = G;
+    }
+    if (Gmax == 0) return false;
+    int G = fpc_hint > 0 ? std::min(fpc_hint, Gmax) : Gmax;
+    G = std::max(1, std::min(G, (F + di.sm_count - 1) / di.sm_count));
+    plan->frames_per_cta = G;
+    plan->threads = threads;
+    plan->smem_bytes = (int)pos_layout(g, G).total;
+    int occ = 0;
+    if (cudaFuncSetAttribute(k_fused_pos<Q, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem_bytes) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_pos<Q, KC>, threads, plan->smem_bytes) !=
+            cudaSuccess ||
+        occ < 1)
+        return false;
+    plan->grid = std::max(1, std::min((F + G - 1) / G, di.sm_count * occ));
+    return true;
+}
+
+template <int Q, int KC>
+cudaError_t fused_pos(const Graph& g, const FusedPlan& p, int F, const float* y, int T_it, int early_stop,
+                      uint8_t* hat, int32_t* iters, uint8_t* ok, float* post, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_fused_pos<Q, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem_bytes);
+    if (e != cudaSuccess) return e;
+    k_fused_pos<Q, KC><<<p.grid, p.threads, p.smem_bytes, s>>>(g, F, p.frames_per_cta, y, T_it, early_stop, hat,
+                                                                iters, ok, post);
+    return cudaGetLastError();
+}
+
 template <int Q, int KC>
 bool plan_qk(const Graph& g, const DeviceInfo& di, int F, int threads_hint, int fpc_hint, FusedPlan* plan)
 {
@@ -226,36 +404,39 @@ cudaError_t fused_qk(const Graph& g, const FusedPlan& p, int F, const float* y, 
 }
 
 // Which k_fused<Q, KC> instance serves this graph.
-inline int fused_kc(const Graph& g) { return (g.Q <= 16 && g.dv == 2 && g.K <= 4) ? g.K : 0; }
+inline int fused_kc(const Graph& g)
+{
+    return (g.Q <= 16 && g.dv == 2 && g.K <= 4 && g.n <= 32767 && g.slot && g.pos_of) ? g.K : 0;
+}
 
 }  // namespace
 
-#define JBP_FUSED_DISPATCH(FN, ...)                                                  \
+#define JBP_FUSED_DISPATCH(FN_POS, FN_TEAM, ...)                                     \
     do {                                                                             \
         const int kc = fused_kc(g);                                                  \
         switch (g.Q * 8 + kc) {                                                      \
-            case 2 * 8 + 0: return FN<2, 0>(__VA_ARGS__);                            \
-            case 2 * 8 + 1: return FN<2, 1>(__VA_ARGS__);                            \
-            case 2 * 8 + 2: return FN<2, 2>(__VA_ARGS__);                            \
-            case 2 * 8 + 3: return FN<2, 3>(__VA_ARGS__);                            \
-            case 2 * 8 + 4: return FN<2, 4>(__VA_ARGS__);                            \
-            case 4 * 8 + 0: return FN<4, 0>(__VA_ARGS__);                            \
-            case 4 * 8 + 1: return FN<4, 1>(__VA_ARGS__);                            \
-            case 4 * 8 + 2: return FN<4, 2>(__VA_ARGS__);                            \
-            case 4 * 8 + 3: return FN<4, 3>(__VA_ARGS__);                            \
-            case 4 * 8 + 4: return FN<4, 4>(__VA_ARGS__);                            \
-            case 8 * 8 + 0: return FN<8, 0>(__VA_ARGS__);                            \
-            case 8 * 8 + 1: return FN<8, 1>(__VA_ARGS__);                            \
-            case 8 * 8 + 2: return FN<8, 2>(__VA_ARGS__);                            \
-            case 8 * 8 + 3: return FN<8, 3>(__VA_ARGS__);                            \
-            case 8 * 8 + 4: return FN<8, 4>(__VA_ARGS__);                            \
-            case 16 * 8 + 0: return FN<16, 0>(__VA_ARGS__);                          \
-            case 16 * 8 + 1: return FN<16, 1>(__VA_ARGS__);                          \
-            case 16 * 8 + 2: return FN<16, 2>(__VA_ARGS__);                          \
-            case 16 * 8 + 3: return FN<16, 3>(__VA_ARGS__);                          \
-            case 16 * 8 + 4: return FN<16, 4>(__VA_ARGS__);                          \
-            case 32 * 8 + 0: return FN<32, 0>(__VA_ARGS__);                          \
-            case 64 * 8 + 0: return FN<64, 0>(__VA_ARGS__);                          \
+            case 2 * 8 + 0: return FN_TEAM<2, 0>(__VA_ARGS__);                       \
+            case 2 * 8 + 1: return FN_POS<2, 1>(__VA_ARGS__);                        \
+            case 2 * 8 + 2: return FN_POS<2, 2>(__VA_ARGS__);                        \
+            case 2 * 8 + 3: return FN_POS<2, 3>(__VA_ARGS__);                        \
+            case 2 * 8 + 4: return FN_POS<2, 4>(__VA_ARGS__);                        \
+            case 4 * 8 + 0: return FN_TEAM<4, 0>(__VA_ARGS__);                       \
+            case 4 * 8 + 1: return FN_POS<4, 1>(__VA_ARGS__);                        \
+            case 4 * 8 + 2: return FN_POS<4, 2>(__VA_ARGS__);                        \
+            case 4 * 8 + 3: return FN_POS<4, 3>(__VA_ARGS__);                        \
+            case 4 * 8 + 4: return FN_POS<4, 4>(__VA_ARGS__);                        \
+            case 8 * 8 + 0: return FN_TEAM<8, 0>(__VA_ARGS__);                       \
+            case 8 * 8 + 1: return FN_POS<8, 1>(__VA_ARGS__);                        \
+            case 8 * 8 + 2: return FN_POS<8, 2>(__VA_ARGS__);                        \
+            case 8 * 8 + 3: return FN_POS<8, 3>(__VA_ARGS__);                        \
+            case 8 * 8 + 4: return FN_POS<8, 4>(__VA_ARGS__);                        \
+            case 16 * 8 + 0: return FN_TEAM<16, 0>(__VA_ARGS__);                     \
+            case 16 * 8 + 1: return FN_POS<16, 1>(__VA_ARGS__);                      \
+            case 16 * 8 + 2: return FN_POS<16, 2>(__VA_ARGS__);                      \
+            case 16 * 8 + 3: return FN_POS<16, 3>(__VA_ARGS__);                      \
+            case 16 * 8 + 4: return FN_POS<16, 4>(__VA_ARGS__);                      \
+            case 32 * 8 + 0: return FN_TEAM<32, 0>(__VA_ARGS__);                     \
+            case 64 * 8 + 0: return FN_TEAM<64, 0>(__VA_ARGS__);                     \
             default: break;                                                          \
         }                                                                            \
     } while (0)
@@ -263,7 +444,7 @@ inline int fused_kc(const Graph& g) { return (g.Q <= 16 && g.dv == 2 && g.K <= 4
 bool fused_plan(const Graph& g, const DeviceInfo& di, int F, int threads_hint, int fpc_hint, FusedPlan* plan)
 {
     if (g.dc != kDC || F <= 0) return false;
-    JBP_FUSED_DISPATCH(plan_qk, g, di, F, threads_hint, fpc_hint, plan);
+    JBP_FUSED_DISPATCH(plan_pos, plan_qk, g, di, F, threads_hint, fpc_hint, plan);
     return false;
 }
 
@@ -271,7 +452,7 @@ cudaError_t launch_fused(const Graph& g, const FusedPlan& plan, int F, const flo
                          uint8_t* hat, int32_t* iters, uint8_t* ok, float* post, cudaStream_t s)
 {
     if (F <= 0) return cudaSuccess;
-    JBP_FUSED_DISPATCH(fused_qk, g, plan, F, y, T_it, early_stop, hat, iters, ok, post, s);
+    JBP_FUSED_DISPATCH(fused_pos, fused_qk, g, plan, F, y, T_it, early_stop, hat, iters, ok, post, s);
     return cudaErrorInvalidValue;
 }
 

@@ -181,6 +181,9 @@ extern "C" int jbp_decode_noalloc(const jbp_code* code, int32_t K, const jbp_cha
     g.gf_mul = D + o_mul;
     g.gf_div = D + o_div;
     g.log_fallbacks = nullptr;
+    g.pos_of = nullptr;
+    g.slot = nullptr;
+    g.tc_error = nullptr;
     float* msg = reinterpret_cast<float*>(D + o_msg);
     float* ch2v = reinterpret_cast<float*>(D + o_ch2v);
     uint8_t* active = D + o_act;

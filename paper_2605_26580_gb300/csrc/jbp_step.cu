@@ -265,7 +265,8 @@ cudaError_t launch_check(const Graph& g, const DeviceInfo& di, int F, float* msg
                          cudaStream_t s)
 {
     if (F <= 0) return cudaSuccess;
-    if (precision != 0) return launch_check_tc(g, di, F, msg, active, precision, s);
+    // tensor-core transforms for q >= 16; smaller fields use the FP32 butterflies
+    if (precision != 0 && g.Q >= 16) return launch_check_tc(g, di, F, msg, active, precision, s);
     JBP_DISPATCH_Q(g.Q, (check_q<Qc>(g, di, F, msg, active, s)));
 }
 

@@ -81,7 +81,7 @@ def lib():
             L.jbp_step_var.argtypes = [vp, i32, vp, vp, vp, vp, vp]
             L.jbp_step_syndrome.argtypes = [vp, i32, vp, vp, vp]
             L.jbp_query.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]
-            L.jbp_stats.argtypes = [vp, C.POINTER(u64)]
+            L.jbp_stats.argtypes = [vp, C.POINTER(u64), C.POINTER(i32)]
             L.jbp_decode_noalloc.argtypes = [C.POINTER(Code), i32, C.POINTER(Channel), i32, i32, i32, vp, vp, vp,
                                              vp, vp]
             for name in EXPORTS:
@@ -176,7 +176,12 @@ class Decoder:
 
     def log_fallbacks(self) -> int:
         v = C.c_uint64()
-        check(lib().jbp_stats(self.ptr, C.byref(v)))
+        check(lib().jbp_stats(self.ptr, C.byref(v), None))
+        return v.value
+
+    def tc_timeouts(self) -> int:
+        v = C.c_int32()
+        check(lib().jbp_stats(self.ptr, None, C.byref(v)))
         return v.value
 
     # -- whole decodes --------------------------------------------------------

@@ -264,3 +264,68 @@ def test_literal_channel_mode(env):
     print("literal mode: differing decisions at FP64 margins", np.sort(ref["margin"][diff])[:10])
     assert not (diff & (ref["margin"] > 1e-4)).any()
     assert (got["hat"][:, 0] == got["hat"][:, 1]).all()   # symmetric users, identical decisions
+
+
+def tc_bound(prec, q):
+    """Linear error bound (relative to the largest entry) of the tensor-core check
+    node: the FP32 butterfly bound plus the operand split error.  One BF16 term
+    keeps 8 significant bits (2^-9 relative), two keep 16 (2^-17), three about
+    24; the split error enters the forward input, the product (three factors,
+    to first order one each) and the inverse input: 4 q u_split."""
+    u = {3: 2.0 ** -25, 1: 2.0 ** -17, 2: 2.0 ** -9}[prec]
+    return 2 * wht_bound(q) + 4 * q * u
+
+
+@pytest.mark.parametrize("prec", [3, 1, 2])
+@pytest.mark.parametrize("K,q,n", [(4, 16, 256), (2, 64, 128), (3, 32, 64), (1, 16, 40)])
+def test_step_check_tensor_cores(env, prec, K, q, n):
+    """tcgen05 check node (BF16X3 / BF16X2 / BF16 operand splits) against the oracle."""
+    jbp, O, torch = env
+    code = I.make_code(n, q)
+    rng = np.random.default_rng(11 * n + q + prec)
+    E = code["P"] * code["dc"]
+    F = 5
+    v2c_lin = np.exp(I.random_log_messages(rng, (F, K, E), q, spread=3.0)).astype(np.float32)
+    ctx, dec = _decoder(jbp, code, K, 1.0, None)
+    try:
+        msg_d = torch.from_numpy(v2c_lin).cuda()
+        dec.step_check(msg_d, precision=prec)
+        torch.cuda.synchronize()
+        c2v_g = np.log(msg_d.cpu().numpy().astype(np.float64))
+        assert dec.tc_timeouts() == 0
+    finally:
+        dec.close()
+        ctx.close()
+    c2v_o = O.step_check_v2c(code, K, np.log(v2c_lin.astype(np.float64)))
+    lin = np.abs(np.exp(c2v_g) - np.exp(c2v_o)).max()
+    e_big, _ = masked_log_err(c2v_g, c2v_o, thresh=math.log(0.5))
+    e_log4, _ = masked_log_err(c2v_g, c2v_o)
+    B = tc_bound(prec, q)
+    print("tensor-core check prec=%d K=%d q=%d: linear err %.2e (bound %.2e), log err %.2e (rho>=0.5), %.2e (rho>=1e-4)"
+          % (prec, K, q, lin, B, e_big, e_log4))
+    assert np.isfinite(c2v_g).all()
+    assert lin <= B
+    assert np.allclose(c2v_g.max(-1), 0.0, atol=1e-5)
+
+
+@pytest.mark.parametrize("prec", [3, 1, 2])
+def test_decode_precision_variants(env, prec):
+    """Whole decodes with the tensor-core check node (step form): BF16X3 keeps the
+    decisions of the FP32 oracle wherever the margin exceeds 1e-3; BF16X2 and BF16
+    are reported (SER against the oracle's)."""
+    jbp, O, torch = env
+    code = I.make_code(64, 16)
+    fr = I.make_frames(code, 2, 16.0, 60, seed=91)
+    ctx, dec = _decoder(jbp, code, 2, fr["sigma2"], fr["perm"], iters=12, early_stop=True, precision=prec)
+    try:
+        got = dec.decode(fr["y"])
+    finally:
+        dec.close()
+        ctx.close()
+    ref = O.decode(code, 2, fr["sigma2"], fr["perm"], fr["y"], 12, early_stop=True, want_margin=True)
+    diff = got["hat"] != ref["hat"]
+    ser_g, ser_o = (got["hat"] != fr["c"]).mean(), (ref["hat"] != fr["c"]).mean()
+    print("precision %d: SER gpu %.5f oracle %.5f; decisions differing at margin > 1e-3: %d"
+          % (prec, ser_g, ser_o, int((diff & (ref["margin"] > 1e-3)).sum())))
+    if prec == 3:
+        assert not (diff & (ref["margin"] > 1e-3)).any()
