@@ -123,7 +123,9 @@ typedef struct {
  * the outputs are written.  on_device = 1: device pointers; the work is
  * enqueued on `stream` (a cudaStream_t, NULL = the handle's own stream) and the
  * call returns without waiting; outputs are valid once that stream reaches
- * this point.  form: jbp_form.  Buffers must not overlap. */
+ * this point.  form: jbp_form.  sigma2 [F]: optional (NULL = the handle's
+ * channel) per-frame noise variance, host or device like the other buffers.
+ * Buffers must not overlap. */
 typedef struct {
     int32_t F;
     const float *y;
@@ -134,6 +136,7 @@ typedef struct {
     int32_t on_device;
     int32_t form;
     void *stream;
+    const float *sigma2;
 } jbp_batch;
 
 /* Create a context on opt->device.  Fails with JBP_EINVAL on bad options,
@@ -159,9 +162,31 @@ int jbp_destroy(jbp_h *h);
 /* Decode one batch (see jbp_batch). */
 int jbp_decode(jbp_h *h, jbp_batch *batch);
 
+/* Decode several device batches of possibly different decoders (codes, K, q)
+ * of one context in one call: the parts run concurrently on the context's
+ * stream pool (parts of one handle run in order on one stream; at most 32
+ * distinct handles).  Every batch must have on_device = 1.  Work is ordered
+ * after prior work on `stream` (NULL = the context's stream) and completion is
+ * ordered before later work on it; the call returns without waiting.  The
+ * first call with a given argument set autotunes each fused part's launch
+ * shape (jbp_tune) and runs eagerly; the second captures the whole
+ * multi-part decode as one CUDA graph, which later calls with identical
+ * arguments (handles, sizes, pointers, stream) replay with one launch. */
+int jbp_decode_many(jbp_ctx *ctx, int32_t nparts, jbp_h *const *handles, const jbp_batch *batches, void *stream);
+
+/* Autotune the fused-form launch shape of a handle on a device batch (runs a
+ * few short timed launches that write the first frames' outputs) and keep the
+ * fastest; *threads and *frames_per_cta receive the choice (0 = default).
+ * Synchronous.  With batch == NULL the shape is set from *threads and
+ * *frames_per_cta instead (0 = default; threads > 256 selects, for K = 4, the
+ * variant that splits each channel use over two lanes).  The per-frame
+ * arithmetic does not depend on the shape. */
+int jbp_tune(jbp_h *h, const jbp_batch *batch, int32_t *threads, int32_t *frames_per_cta);
+
 /* Serving: queue one frame (y_frame [n] host pointer, copied before return)
- * for continuous batching on the context's device.  *ticket identifies it. */
-int jbp_submit(jbp_h *h, const float *y_frame, uint64_t *ticket);
+ * for continuous batching on the context's device; sigma2 > 0 is this
+ * frame's noise variance (<= 0: the handle's channel).  *ticket identifies it. */
+int jbp_submit(jbp_h *h, const float *y_frame, double sigma2, uint64_t *ticket);
 
 /* Serving: JBP_EAGAIN while the request runs; JBP_OK once finished, with
  * hat [K*n], iters [1] and ok [K] written (host pointers; any may be NULL).

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -93,27 +94,25 @@ static int gf_mul_host(int a, int b, int m)
 
 namespace {
 
-// Device buffers of one decode (grown on demand).  Sizes in frames.
+// A device buffer that only grows; its byte size is recorded so that it can be
+// freed without knowing which decoder last used it.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// Device buffers of one decode: step-form state and host-path staging.
 struct Workspace {
-    int cap_step = 0;      // frames of msg/ch2v/active/unsat
-    float* msg = nullptr;
-    float* ch2v = nullptr;
-    uint8_t* active = nullptr;
-    uint8_t* unsat = nullptr;
-    int cap_io = 0;        // frames of staging
-    bool io_post = false;
-    float* y = nullptr;
-    uint8_t* hat = nullptr;
-    int32_t* iters = nullptr;
-    uint8_t* ok = nullptr;
-    float* post = nullptr;
-    int64_t bytes = 0;
+    DevBuf msg, ch2v, active, unsat;             // step form, per frame state
+    DevBuf y, hat, iters, ok, post, sig;         // staging for host buffers / serving
+    uint64_t gen = 0;                            // bumped on every reallocation
 };
 
 struct Request {
     uint64_t ticket;
     jbp_h* h;
     std::vector<float> y;
+    float sigma2;   // > 0: this frame's noise variance; otherwise the handle's
     double t_submit;
 };
 
@@ -129,11 +128,12 @@ struct Slot {
     Workspace ws;
     size_t host_cap = 0;   // bytes of each pinned array below
     float* h_y = nullptr;
+    float* h_sig = nullptr;
     uint8_t* h_hat = nullptr;
     int32_t* h_iters = nullptr;
     uint8_t* h_ok = nullptr;
     bool busy = false;
-    jbp_h* h = nullptr;
+    jbp_h* h = nullptr;          // decoder of the batch in flight (set under the context lock)
     std::vector<Request> reqs;
     int64_t state_bytes = 0;
 };
@@ -164,6 +164,17 @@ struct jbp_ctx {
     std::vector<Slot> slots;
     int64_t inflight_bytes = 0;
     int handles = 0;
+
+    // multi-part decodes: stream pool, fork/join events, graphs keyed by arguments
+    std::mutex many_mu;
+    std::vector<cudaStream_t> pool;
+    std::vector<cudaEvent_t> pool_ev;
+    cudaEvent_t fork_ev = nullptr;
+    struct GraphEntry {
+        int seen = 0;
+        cudaGraphExec_t exec = nullptr;
+    };
+    std::map<std::vector<uintptr_t>, GraphEntry> graphs;
 };
 
 struct jbp_h {
@@ -184,6 +195,9 @@ struct jbp_h {
     Workspace ws;
     std::mutex ws_mu;
     bool fused_ok = false;
+    int tune_threads = 0, tune_fpc = 0;   // fused launch shape chosen by the autotuner (0 = default)
+    bool tuned = false;
+    uint64_t ws_gen = 0;                  // bumped whenever h->ws is reallocated (invalidates graphs)
 
     Graph graph() const
     {
@@ -196,6 +210,7 @@ struct jbp_h {
         g.pos_of = d_pos_of;
         g.slot = d_slot;
         g.tc_error = d_tc_error;
+        g.sigma2_f = nullptr;
         return g;
     }
 };
@@ -229,93 +244,92 @@ static void dev_free(jbp_ctx* ctx, void* p, size_t bytes)
     ctx->used -= (int64_t)std::max<size_t>(bytes, 16);
 }
 
-static void ws_io_free(jbp_ctx* ctx, const jbp_h* h, Workspace& w);
-
-static void ws_release(jbp_ctx* ctx, const jbp_h* h, Workspace& w)
+static int buf_ensure(jbp_ctx* ctx, DevBuf& b, size_t bytes, bool* grew)
 {
-    const size_t fs = (size_t)h->K * h->E * h->Q, vs = (size_t)h->K * h->n * h->Q;
-    dev_free(ctx, w.msg, sizeof(float) * fs * w.cap_step);
-    dev_free(ctx, w.ch2v, sizeof(float) * vs * w.cap_step);
-    dev_free(ctx, w.active, (size_t)w.cap_step);
-    dev_free(ctx, w.unsat, (size_t)w.cap_step * h->K);
-    ws_io_free(ctx, h, w);
-    w = Workspace();
+    bytes = std::max<size_t>(bytes, 16);
+    if (bytes <= b.bytes) return JBP_OK;
+    dev_free(ctx, b.p, b.bytes);
+    b.p = nullptr;
+    b.bytes = 0;
+    int rc = dev_alloc(ctx, reinterpret_cast<unsigned char**>(&b.p), bytes, nullptr);
+    if (rc) return rc;
+    b.bytes = bytes;
+    *grew = true;
+    return JBP_OK;
+}
+
+static void buf_free(jbp_ctx* ctx, DevBuf& b)
+{
+    dev_free(ctx, b.p, b.bytes);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+static void ws_release(jbp_ctx* ctx, Workspace& w)
+{
+    for (DevBuf* b : {&w.msg, &w.ch2v, &w.active, &w.unsat, &w.y, &w.hat, &w.iters, &w.ok, &w.post, &w.sig})
+        buf_free(ctx, *b);
+    w.gen++;
 }
 
 static int ws_step(jbp_ctx* ctx, const jbp_h* h, Workspace& w, int F)
 {
-    if (F <= w.cap_step) return JBP_OK;
     const size_t fs = (size_t)h->K * h->E * h->Q, vs = (size_t)h->K * h->n * h->Q;
-    dev_free(ctx, w.msg, sizeof(float) * fs * w.cap_step);
-    dev_free(ctx, w.ch2v, sizeof(float) * vs * w.cap_step);
-    dev_free(ctx, w.active, (size_t)w.cap_step);
-    dev_free(ctx, w.unsat, (size_t)w.cap_step * h->K);
-    w.msg = nullptr; w.ch2v = nullptr; w.active = nullptr; w.unsat = nullptr; w.cap_step = 0;
+    bool grew = false;
     int rc;
-    if ((rc = dev_alloc(ctx, &w.msg, fs * F, nullptr)) || (rc = dev_alloc(ctx, &w.ch2v, vs * F, nullptr)) ||
-        (rc = dev_alloc(ctx, &w.active, (size_t)F, nullptr)) || (rc = dev_alloc(ctx, &w.unsat, (size_t)F * h->K, nullptr))) {
-        dev_free(ctx, w.msg, sizeof(float) * fs * F);
-        dev_free(ctx, w.ch2v, sizeof(float) * vs * F);
-        dev_free(ctx, w.active, (size_t)F);
-        w.msg = nullptr; w.ch2v = nullptr; w.active = nullptr; w.unsat = nullptr;
+    if ((rc = buf_ensure(ctx, w.msg, sizeof(float) * fs * F, &grew)) ||
+        (rc = buf_ensure(ctx, w.ch2v, sizeof(float) * vs * F, &grew)) ||
+        (rc = buf_ensure(ctx, w.active, (size_t)F, &grew)) || (rc = buf_ensure(ctx, w.unsat, (size_t)F * h->K, &grew))) {
+        w.gen++;
         return rc;
     }
-    w.cap_step = F;
+    if (grew) w.gen++;
     return JBP_OK;
-}
-
-static void ws_io_free(jbp_ctx* ctx, const jbp_h* h, Workspace& w)
-{
-    const size_t vs = (size_t)h->K * h->n * h->Q;
-    dev_free(ctx, w.y, sizeof(float) * (size_t)w.cap_io * h->n);
-    dev_free(ctx, w.hat, (size_t)w.cap_io * h->K * h->n);
-    dev_free(ctx, w.iters, sizeof(int32_t) * (size_t)w.cap_io);
-    dev_free(ctx, w.ok, (size_t)w.cap_io * h->K);
-    if (w.io_post) dev_free(ctx, w.post, sizeof(float) * vs * w.cap_io);
-    w.y = nullptr; w.hat = nullptr; w.iters = nullptr; w.ok = nullptr; w.post = nullptr;
-    w.cap_io = 0; w.io_post = false;
 }
 
 static int ws_io(jbp_ctx* ctx, const jbp_h* h, Workspace& w, int F, bool post)
 {
-    if (F <= w.cap_io && (!post || w.io_post)) return JBP_OK;
-    ws_io_free(ctx, h, w);
     const size_t vs = (size_t)h->K * h->n * h->Q;
-    const int cap = std::max(F, 1);
+    const size_t cap = std::max(F, 1);
+    bool grew = false;
     int rc;
-    if ((rc = dev_alloc(ctx, &w.y, (size_t)cap * h->n, nullptr)) || (rc = dev_alloc(ctx, &w.hat, (size_t)cap * h->K * h->n, nullptr)) ||
-        (rc = dev_alloc(ctx, &w.iters, (size_t)cap, nullptr)) || (rc = dev_alloc(ctx, &w.ok, (size_t)cap * h->K, nullptr)) ||
-        (post && (rc = dev_alloc(ctx, &w.post, vs * cap, nullptr)))) {
-        // free what was allocated (null pointers are skipped)
-        w.cap_io = cap;
-        w.io_post = (w.post != nullptr);
-        ws_io_free(ctx, h, w);
+    if ((rc = buf_ensure(ctx, w.y, sizeof(float) * cap * h->n, &grew)) ||
+        (rc = buf_ensure(ctx, w.hat, cap * h->K * h->n, &grew)) ||
+        (rc = buf_ensure(ctx, w.iters, sizeof(int32_t) * cap, &grew)) ||
+        (rc = buf_ensure(ctx, w.ok, cap * h->K, &grew)) || (rc = buf_ensure(ctx, w.sig, sizeof(float) * cap, &grew)) ||
+        (post && (rc = buf_ensure(ctx, w.post, sizeof(float) * vs * cap, &grew)))) {
+        w.gen++;
         return rc;
     }
-    w.cap_io = cap;
-    w.io_post = post;
+    if (grew) w.gen++;
     return JBP_OK;
 }
+
+template <class T>
+static T* P(const DevBuf& b) { return static_cast<T*>(b.p); }
 
 // ---------------------------------------------------------------------------
 // decode forms
 // ---------------------------------------------------------------------------
 
-static int run_step_iters(jbp_h* h, Workspace& w, int F, const float* y, uint8_t* hat, int32_t* iters,
+static int run_step_iters(jbp_h* h, const Graph& g, Workspace& w, int F, const float* y, uint8_t* hat, int32_t* iters,
                           uint8_t* ok, float* post, cudaStream_t s)
 {
     jbp_ctx* ctx = h->ctx;
-    const Graph g = h->graph();
     const size_t fs = (size_t)h->K * h->E * h->Q;
-    JBP_CU(launch_fill(w.msg, fs * F, 1.0f, s), "init msg");
-    JBP_CU(cudaMemsetAsync(w.active, 1, (size_t)F, s), "memset active");
-    JBP_CU(cudaMemsetAsync(w.unsat, 0, (size_t)F * h->K, s), "memset unsat");
-    StepCtl c{w.active, w.unsat, iters, ok};
+    float* msg = P<float>(w.msg);
+    float* ch2v = P<float>(w.ch2v);
+    uint8_t* active = P<uint8_t>(w.active);
+    uint8_t* unsat = P<uint8_t>(w.unsat);
+    JBP_CU(launch_fill(msg, fs * F, 1.0f, s), "init msg");
+    JBP_CU(cudaMemsetAsync(active, 1, (size_t)F, s), "memset active");
+    JBP_CU(cudaMemsetAsync(unsat, 0, (size_t)F * h->K, s), "memset unsat");
+    StepCtl c{active, unsat, iters, ok};
     for (int t = 1; t <= ctx->opt.iters; ++t) {
-        JBP_CU(launch_channel(g, ctx->di, F, y, w.msg, w.ch2v, w.active, s), "channel kernel");
-        JBP_CU(launch_check(g, ctx->di, F, w.msg, w.active, ctx->opt.precision, s), "check kernel");
-        JBP_CU(launch_var(g, ctx->di, F, w.ch2v, w.msg, post, hat, w.active, s), "var kernel");
-        JBP_CU(launch_syndrome(g, ctx->di, F, hat, w.unsat, w.active, s), "syndrome kernel");
+        JBP_CU(launch_channel(g, ctx->di, F, y, msg, ch2v, active, s), "channel kernel");
+        JBP_CU(launch_check(g, ctx->di, F, msg, active, ctx->opt.precision, s), "check kernel");
+        JBP_CU(launch_var(g, ctx->di, F, ch2v, msg, post, hat, active, s), "var kernel");
+        JBP_CU(launch_syndrome(g, ctx->di, F, hat, unsat, active, s), "syndrome kernel");
         JBP_CU(launch_finalize(F, h->K, t, ctx->opt.early_stop, c, s), "finalize kernel");
     }
     return JBP_OK;
@@ -323,10 +337,12 @@ static int run_step_iters(jbp_h* h, Workspace& w, int F, const float* y, uint8_t
 
 // Decode F frames whose buffers are all on the device, on stream s.
 static int decode_device(jbp_h* h, Workspace& w, int form, int F, const float* y, uint8_t* hat, int32_t* iters,
-                         uint8_t* ok, float* post, cudaStream_t s)
+                         uint8_t* ok, float* post, const float* sigma2_f, cudaStream_t s)
 {
     if (F == 0) return JBP_OK;
     jbp_ctx* ctx = h->ctx;
+    Graph g = h->graph();
+    g.sigma2_f = sigma2_f;
     // the fused kernel runs the FP32 butterfly check node; the tensor-core
     // precision variants run in the step form
     if (form == JBP_FORM_AUTO) form = (h->fused_ok && ctx->opt.precision == JBP_PREC_FP32) ? JBP_FORM_FUSED : JBP_FORM_STEP;
@@ -336,22 +352,23 @@ static int decode_device(jbp_h* h, Workspace& w, int form, int F, const float* y
     if (form == JBP_FORM_FUSED) {
         if (!h->fused_ok) return fail(JBP_EINVAL, "one frame does not fit the fused form (shared memory)");
         FusedPlan plan;
-        if (!fused_plan(h->graph(), ctx->di, F, 0, 0, &plan)) return fail(JBP_EINVAL, "no fused launch plan");
-        JBP_CU(launch_fused(h->graph(), plan, F, y, ctx->opt.iters, ctx->opt.early_stop, hat, iters, ok, post, s),
-               "fused kernel");
+        if (!fused_plan(g, ctx->di, F, h->tune_threads, h->tune_fpc, &plan)) return fail(JBP_EINVAL, "no fused launch plan");
+        JBP_CU(launch_fused(g, plan, F, y, ctx->opt.iters, ctx->opt.early_stop, hat, iters, ok, post, s), "fused kernel");
         return JBP_OK;
     }
     if (form == JBP_FORM_STEP) {
         int rc = ws_step(ctx, h, w, F);
         if (rc) return rc;
-        return run_step_iters(h, w, F, y, hat, iters, ok, post, s);
+        return run_step_iters(h, g, w, F, y, hat, iters, ok, post, s);
     }
     if (form == JBP_FORM_PLAIN) {
         int rc = ws_step(ctx, h, w, 1);
         if (rc) return rc;
         const size_t vs = (size_t)h->K * h->n * h->Q;
         for (int f = 0; f < F; ++f) {
-            rc = run_step_iters(h, w, 1, y + (size_t)f * h->n, hat + (size_t)f * h->K * h->n, iters + f,
+            Graph gf = g;
+            if (sigma2_f) gf.sigma2_f = sigma2_f + f;
+            rc = run_step_iters(h, gf, w, 1, y + (size_t)f * h->n, hat + (size_t)f * h->K * h->n, iters + f,
                                 ok + (size_t)f * h->K, post ? post + vs * f : nullptr, s);
             if (rc) return rc;
         }
@@ -408,10 +425,17 @@ extern "C" int jbp_context_destroy(jbp_ctx* ctx)
     cudaSetDevice(ctx->device);
     for (Slot& s : ctx->slots) {
         if (s.stream) cudaStreamSynchronize(s.stream);
+        ws_release(ctx, s.ws);
         if (s.done) cudaEventDestroy(s.done);
         if (s.stream) cudaStreamDestroy(s.stream);
         cudaFreeHost(s.h_y); cudaFreeHost(s.h_hat); cudaFreeHost(s.h_iters); cudaFreeHost(s.h_ok);
+        cudaFreeHost(s.h_sig);
     }
+    for (auto& kv : ctx->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    for (cudaStream_t st : ctx->pool) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : ctx->pool_ev) cudaEventDestroy(ev);
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return JBP_OK;
@@ -482,7 +506,7 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
             gmul[(size_t)h * q + x] = (uint8_t)gf_mul_host(h, x, m);
             gdiv[(size_t)h * q + x] = (uint8_t)gf_mul_host(inv[h], x, m);
         }
-    const int scf = chan_scratch_floats(K, q);
+    const int scf = blk_scratch_floats(K, q);
     const int team_lanes = q < 32 ? q : 32;
     if ((size_t)(32 / team_lanes) * scf * sizeof(float) > (size_t)ctx->di.smem_optin)
         return fail(JBP_EINVAL, "K = %d, q = %d: channel trellis does not fit shared memory", K, q);
@@ -553,16 +577,27 @@ extern "C" int jbp_destroy(jbp_h* h)
                 if (s.busy && s.h == h) return false;
             return true;
         });
-        for (Slot& s : ctx->slots) {
-            if (s.h != h) continue;
-            ws_release(ctx, h, s.ws);
-            s.h = nullptr;
-        }
         if (counted) ctx->handles--;
     }
     cudaSetDevice(ctx->device);
+    {
+        // graphs captured with this handle refer to its tables and workspace
+        std::lock_guard<std::mutex> lk(ctx->many_mu);
+        for (cudaStream_t st : ctx->pool) cudaStreamSynchronize(st);
+        for (auto it = ctx->graphs.begin(); it != ctx->graphs.end();) {
+            bool uses = false;
+            for (size_t i = 1; i < it->first.size(); i += 10)
+                if (it->first[i] == (uintptr_t)h) uses = true;
+            if (uses) {
+                if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
+                it = ctx->graphs.erase(it);
+            } else {
+                ++it;
+            }
+        }
+    }
     cudaStreamSynchronize(ctx->stream);
-    ws_release(ctx, h, h->ws);
+    ws_release(ctx, h->ws);
     dev_free(ctx, h->d_chk_var, sizeof(int32_t) * h->E);
     dev_free(ctx, h->d_chk_coef, (size_t)h->E);
     dev_free(ctx, h->d_var_edge, sizeof(int32_t) * (size_t)h->n * h->dv);
@@ -617,7 +652,7 @@ extern "C" int jbp_decode(jbp_h* h, jbp_batch* b)
     if (b->on_device) {
         cudaStream_t s = b->stream ? (cudaStream_t)b->stream : ctx->stream;
         std::lock_guard<std::mutex> lk(h->ws_mu);
-        return decode_device(h, h->ws, b->form, F, b->y, b->hat, b->iters, b->ok, b->logpost, s);
+        return decode_device(h, h->ws, b->form, F, b->y, b->hat, b->iters, b->ok, b->logpost, b->sigma2, s);
     }
     cudaStream_t s = ctx->stream;
     std::lock_guard<std::mutex> lk(h->ws_mu);
@@ -625,20 +660,199 @@ extern "C" int jbp_decode(jbp_h* h, jbp_batch* b)
     int rc = ws_io(ctx, h, w, F, b->logpost != nullptr);
     if (rc) return rc;
     const size_t vs = (size_t)h->K * h->n * h->Q;
-    JBP_CU(cudaMemcpyAsync(w.y, b->y, sizeof(float) * (size_t)F * h->n, cudaMemcpyHostToDevice, s), "copy y");
-    rc = decode_device(h, w, b->form, F, w.y, w.hat, w.iters, w.ok, b->logpost ? w.post : nullptr, s);
+    float* dy = P<float>(w.y);
+    float* dsig = P<float>(w.sig);
+    float* dpost = P<float>(w.post);
+    uint8_t* dhat = P<uint8_t>(w.hat);
+    int32_t* dit = P<int32_t>(w.iters);
+    uint8_t* dok = P<uint8_t>(w.ok);
+    JBP_CU(cudaMemcpyAsync(dy, b->y, sizeof(float) * (size_t)F * h->n, cudaMemcpyHostToDevice, s), "copy y");
+    if (b->sigma2) JBP_CU(cudaMemcpyAsync(dsig, b->sigma2, sizeof(float) * F, cudaMemcpyHostToDevice, s), "copy sigma2");
+    rc = decode_device(h, w, b->form, F, dy, dhat, dit, dok, b->logpost ? dpost : nullptr, b->sigma2 ? dsig : nullptr, s);
     if (rc) return rc;
-    JBP_CU(cudaMemcpyAsync(b->hat, w.hat, (size_t)F * h->K * h->n, cudaMemcpyDeviceToHost, s), "copy hat");
-    JBP_CU(cudaMemcpyAsync(b->iters, w.iters, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s), "copy iters");
-    JBP_CU(cudaMemcpyAsync(b->ok, w.ok, (size_t)F * h->K, cudaMemcpyDeviceToHost, s), "copy ok");
+    JBP_CU(cudaMemcpyAsync(b->hat, dhat, (size_t)F * h->K * h->n, cudaMemcpyDeviceToHost, s), "copy hat");
+    JBP_CU(cudaMemcpyAsync(b->iters, dit, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s), "copy iters");
+    JBP_CU(cudaMemcpyAsync(b->ok, dok, (size_t)F * h->K, cudaMemcpyDeviceToHost, s), "copy ok");
     if (b->logpost)
-        JBP_CU(cudaMemcpyAsync(b->logpost, w.post, sizeof(float) * vs * F, cudaMemcpyDeviceToHost, s), "copy post");
+        JBP_CU(cudaMemcpyAsync(b->logpost, dpost, sizeof(float) * vs * F, cudaMemcpyDeviceToHost, s), "copy post");
     JBP_CU(cudaStreamSynchronize(s), "jbp_decode");
     if (ctx->opt.precision != JBP_PREC_FP32) {
         int err = 0;
         JBP_CU(cudaMemcpy(&err, h->d_tc_error, sizeof err, cudaMemcpyDeviceToHost), "jbp_decode: status");
         if (err) return fail(JBP_ETIMEOUT, "a tensor-core completion wait expired");
     }
+    return JBP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner and multi-part decodes
+// ---------------------------------------------------------------------------
+
+// Time candidate fused launch shapes (threads per CTA x frames per CTA) on the
+// first min(F, 4 * SMs) frames of a batch, a few iterations each, and keep the
+// fastest for this handle.  Every candidate runs the same per-frame arithmetic,
+// so the choice changes speed only.
+static int autotune(jbp_h* h, int F, const float* y, uint8_t* hat, int32_t* iters, uint8_t* ok,
+                    const float* sigma2_f, cudaStream_t s)
+{
+    jbp_ctx* ctx = h->ctx;
+    if (!h->fused_ok || F <= 0) return JBP_OK;
+    Graph g = h->graph();
+    g.sigma2_f = sigma2_f;
+    const int Fs = std::min(F, 4 * ctx->di.sm_count);
+    const int T = std::min(ctx->opt.iters, 4);
+    cudaEvent_t a, b;
+    JBP_CU(cudaEventCreate(&a), "tune event");
+    JBP_CU(cudaEventCreate(&b), "tune event");
+    float best = 1e30f;
+    int bt = 0, bf = 0;
+    const int threads_c[] = {128, 192, 256, 384, 512};
+    const int fpc_c[] = {1, 2, 4, 8, 16, 0};
+    for (int th : threads_c)
+        for (int fc : fpc_c) {
+            FusedPlan plan;
+            if (!fused_plan(g, ctx->di, Fs, th, fc, &plan)) continue;
+            if (fc > 0 && plan.frames_per_cta != fc) continue;   // duplicate of a smaller hint
+            float ms = 0;
+            for (int rep = 0; rep < 2; ++rep) {
+                cudaEventRecord(a, s);
+                if (launch_fused(g, plan, Fs, y, T, 0, hat, iters, ok, nullptr, s) != cudaSuccess) break;
+                cudaEventRecord(b, s);
+                cudaEventSynchronize(b);
+                cudaEventElapsedTime(&ms, a, b);
+            }
+            const float per_frame = ms / Fs;
+            if (per_frame < best) {
+                best = per_frame;
+                bt = th;
+                bf = fc;
+            }
+        }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaGetLastError();
+    h->tune_threads = bt;
+    h->tune_fpc = bf;
+    h->tuned = true;
+    return JBP_OK;
+}
+
+extern "C" int jbp_tune(jbp_h* h, const jbp_batch* b, int32_t* threads, int32_t* frames_per_cta)
+{
+    if (!h) return fail(JBP_EINVAL, "jbp_tune: NULL handle");
+    if (!b) {
+        // manual shape
+        if (!threads || !frames_per_cta || *threads < 0 || *frames_per_cta < 0)
+            return fail(JBP_EINVAL, "jbp_tune: a manual shape needs threads and frames_per_cta >= 0");
+        h->tune_threads = *threads;
+        h->tune_fpc = *frames_per_cta;
+        h->tuned = true;
+        return JBP_OK;
+    }
+    if (!b->on_device) return fail(JBP_EINVAL, "jbp_tune: needs a device batch");
+    JBP_CU(cudaSetDevice(h->ctx->device), "cudaSetDevice");
+    cudaStream_t s = b->stream ? (cudaStream_t)b->stream : h->ctx->stream;
+    int rc = autotune(h, b->F, b->y, b->hat, b->iters, b->ok, b->sigma2, s);
+    if (rc) return rc;
+    if (threads) *threads = h->tune_threads;
+    if (frames_per_cta) *frames_per_cta = h->tune_fpc;
+    return JBP_OK;
+}
+
+static int many_enqueue(jbp_ctx* ctx, int nparts, jbp_h* const* handles, const jbp_batch* bs, cudaStream_t main)
+{
+    JBP_CU(cudaEventRecord(ctx->fork_ev, main), "fork");
+    // distinct handles go to pool streams round-robin (parts of one handle share
+    // its workspace, so they stay in order on one stream)
+    std::vector<jbp_h*> order;
+    for (int i = 0; i < nparts; ++i)
+        if (std::find(order.begin(), order.end(), handles[i]) == order.end()) order.push_back(handles[i]);
+    const size_t S = std::min(order.size(), ctx->pool.size());
+    for (size_t u = 0; u < S; ++u) JBP_CU(cudaStreamWaitEvent(ctx->pool[u], ctx->fork_ev, 0), "fork wait");
+    for (size_t u = 0; u < order.size(); ++u) {
+        cudaStream_t st = ctx->pool[u % S];
+        for (int i = 0; i < nparts; ++i) {
+            if (handles[i] != order[u]) continue;
+            const jbp_batch& b = bs[i];
+            int rc = decode_device(handles[i], handles[i]->ws, b.form, b.F, b.y, b.hat, b.iters, b.ok, b.logpost,
+                                   b.sigma2, st);
+            if (rc) return rc;
+        }
+    }
+    for (size_t u = 0; u < S; ++u) {
+        JBP_CU(cudaEventRecord(ctx->pool_ev[u], ctx->pool[u]), "join");
+        JBP_CU(cudaStreamWaitEvent(main, ctx->pool_ev[u], 0), "join wait");
+    }
+    return JBP_OK;
+}
+
+extern "C" int jbp_decode_many(jbp_ctx* ctx, int32_t nparts, jbp_h* const* handles, const jbp_batch* batches,
+                               void* stream)
+{
+    if (!ctx || nparts < 0 || (nparts > 0 && (!handles || !batches))) return fail(JBP_EINVAL, "jbp_decode_many: bad argument");
+    for (int i = 0; i < nparts; ++i) {
+        const jbp_batch& b = batches[i];
+        if (!handles[i] || handles[i]->ctx != ctx) return fail(JBP_EINVAL, "part %d: handle of another context", i);
+        if (!b.on_device) return fail(JBP_EINVAL, "part %d: jbp_decode_many takes device batches", i);
+        if (b.F < 0 || (b.F > 0 && (!b.y || !b.hat || !b.iters || !b.ok))) return fail(JBP_EINVAL, "part %d: bad batch", i);
+    }
+    JBP_CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    std::lock_guard<std::mutex> lk(ctx->many_mu);
+    if (ctx->pool.empty()) {
+        ctx->pool.resize(32);
+        ctx->pool_ev.resize(32);
+        for (int i = 0; i < 32; ++i) {
+            JBP_CU(cudaStreamCreateWithFlags(&ctx->pool[i], cudaStreamNonBlocking), "pool stream");
+            JBP_CU(cudaEventCreateWithFlags(&ctx->pool_ev[i], cudaEventDisableTiming), "pool event");
+        }
+        JBP_CU(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming), "fork event");
+    }
+    cudaStream_t main = stream ? (cudaStream_t)stream : ctx->stream;
+    std::vector<uintptr_t> key;
+    key.push_back((uintptr_t)main);
+    for (int i = 0; i < nparts; ++i) {
+        const jbp_batch& b = batches[i];
+        for (uintptr_t v : {(uintptr_t)handles[i], (uintptr_t)handles[i]->ws.gen, (uintptr_t)b.F, (uintptr_t)b.y,
+                            (uintptr_t)b.hat, (uintptr_t)b.iters, (uintptr_t)b.ok, (uintptr_t)b.logpost,
+                            (uintptr_t)b.form, (uintptr_t)b.sigma2})
+            key.push_back(v);
+    }
+    auto& ge = ctx->graphs[key];
+    if (ge.exec) {
+        JBP_CU(cudaGraphLaunch(ge.exec, main), "graph launch");
+        return JBP_OK;
+    }
+    if (ge.seen == 0) {
+        // first call: tune the fused parts, size the workspaces, run eagerly
+        for (int i = 0; i < nparts; ++i) {
+            jbp_h* h = handles[i];
+            const jbp_batch& b = batches[i];
+            if (!h->tuned && h->fused_ok && ctx->opt.precision == JBP_PREC_FP32 &&
+                (b.form == JBP_FORM_AUTO || b.form == JBP_FORM_FUSED)) {
+                int rc = autotune(h, b.F, b.y, b.hat, b.iters, b.ok, b.sigma2, main);
+                if (rc) return rc;
+            }
+        }
+        ge.seen = 1;
+        return many_enqueue(ctx, nparts, handles, batches, main);
+    }
+    // second call with these arguments: capture the whole decode as one graph
+    JBP_CU(cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal), "begin capture");
+    int rc = many_enqueue(ctx, nparts, handles, batches, main);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(main, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&ge.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        ge.exec = nullptr;
+        return cuda_fail(e, "graph instantiate");
+    }
+    JBP_CU(cudaGraphLaunch(ge.exec, main), "graph launch");
     return JBP_OK;
 }
 
@@ -698,7 +912,7 @@ extern "C" int jbp_step_syndrome(jbp_h* h, int32_t F, const uint8_t* hat, uint8_
 // different slots overlap on the device.  Each frame's arithmetic does not
 // depend on which other frames share its launch.
 
-static constexpr int kSlots = 4;
+static constexpr int kSlots = 16;
 static constexpr int kMaxServeBatch = 8192;
 
 static int slot_prepare(jbp_ctx* ctx, Slot& s, jbp_h* h, int F)
@@ -707,17 +921,15 @@ static int slot_prepare(jbp_ctx* ctx, Slot& s, jbp_h* h, int F)
         JBP_CU(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking), "slot stream");
         JBP_CU(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming), "slot event");
     }
-    if (s.h != h && (s.ws.cap_step || s.ws.cap_io)) {
-        if (s.h) ws_release(ctx, s.h, s.ws);
-    }
-    s.h = h;
     const size_t need = std::max<size_t>({sizeof(float) * (size_t)F * h->n, (size_t)F * h->K * h->n,
                                           sizeof(int32_t) * (size_t)F, (size_t)F * h->K});
     if (need > s.host_cap) {
         cudaFreeHost(s.h_y); cudaFreeHost(s.h_hat); cudaFreeHost(s.h_iters); cudaFreeHost(s.h_ok);
-        s.h_y = nullptr; s.h_hat = nullptr; s.h_iters = nullptr; s.h_ok = nullptr; s.host_cap = 0;
+        cudaFreeHost(s.h_sig);
+        s.h_y = nullptr; s.h_hat = nullptr; s.h_iters = nullptr; s.h_ok = nullptr; s.h_sig = nullptr; s.host_cap = 0;
         const size_t cap = std::max(need, (size_t)(1 << 16));
         JBP_CU(cudaMallocHost((void**)&s.h_y, cap), "pinned y");
+        JBP_CU(cudaMallocHost((void**)&s.h_sig, cap), "pinned sigma2");
         JBP_CU(cudaMallocHost((void**)&s.h_hat, cap), "pinned hat");
         JBP_CU(cudaMallocHost((void**)&s.h_iters, cap), "pinned iters");
         JBP_CU(cudaMallocHost((void**)&s.h_ok, cap), "pinned ok");
@@ -730,13 +942,22 @@ static int slot_launch(jbp_ctx* ctx, Slot& s)
 {
     jbp_h* h = s.h;
     const int F = (int)s.reqs.size();
-    for (int f = 0; f < F; ++f) memcpy(s.h_y + (size_t)f * h->n, s.reqs[f].y.data(), sizeof(float) * h->n);
-    JBP_CU(cudaMemcpyAsync(s.ws.y, s.h_y, sizeof(float) * (size_t)F * h->n, cudaMemcpyHostToDevice, s.stream), "serve copy y");
-    int rc = decode_device(h, s.ws, JBP_FORM_AUTO, F, s.ws.y, s.ws.hat, s.ws.iters, s.ws.ok, nullptr, s.stream);
+    for (int f = 0; f < F; ++f) {
+        memcpy(s.h_y + (size_t)f * h->n, s.reqs[f].y.data(), sizeof(float) * h->n);
+        s.h_sig[f] = s.reqs[f].sigma2 > 0.0f ? s.reqs[f].sigma2 : (float)h->sigma2;
+    }
+    float* dy = P<float>(s.ws.y);
+    float* dsig = P<float>(s.ws.sig);
+    uint8_t* dhat = P<uint8_t>(s.ws.hat);
+    int32_t* dit = P<int32_t>(s.ws.iters);
+    uint8_t* dok = P<uint8_t>(s.ws.ok);
+    JBP_CU(cudaMemcpyAsync(dy, s.h_y, sizeof(float) * (size_t)F * h->n, cudaMemcpyHostToDevice, s.stream), "serve copy y");
+    JBP_CU(cudaMemcpyAsync(dsig, s.h_sig, sizeof(float) * (size_t)F, cudaMemcpyHostToDevice, s.stream), "serve copy sigma2");
+    int rc = decode_device(h, s.ws, JBP_FORM_AUTO, F, dy, dhat, dit, dok, nullptr, dsig, s.stream);
     if (rc) return rc;
-    JBP_CU(cudaMemcpyAsync(s.h_hat, s.ws.hat, (size_t)F * h->K * h->n, cudaMemcpyDeviceToHost, s.stream), "serve copy hat");
-    JBP_CU(cudaMemcpyAsync(s.h_iters, s.ws.iters, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s.stream), "serve copy iters");
-    JBP_CU(cudaMemcpyAsync(s.h_ok, s.ws.ok, (size_t)F * h->K, cudaMemcpyDeviceToHost, s.stream), "serve copy ok");
+    JBP_CU(cudaMemcpyAsync(s.h_hat, dhat, (size_t)F * h->K * h->n, cudaMemcpyDeviceToHost, s.stream), "serve copy hat");
+    JBP_CU(cudaMemcpyAsync(s.h_iters, dit, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s.stream), "serve copy iters");
+    JBP_CU(cudaMemcpyAsync(s.h_ok, dok, (size_t)F * h->K, cudaMemcpyDeviceToHost, s.stream), "serve copy ok");
     JBP_CU(cudaEventRecord(s.done, s.stream), "serve event");
     return JBP_OK;
 }
@@ -744,10 +965,11 @@ static int slot_launch(jbp_ctx* ctx, Slot& s)
 static void server_main(jbp_ctx* ctx)
 {
     cudaSetDevice(ctx->device);
-    std::unique_lock<std::mutex> lk(ctx->mu);
+    std::vector<std::pair<uint64_t, Result>> finished;
+    std::vector<double> lat;
     while (true) {
         bool any_busy = false;
-        // (1) retire finished launches
+        // (1) retire finished launches: CUDA queries and copies outside the lock
         for (Slot& s : ctx->slots) {
             if (!s.busy) continue;
             cudaError_t q = cudaEventQuery(s.done);
@@ -757,48 +979,70 @@ static void server_main(jbp_ctx* ctx)
             }
             const double t = now_us();
             jbp_h* h = s.h;
+            finished.clear();
+            lat.clear();
             for (size_t f = 0; f < s.reqs.size(); ++f) {
                 Result r;
                 r.hat.assign(s.h_hat + f * h->K * h->n, s.h_hat + (f + 1) * h->K * h->n);
                 r.ok.assign(s.h_ok + f * h->K, s.h_ok + (f + 1) * h->K);
                 r.iters = q == cudaSuccess ? s.h_iters[f] : -1;
-                ctx->done[s.reqs[f].ticket] = std::move(r);
-                ctx->pending.erase(s.reqs[f].ticket);
-                ctx->latencies.push_back(t - s.reqs[f].t_submit);
-                ctx->completed++;
+                finished.emplace_back(s.reqs[f].ticket, std::move(r));
+                lat.push_back(t - s.reqs[f].t_submit);
             }
-            ctx->inflight_bytes -= s.state_bytes;
-            s.reqs.clear();
-            s.busy = false;
+            {
+                std::lock_guard<std::mutex> lk(ctx->mu);
+                for (auto& fr : finished) {
+                    ctx->done[fr.first] = std::move(fr.second);
+                    ctx->pending.erase(fr.first);
+                }
+                ctx->latencies.insert(ctx->latencies.end(), lat.begin(), lat.end());
+                ctx->completed += finished.size();
+                ctx->inflight_bytes -= s.state_bytes;
+                s.reqs.clear();
+                s.busy = false;
+            }
             ctx->cv_idle.notify_all();
         }
-        // (2) admit queued frames into free slots
-        while (!ctx->queue.empty()) {
+        // (2) admit queued frames into free slots: take the batch under the lock,
+        //     stage and launch outside it
+        while (true) {
             Slot* free_slot = nullptr;
-            for (Slot& s : ctx->slots)
-                if (!s.busy) { free_slot = &s; break; }
-            if (!free_slot) break;
-            jbp_h* h = ctx->queue.front().h;
-            const int64_t per_frame = state_bytes(h->graph()) + (int64_t)h->n * 4 + (int64_t)h->K * (h->n + 1) + 4;
+            jbp_h* h = nullptr;
             std::vector<Request> batch;
             int64_t bytes = 0;
-            for (auto it = ctx->queue.begin(); it != ctx->queue.end() && (int)batch.size() < kMaxServeBatch;) {
-                if (it->h == h && ctx->inflight_bytes + bytes + per_frame <= ctx->budget / 2) {
-                    bytes += per_frame;
-                    batch.push_back(std::move(*it));
-                    it = ctx->queue.erase(it);
-                } else {
-                    ++it;
+            {
+                std::lock_guard<std::mutex> lk(ctx->mu);
+                if (ctx->queue.empty()) break;
+                for (Slot& s : ctx->slots)
+                    if (!s.busy) {
+                        free_slot = &s;
+                        break;
+                    }
+                if (!free_slot) break;
+                h = ctx->queue.front().h;
+                const int64_t per_frame = state_bytes(h->graph()) + (int64_t)h->n * 4 + (int64_t)h->K * (h->n + 1) + 8;
+                for (auto it = ctx->queue.begin(); it != ctx->queue.end() && (int)batch.size() < kMaxServeBatch;) {
+                    if (it->h == h && ctx->inflight_bytes + bytes + per_frame <= ctx->budget / 2) {
+                        bytes += per_frame;
+                        batch.push_back(std::move(*it));
+                        it = ctx->queue.erase(it);
+                    } else {
+                        ++it;
+                    }
                 }
+                if (batch.empty()) break;   // over budget: wait for a launch to retire
+                free_slot->busy = true;
+                free_slot->h = h;
+                free_slot->reqs = std::move(batch);
+                free_slot->state_bytes = bytes;
+                ctx->inflight_bytes += bytes;
             }
-            if (batch.empty()) break;   // over budget: wait for a launch to retire
             Slot& s = *free_slot;
-            s.reqs = std::move(batch);
-            s.state_bytes = bytes;
             int rc = slot_prepare(ctx, s, h, (int)s.reqs.size());
             if (!rc) rc = slot_launch(ctx, s);
+            any_busy = true;
             if (rc) {
-                // publish the failure to each ticket
+                std::lock_guard<std::mutex> lk(ctx->mu);
                 for (const Request& r : s.reqs) {
                     Result res;
                     res.iters = -1;
@@ -808,28 +1052,29 @@ static void server_main(jbp_ctx* ctx)
                     ctx->pending.erase(r.ticket);
                 }
                 s.reqs.clear();
+                s.busy = false;
+                ctx->inflight_bytes -= s.state_bytes;
                 cudaGetLastError();
-                continue;
             }
-            s.busy = true;
-            any_busy = true;
-            ctx->inflight_bytes += bytes;
         }
-        if (ctx->stop && !any_busy) break;
+        std::unique_lock<std::mutex> lk(ctx->mu);
+        if (ctx->stop && !any_busy && ctx->queue.empty()) break;
         if (any_busy)
-            ctx->cv.wait_for(lk, std::chrono::microseconds(20));
+            ctx->cv.wait_for(lk, std::chrono::microseconds(50));
         else
             ctx->cv.wait(lk, [&] { return ctx->stop || !ctx->queue.empty(); });
     }
 }
 
-extern "C" int jbp_submit(jbp_h* h, const float* y_frame, uint64_t* ticket)
+extern "C" int jbp_submit(jbp_h* h, const float* y_frame, double sigma2, uint64_t* ticket)
 {
     if (!h || !y_frame || !ticket) return fail(JBP_EINVAL, "jbp_submit: NULL argument");
+    if (!std::isfinite(sigma2)) return fail(JBP_EINVAL, "jbp_submit: sigma2 not finite");
     jbp_ctx* ctx = h->ctx;
     Request r;
     r.h = h;
     r.y.assign(y_frame, y_frame + h->n);
+    r.sigma2 = (float)sigma2;
     r.t_submit = now_us();
     {
         std::lock_guard<std::mutex> lk(ctx->mu);

@@ -34,7 +34,7 @@ constexpr float kNegInf = -__builtin_inff();
 // Device view of one decoder: code, interleavers, channel and GF tables.
 struct Graph {
     int n, P, E, dc, dv, K, Q;
-    float inv_sigma2;
+    float inv_sigma2;         // 1 / noise variance of every frame, unless sigma2_f is set
     const int32_t* chk_var;   // [E]     variable of check-major edge e
     const uint8_t* chk_coef;  // [E]     H_{j,l} of edge e
     const int32_t* var_edge;  // [n*dv]  edges of variable i, ascending
@@ -45,7 +45,14 @@ struct Graph {
     const int32_t* pos_of;    // [K*n]   pos_of[k*n+i] = pi_k(i)                 (fused layout)
     const uint16_t* slot;     // [K*E]   pi_k(var of e)*2 + (e's rank in its var) (fused layout)
     int* tc_error;            // set to 1 if a tensor-core wait expired (may be null: FP32 only)
+    const float* sigma2_f;    // [F]     per-frame noise variance of this batch (may be null)
 };
+
+// 1 / sigma2 of frame f
+__device__ __forceinline__ float frame_inv_s2(const Graph& g, long f)
+{
+    return g.sigma2_f ? 1.0f / g.sigma2_f[f] : g.inv_sigma2;
+}
 
 __device__ __forceinline__ float* edge_ptr(float* blk, int e, int cbs, int Q)
 {
@@ -369,7 +376,7 @@ __device__ __forceinline__ void chan_reg(const float (&mu)[K][Q], const GaussTer
 // v2c_0 = ch2v * c2v_1, v2c_1 = ch2v * c2v_0, each rescaled to max 1).
 template <int K, int Q>
 __device__ __forceinline__ void chan_thread(const Graph& g, float* msg_f, size_t ustride, int cbs, float* ch2v_f,
-                                            float y, int u)
+                                            float y, float inv_s2, int u)
 {
     float mu[K][Q];
     int var[K];
@@ -386,7 +393,7 @@ __device__ __forceinline__ void chan_thread(const Graph& g, float* msg_f, size_t
 #pragma unroll
         for (int a = 0; a < Q; ++a) mu[k][a] = a0[a] * inv;
     }
-    const GaussTerm gt = gauss_term(y, K, Q, g.inv_sigma2);
+    const GaussTerm gt = gauss_term(y, K, Q, inv_s2);
     chan_reg<K, Q>(mu, gt, g.log_fallbacks, [&](int k, const float (&o)[Q]) {
         const int i = var[k];
         float* blk = msg_f + k * ustride;
@@ -453,8 +460,8 @@ __host__ __device__ __forceinline__ int chan_scratch_floats(int K, int Q)
 // res [K*Q] receives the final messages (max 1, floored).  Returns true
 // (team-uniform) if the linear pass underflowed; the caller reruns in LogSR.
 template <int Q, class SR>
-__device__ bool chan_trellis(const Graph& g, const float* msg_f, size_t ustride, int cbs, float y, int u,
-                             float* sc, float* res, TeamLane L)
+__device__ bool chan_trellis(const Graph& g, const float* msg_f, size_t ustride, int cbs, float y, float inv_s2,
+                             int u, float* sc, float* res, TeamLane L)
 {
     constexpr int T = Shape<Q>::T, V = Shape<Q>::V, D = Q - 1;
     const int K = g.K, S = K * D;
@@ -486,7 +493,7 @@ __device__ bool chan_trellis(const Graph& g, const float* msg_f, size_t ustride,
         for (int v = 0; v < V; ++v) mu[k * Q + v * T + L.tl] = SR::rescale(l[v], mx);
     }
 
-    const GaussTerm gt = gauss_term(y, K, Q, g.inv_sigma2);
+    const GaussTerm gt = gauss_term(y, K, Q, inv_s2);
     for (int s = L.tl; s <= S; s += T) B[s] = SR::kLog ? gt.expo(s) : __expf(gt.expo(s));
 
     for (int j = 1; j + 1 < K; ++j) {
@@ -551,6 +558,205 @@ __device__ bool chan_trellis(const Graph& g, const float* msg_f, size_t ustride,
         }
     }
     __syncwarp(L.mask);
+    return bad;
+}
+
+// -- team shape, register-blocked linear trellis -----------------------------
+//
+// The three trellis operations are correlations Y(o) = sum_t A(t) X(o + t + xoff)
+// (a prefix convolution is the correlation with the reversed message and
+// xoff = -(q-1)).  A team computes one with each lane owning kBR consecutive
+// outputs and, when there are fewer output blocks than lanes, a contiguous
+// chunk of the taps; the chunks' partial sums are combined with shuffles.  A
+// sliding window keeps the X values in registers, so a lane loads one X and
+// one A per tap for kBR multiply-adds.  kBR is odd: lanes start kBR words
+// apart, which maps the 32 lanes of a warp onto 32 distinct banks, and the tap
+// chunk length is odd for the same reason.  X arrays carry zero pads (BlkPad)
+// so that no load needs a bounds check.
+
+constexpr int kBR = 9;
+
+template <int Q>
+struct BlkPad {
+    static constexpr int L = Q;            // left zero pad (prefix convolutions read X(s - (q-1)))
+    static constexpr int R = Q + 48;       // right pad: convolution tails (zeros), block and window overrun
+};
+
+__host__ __device__ __forceinline__ int blk_pad(int Q) { return Q + Q + 48; }
+
+// Y(o) for o < L at Y[o]; A(t) at A[t] (t < NT; AREV: A(NT-1-t)); X(i) at X[i]
+// (i may run kBR + q beyond the data, into zero pads).  mode 0: rescale Y to
+// max 1; mode 1: normalise to max 1 and floor at kRelFloor.  Returns the team
+// max before scaling.
+template <int T, bool AREV>
+__device__ __noinline__ float team_corr(float* Y, int L, const float* A, int NT, const float* X, int xoff, int mode,
+                                        TeamLane Lr)
+{
+    const int nb = (L + kBR - 1) / kBR;
+    int C = 1;
+    while (C * 2 * nb <= T) C *= 2;
+    const int passes = (nb + T - 1) / T;  // only when C == 1 and nb > T
+    int tc = (NT + C - 1) / C;
+    if (C > 1) tc |= 1;
+    float mx_all = kNegInf;
+    for (int ps = 0; ps < passes; ++ps) {
+        const int ob = (C == 1) ? (Lr.tl + ps * T) : (Lr.tl / C);
+        const int c = (C == 1) ? 0 : (Lr.tl % C);
+        const bool active = ob < nb;
+        const int o0 = ob * kBR;
+        const int tb = min(NT, c * tc), te = min(NT, tb + tc);
+        float acc[kBR];
+#pragma unroll
+        for (int r = 0; r < kBR; ++r) acc[r] = 0.0f;
+        if (active && tb < te) {
+            float xw[2 * kBR];
+            const float* xp = X + o0 + tb + xoff;
+#pragma unroll
+            for (int i = 0; i < 2 * kBR - 1; ++i) xw[i] = xp[i];
+            const float* ap = AREV ? A + (NT - 1 - tb) : A + tb;
+            int t0 = tb;
+            // full groups of kBR taps
+            for (; t0 + kBR <= te; t0 += kBR) {
+#pragma unroll
+                for (int j = 0; j < kBR; ++j) {
+                    const float a = AREV ? ap[-(t0 - tb) - j] : ap[(t0 - tb) + j];
+#pragma unroll
+                    for (int r = 0; r < kBR; ++r) acc[r] = fmaf(a, xw[r + j], acc[r]);
+                }
+                if (t0 + kBR < te) {
+#pragma unroll
+                    for (int i = 0; i < kBR - 1; ++i) xw[i] = xw[i + kBR];
+                    const float* xn = xp + (t0 - tb) + 2 * kBR - 1;
+#pragma unroll
+                    for (int i = 0; i < kBR; ++i) xw[kBR - 1 + i] = xn[i];
+                }
+            }
+            // tail
+            if (t0 < te) {
+#pragma unroll
+                for (int j = 0; j < kBR; ++j) {
+                    if (t0 + j < te) {
+                        const float a = AREV ? ap[-(t0 - tb) - j] : ap[(t0 - tb) + j];
+#pragma unroll
+                        for (int r = 0; r < kBR; ++r) acc[r] = fmaf(a, xw[r + j], acc[r]);
+                    }
+                }
+            }
+        }
+        for (int off = 1; off < C; off <<= 1)
+#pragma unroll
+            for (int r = 0; r < kBR; ++r) acc[r] += __shfl_xor_sync(Lr.mask, acc[r], off, T);
+        float lmx = kNegInf;
+        if (active && c == 0) {
+#pragma unroll
+            for (int r = 0; r < kBR; ++r)
+                if (o0 + r < L) {
+                    lmx = fmaxf(lmx, acc[r]);
+                    Y[o0 + r] = acc[r];
+                }
+        }
+        mx_all = fmaxf(mx_all, lmx);
+    }
+    const float mx = team_max<T>(mx_all, Lr.mask);
+    __syncwarp(Lr.mask);
+    const float inv = mx > 0.0f ? 1.0f / mx : 0.0f;
+    for (int o = Lr.tl; o < L; o += T) Y[o] = mode ? fmaxf(Y[o] * inv, kRelFloor) : Y[o] * inv;
+    __syncwarp(Lr.mask);
+    return mx;
+}
+
+// Scratch of the blocked trellis (floats): mu[K*Q] | F_1..F_{K-1} (each with
+// zero pads) | B0, B1 (likewise) | res[K*Q].
+__host__ __device__ __forceinline__ int blk_arr_floats(int len, int Q) { return len + blk_pad(Q); }
+
+__host__ __device__ __forceinline__ int blk_prefix_offset(int j, int Q)
+{
+    const int D = Q - 1;
+    int f = 0;
+    for (int i = 1; i < j; ++i) f += blk_arr_floats(i * D + 1, Q);
+    return f;
+}
+
+__host__ __device__ __forceinline__ int blk_scratch_floats(int K, int Q)
+{
+    const int D = Q - 1, S = K * D;
+    return K * Q + blk_prefix_offset(K, Q) + 2 * blk_arr_floats(S + 1, Q) + K * Q;
+}
+
+// Zero a team's blocked-trellis scratch (the pads must read as zero).
+template <int T>
+__device__ __forceinline__ void blk_clear(float* sc, int floats, TeamLane Lr)
+{
+    for (int i = Lr.tl; i < floats; i += T) sc[i] = 0.0f;
+    __syncwarp(Lr.mask);
+}
+
+// Team-shape channel messages of use u, linear domain, register-blocked.
+// Same quantity as chan_trellis<Q, LinSR>; res [K*Q] gets the final messages.
+// Returns true if the pass underflowed (the caller reruns in log space and then
+// clears the scratch again).
+template <int Q>
+__device__ bool chan_blocked(const Graph& g, const float* msg_f, size_t ustride, int cbs, float y, float inv_s2, int u,
+                             float* sc, float* res, TeamLane Lr)
+{
+    constexpr int T = Shape<Q>::T, V = Shape<Q>::V, D = Q - 1, PL = BlkPad<Q>::L;
+    const int K = g.K, S = K * D;
+    float* mu = sc;
+    float* Fb = mu + K * Q;                               // F_j data at Fb + blk_prefix_offset(j) + PL
+    float* B = Fb + blk_prefix_offset(K, Q) + PL;         // data pointers (pads before and after)
+    float* Bn = B + blk_arr_floats(S + 1, Q);
+    bool bad = false;
+    for (int k = 0; k < K; ++k) {
+        const int i = g.use_pos[k * g.n + u];
+        const float* blk = msg_f + k * ustride;
+        float l[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) l[v] = 1.0f;
+        for (int d = 0; d < g.dv; ++d) {
+            const float* m = edge_ptr(blk, g.var_edge[i * g.dv + d], cbs, Q);
+#pragma unroll
+            for (int v = 0; v < V; ++v) l[v] *= m[v * T + Lr.tl];
+        }
+        float mx = l[0];
+#pragma unroll
+        for (int v = 1; v < V; ++v) mx = fmaxf(mx, l[v]);
+        mx = team_max<T>(mx, Lr.mask);
+        const float inv = 1.0f / mx;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int a = v * T + Lr.tl;
+            mu[k * Q + a] = l[v] * inv;
+            if (k == 0) Fb[PL + a] = l[v] * inv;   // F_1 = mu_0, padded copy
+        }
+    }
+    const GaussTerm gt = gauss_term(y, K, Q, inv_s2);
+    for (int s = Lr.tl; s <= S; s += T) B[s] = __expf(gt.expo(s));
+    __syncwarp(Lr.mask);
+    for (int j = 1; j + 1 < K; ++j) {
+        const float m = team_corr<T, true>(Fb + blk_prefix_offset(j + 1, Q) + PL, (j + 1) * D + 1, mu + j * Q, Q,
+                                           Fb + blk_prefix_offset(j, Q) + PL, -(Q - 1), 0, Lr);
+        if (!(m > 0.0f)) bad = true;
+    }
+    for (int k = K - 1; k >= 0; --k) {
+        if (k == 0) {
+            float mx = kNegInf;
+            for (int a = Lr.tl; a < Q; a += T) mx = fmaxf(mx, B[a]);
+            mx = team_max<T>(mx, Lr.mask);
+            if (!(mx >= kFallbackMax)) bad = true;
+            const float inv = mx > 0.0f ? 1.0f / mx : 0.0f;
+            for (int a = Lr.tl; a < Q; a += T) res[a] = fmaxf(B[a] * inv, kRelFloor);
+            __syncwarp(Lr.mask);
+        } else {
+            const float* Fk = Fb + blk_prefix_offset(k, Q) + PL;
+            const float m = team_corr<T, false>(res + k * Q, Q, Fk, k * D + 1, B, 0, 1, Lr);
+            if (!(m >= kFallbackMax)) bad = true;
+            const float m2 = team_corr<T, false>(Bn, k * D + 1, mu + k * Q, Q, B, 0, 0, Lr);
+            if (!(m2 > 0.0f)) bad = true;
+            float* t = B;
+            B = Bn;
+            Bn = t;
+        }
+    }
     return bad;
 }
 
@@ -890,7 +1096,8 @@ __device__ __forceinline__ void sstore(float* base, const float (&v)[Q])
 // Channel node of use p, thread shape, position-major layout.  msg_f / ch2v_f:
 // the frame's blocks; NB = ceil(n / 32).
 template <int K, int Q>
-__device__ __forceinline__ void chan_thread_pos(const Graph& g, float* msg_f, float* ch2v_f, int NB, float y, int p)
+__device__ __forceinline__ void chan_thread_pos(const Graph& g, float* msg_f, float* ch2v_f, int NB, float y,
+                                                float inv_s2, int p)
 {
     float mu[K][Q];
 #pragma unroll
@@ -905,7 +1112,7 @@ __device__ __forceinline__ void chan_thread_pos(const Graph& g, float* msg_f, fl
 #pragma unroll
         for (int a = 0; a < Q; ++a) mu[k][a] = a0[a] * inv;
     }
-    const GaussTerm gt = gauss_term(y, K, Q, g.inv_sigma2);
+    const GaussTerm gt = gauss_term(y, K, Q, inv_s2);
     chan_reg<K, Q>(mu, gt, g.log_fallbacks, [&](int k, const float (&o)[Q]) {
         const int row = (k * NB + (p >> 5)) * 2;
         sstore<Q>(ch2v_f + pos_vec<Q>(k * NB + (p >> 5), p), o);
@@ -929,6 +1136,101 @@ __device__ __forceinline__ void chan_thread_pos(const Graph& g, float* msg_f, fl
         sstore<Q>(p0, c0);
         sstore<Q>(p1, c1);
     });
+}
+
+// Channel node of use p for K = 4 split over a pair of lanes (lanes 2m, 2m+1 of
+// a warp; `half` = lane & 1, `mask` = the pair's lanes).  Lane h owns users
+// 2h and 2h+1: it forms P_own = mu_{2h} (*) mu_{2h+1}, receives the other
+// half's pair convolution by shuffles, scores it against G (the suffix H), and
+// emits its users' messages sum_b mu_{2h+1}(b) H(a+b) and sum_b mu_{2h}(b) H(a+b).
+// Each lane does half of the single-thread work with about half the registers.
+template <int Q>
+__device__ __forceinline__ void chan_pair_pos(const Graph& g, float* msg_f, float* ch2v_f, int NB, float y,
+                                              float inv_s2, int p, int half, unsigned mask)
+{
+    constexpr int D = Q - 1, K = 4;
+    float mu[2][Q];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int k = 2 * half + j;
+        const int row = (k * NB + (p >> 5)) * 2;
+        float a0[Q], a1[Q];
+        sload<Q>(msg_f + pos_vec<Q>(row, p), a0);
+        sload<Q>(msg_f + pos_vec<Q>(row + 1, p), a1);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) a0[a] *= a1[a];
+        const float inv = 1.0f / vmax(a0);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) mu[j][a] = a0[a] * inv;
+    }
+    float Po[2 * D + 1];
+    {
+        float Pown[2 * D + 1];
+        rconv(mu[0], mu[1], Pown);
+#pragma unroll
+        for (int i = 0; i < 2 * D + 1; ++i) Po[i] = __shfl_xor_sync(mask, Pown[i], 1);
+    }
+    const GaussTerm gt = gauss_term(y, K, Q, inv_s2);
+    float H[2 * D + 1];
+    rcorr_g<2 * D + 1, 2 * D + 1>(Po, H, gt);
+    float o[2][Q];
+    rcorr(mu[1], H, o[0]);   // message to user 2h
+    rcorr(mu[0], H, o[1]);   // message to user 2h+1
+    float mx[2];
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        mx[j] = vmax(o[j]);
+        bad = bad || !(mx[j] >= kFallbackMax);
+    }
+    // the log-space recomputation needs all four incoming messages: pair-uniform
+    const bool pair_bad = __shfl_xor_sync(mask, bad ? 1 : 0, 1) || bad;
+    if (pair_bad) {
+        float mu4[K][Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const float x0 = __shfl_xor_sync(mask, mu[0][a], 1), x1 = __shfl_xor_sync(mask, mu[1][a], 1);
+            mu4[2 * half][a] = mu[0][a];
+            mu4[2 * half + 1][a] = mu[1][a];
+            mu4[2 * (1 - half)][a] = x0;
+            mu4[2 * (1 - half) + 1][a] = x1;
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+            if (!(mx[j] >= kFallbackMax)) {
+                if (g.log_fallbacks) atomicAdd(g.log_fallbacks, 1ull);
+                chan_user_log<K, Q>(mu4, 2 * half + j, gt, o[j]);
+                mx[j] = 1.0f;
+            }
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float inv = 1.0f / mx[j];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) o[j][a] = fmaxf(o[j][a] * inv, kRelFloor);
+        const int k = 2 * half + j;
+        const int row = (k * NB + (p >> 5)) * 2;
+        sstore<Q>(ch2v_f + pos_vec<Q>(k * NB + (p >> 5), p), o[j]);
+        float* p0 = msg_f + pos_vec<Q>(row, p);
+        float* p1 = msg_f + pos_vec<Q>(row + 1, p);
+        float c0[Q], c1[Q];
+        sload<Q>(p0, c0);
+        sload<Q>(p1, c1);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const float t = c0[a];
+            c0[a] = o[j][a] * c1[a];
+            c1[a] = o[j][a] * t;
+        }
+        const float i0 = 1.0f / vmax(c0), i1 = 1.0f / vmax(c1);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            c0[a] *= i0;
+            c1[a] *= i1;
+        }
+        sstore<Q>(p0, c0);
+        sstore<Q>(p1, c1);
+    }
 }
 
 // Index h^{-1} x for every x from the images of the basis vectors: multiplying

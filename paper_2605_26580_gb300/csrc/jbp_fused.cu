@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(kFusedMaxThreads) k_fused(Graph g, int F, int 
         s_mul[i] = g.gf_mul[i];
         s_div[i] = g.gf_div[i];
     }
+    if constexpr (KC == 0) blk_clear<T>(sc, scf, L);
 
     const int groups = (F + G - 1) / G;
     for (int grp = blockIdx.x; grp < groups; grp += gridDim.x) {
@@ -99,17 +100,19 @@ __global__ void __launch_bounds__(kFusedMaxThreads) k_fused(Graph g, int F, int 
                 for (int unit = threadIdx.x; unit < gc * n; unit += blockDim.x) {
                     const int gi = unit / n, u = unit % n;
                     if (!s_active[gi]) continue;
-                    chan_thread<KC, Q>(g, s_msg + gi * fs, us, cbs, s_ch2v + gi * vs, s_y[gi * n + u], u);
+                    chan_thread<KC, Q>(g, s_msg + gi * fs, us, cbs, s_ch2v + gi * vs, s_y[gi * n + u],
+                                       frame_inv_s2(g, f0 + gi), u);
                 }
             } else {
                 for (int unit = team; unit < gc * n; unit += teams) {
                     const int gi = unit / n, u = unit % n;
                     if (!s_active[gi]) continue;
                     float* msg_f = s_msg + gi * fs;
-                    const float yv = s_y[gi * n + u];
-                    if (chan_trellis<Q, LinSR>(g, msg_f, us, cbs, yv, u, sc, res, L)) {
+                    const float yv = s_y[gi * n + u], is2 = frame_inv_s2(g, f0 + gi);
+                    if (chan_blocked<Q>(g, msg_f, us, cbs, yv, is2, u, sc, res, L)) {
                         if (g.log_fallbacks && L.tl == 0) atomicAdd(g.log_fallbacks, 1ull);
-                        chan_trellis<Q, LogSR>(g, msg_f, us, cbs, yv, u, sc, res, L);
+                        chan_trellis<Q, LogSR>(g, msg_f, us, cbs, yv, is2, u, sc, res, L);
+                        blk_clear<T>(sc, scf - K * Q, L);
                     }
                     chan_write_team<Q>(g, msg_f, us, cbs, s_ch2v + gi * vs, res, u, L);
                 }
@@ -215,8 +218,13 @@ __host__ __device__ inline PosLayout pos_layout(const Graph& g, int G)
     return L;
 }
 
-template <int Q, int KC>
-__global__ void __launch_bounds__(kFusedMaxThreads) k_fused_pos(Graph g, int F, int G, const float* __restrict__ y,
+// PAIR (K = 4 only): each channel use split over a lane pair, up to 512 threads
+// (128 registers); otherwise one thread per channel use, up to 256 threads.
+template <int Q, int KC, bool PAIR>
+constexpr int pos_max_threads() { return PAIR ? 512 : kFusedMaxThreads; }
+
+template <int Q, int KC, bool PAIR = false>
+__global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Graph g, int F, int G, const float* __restrict__ y,
                                                                 int T_it, int early_stop, uint8_t* hat,
                                                                 int32_t* iters, uint8_t* ok, float* logpost)
 {
@@ -255,10 +263,22 @@ __global__ void __launch_bounds__(kFusedMaxThreads) k_fused_pos(Graph g, int F, 
 
         for (int t = 1; t <= T_it; ++t) {
             // (A) channel nodes, v2c in place
-            for (int unit = threadIdx.x; unit < gc * n; unit += blockDim.x) {
-                const int gi = unit / n, p = unit % n;
-                if (!s_active[gi]) continue;
-                chan_thread_pos<K, Q>(g, s_msg + gi * fs, s_ch2v + gi * vs, NB, s_y[gi * NB * 32 + p], p);
+            if constexpr (PAIR && K == 4) {
+                const int half = threadIdx.x & 1;
+                const unsigned pmask = 3u << (threadIdx.x & 30);
+                for (int unit = threadIdx.x >> 1; unit < gc * n; unit += blockDim.x >> 1) {
+                    const int gi = unit / n, p = unit % n;
+                    if (!s_active[gi]) continue;
+                    chan_pair_pos<Q>(g, s_msg + gi * fs, s_ch2v + gi * vs, NB, s_y[gi * NB * 32 + p],
+                                     frame_inv_s2(g, f0 + gi), p, half, pmask);
+                }
+            } else {
+                for (int unit = threadIdx.x; unit < gc * n; unit += blockDim.x) {
+                    const int gi = unit / n, p = unit % n;
+                    if (!s_active[gi]) continue;
+                    chan_thread_pos<K, Q>(g, s_msg + gi * fs, s_ch2v + gi * vs, NB, s_y[gi * NB * 32 + p],
+                                          frame_inv_s2(g, f0 + gi), p);
+                }
             }
             __syncthreads();
             // (B) check nodes
@@ -319,11 +339,9 @@ __global__ void __launch_bounds__(kFusedMaxThreads) k_fused_pos(Graph g, int F, 
     }
 }
 
-template <int Q, int KC>
-bool plan_pos(const Graph& g, const DeviceInfo& di, int F, int threads_hint, int fpc_hint, FusedPlan* plan)
+template <int Q, int KC, bool PAIR>
+bool plan_pos_v(const Graph& g, const DeviceInfo& di, int F, int threads, int fpc_hint, FusedPlan* plan)
 {
-    int threads = threads_hint > 0 ? threads_hint : 256;
-    threads = std::max(32, std::min(kFusedMaxThreads, threads / 32 * 32));
     int Gmax = 0;
     for (int G = 1; G <= 4096; ++G) {
         if (pos_layout(g, G).total + kStaticSmemMargin > (size_t)di.smem_optin) break;
@@ -335,10 +353,11 @@ bool plan_pos(const Graph& g, const DeviceInfo& di, int F, int threads_hint, int
     plan->frames_per_cta = G;
     plan->threads = threads;
     plan->smem_bytes = (int)pos_layout(g, G).total;
+    plan->variant = PAIR ? 1 : 0;
     int occ = 0;
-    if (cudaFuncSetAttribute(k_fused_pos<Q, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, plan->smem_bytes) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_pos<Q, KC>, threads, plan->smem_bytes) !=
+    if (cudaFuncSetAttribute(k_fused_pos<Q, KC, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             plan->smem_bytes) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_pos<Q, KC, PAIR>, threads, plan->smem_bytes) !=
             cudaSuccess ||
         occ < 1)
         return false;
@@ -346,22 +365,46 @@ bool plan_pos(const Graph& g, const DeviceInfo& di, int F, int threads_hint, int
     return true;
 }
 
+// Launch shape: threads_hint > 256 selects the lane-pair channel (K = 4); the
+// default is one thread per channel use at 256 threads.
+template <int Q, int KC>
+bool plan_pos(const Graph& g, const DeviceInfo& di, int F, int threads_hint, int fpc_hint, FusedPlan* plan)
+{
+    int threads = threads_hint > 0 ? threads_hint : kFusedMaxThreads;
+    threads = std::max(64, std::min(512, threads / 64 * 64));
+    if constexpr (KC == 4) {
+        if (threads > kFusedMaxThreads) return plan_pos_v<Q, KC, true>(g, di, F, threads, fpc_hint, plan);
+    }
+    return plan_pos_v<Q, KC, false>(g, di, F, std::min(threads, kFusedMaxThreads), fpc_hint, plan);
+}
+
+template <int Q, int KC, bool PAIR>
+cudaError_t fused_pos_v(const Graph& g, const FusedPlan& p, int F, const float* y, int T_it, int early_stop,
+                        uint8_t* hat, int32_t* iters, uint8_t* ok, float* post, cudaStream_t s)
+{
+    cudaError_t e =
+        cudaFuncSetAttribute(k_fused_pos<Q, KC, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem_bytes);
+    if (e != cudaSuccess) return e;
+    k_fused_pos<Q, KC, PAIR><<<p.grid, p.threads, p.smem_bytes, s>>>(g, F, p.frames_per_cta, y, T_it, early_stop,
+                                                                      hat, iters, ok, post);
+    return cudaGetLastError();
+}
+
 template <int Q, int KC>
 cudaError_t fused_pos(const Graph& g, const FusedPlan& p, int F, const float* y, int T_it, int early_stop,
                       uint8_t* hat, int32_t* iters, uint8_t* ok, float* post, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_fused_pos<Q, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem_bytes);
-    if (e != cudaSuccess) return e;
-    k_fused_pos<Q, KC><<<p.grid, p.threads, p.smem_bytes, s>>>(g, F, p.frames_per_cta, y, T_it, early_stop, hat,
-                                                                iters, ok, post);
-    return cudaGetLastError();
+    if constexpr (KC == 4) {
+        if (p.variant == 1) return fused_pos_v<Q, KC, true>(g, p, F, y, T_it, early_stop, hat, iters, ok, post, s);
+    }
+    return fused_pos_v<Q, KC, false>(g, p, F, y, T_it, early_stop, hat, iters, ok, post, s);
 }
 
 template <int Q, int KC>
 bool plan_qk(const Graph& g, const DeviceInfo& di, int F, int threads_hint, int fpc_hint, FusedPlan* plan)
 {
     constexpr int T = Shape<Q>::T;
-    const int scf = chan_scratch_floats(g.K, Q);
+    const int scf = blk_scratch_floats(g.K, Q);
     int threads = threads_hint > 0 ? threads_hint : 256;
     threads = std::max(32, std::min(kFusedMaxThreads, threads / 32 * 32));
     for (; threads >= 32; threads -= 32) {
@@ -399,7 +442,7 @@ cudaError_t fused_qk(const Graph& g, const FusedPlan& p, int F, const float* y, 
     cudaError_t e = cudaFuncSetAttribute(k_fused<Q, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem_bytes);
     if (e != cudaSuccess) return e;
     k_fused<Q, KC><<<p.grid, p.threads, p.smem_bytes, s>>>(g, F, p.frames_per_cta, y, T_it, early_stop, hat, iters,
-                                                            ok, post, chan_scratch_floats(g.K, Q));
+                                                            ok, post, blk_scratch_floats(g.K, Q));
     return cudaGetLastError();
 }
 

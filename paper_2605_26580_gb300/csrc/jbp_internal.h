@@ -47,6 +47,7 @@ struct FusedPlan {
     int threads;          // threads per CTA
     int smem_bytes;       // dynamic shared memory per CTA
     int grid;             // CTAs launched (persistent)
+    int variant = 0;      // kernel variant (fused position-major: 1 = lane-pair channel)
 };
 bool fused_plan(const Graph& g, const DeviceInfo& di, int F, int threads_hint, int fpc_hint,
                 FusedPlan* plan);

@@ -184,6 +184,7 @@ extern "C" int jbp_decode_noalloc(const jbp_code* code, int32_t K, const jbp_cha
     g.pos_of = nullptr;
     g.slot = nullptr;
     g.tc_error = nullptr;
+    g.sigma2_f = nullptr;
     float* msg = reinterpret_cast<float*>(D + o_msg);
     float* ch2v = reinterpret_cast<float*>(D + o_ch2v);
     uint8_t* active = D + o_act;

@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(kStepThreads) k_channel_thread(Graph g, int F,
     for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
         const int f = (int)(t / g.n), u = (int)(t % g.n);
         if (active && !active[f]) continue;
-        chan_thread<KC, Q>(g, msg + f * fs, us, 4 * Q, ch2v + f * vs, y[(size_t)f * g.n + u], u);
+        chan_thread<KC, Q>(g, msg + f * fs, us, 4 * Q, ch2v + f * vs, y[(size_t)f * g.n + u], frame_inv_s2(g, f), u);
     }
 }
 
@@ -65,14 +65,16 @@ __global__ void __launch_bounds__(kStepThreads) k_channel_team(Graph g, int F, c
     const TeamLane L = team_lane<T>();
     const long total = (long)F * g.n;
     const size_t us = (size_t)g.E * Q, fs = (size_t)g.K * us, vs = (size_t)g.K * g.n * Q;
+    blk_clear<T>(sc, sc_floats, L);
     for (long unit = (long)blockIdx.x * teams + team; unit < total; unit += (long)gridDim.x * teams) {
         const int f = (int)(unit / g.n), u = (int)(unit % g.n);
         if (active && !active[f]) continue;
         float* msg_f = msg + f * fs;
-        const float yv = y[(size_t)f * g.n + u];
-        if (chan_trellis<Q, LinSR>(g, msg_f, us, 4 * Q, yv, u, sc, res, L)) {
+        const float yv = y[(size_t)f * g.n + u], is2 = frame_inv_s2(g, f);
+        if (chan_blocked<Q>(g, msg_f, us, 4 * Q, yv, is2, u, sc, res, L)) {
             if (g.log_fallbacks && L.tl == 0) atomicAdd(g.log_fallbacks, 1ull);
-            chan_trellis<Q, LogSR>(g, msg_f, us, 4 * Q, yv, u, sc, res, L);
+            chan_trellis<Q, LogSR>(g, msg_f, us, 4 * Q, yv, is2, u, sc, res, L);
+            blk_clear<T>(sc, sc_floats - g.K * Q, L);
         }
         chan_write_team<Q>(g, msg_f, us, 4 * Q, ch2v + f * vs, res, u, L);
     }
@@ -177,7 +179,7 @@ cudaError_t channel_team_q(const Graph& g, const DeviceInfo& di, int F, const fl
                            const uint8_t* active, cudaStream_t s)
 {
     constexpr int T = Shape<Q>::T;
-    const int scf = chan_scratch_floats(g.K, Q);
+    const int scf = blk_scratch_floats(g.K, Q);
     const size_t per_team = (size_t)scf * sizeof(float);
     int threads = kStepThreads;
     while (threads > 32 && (size_t)(threads / T) * per_team > (size_t)di.smem_optin) threads -= 32;

@@ -185,8 +185,11 @@ def _encoder(code: dict) -> dict:
     return {"rank": rank, "k": k, "info_pos": info.astype(np.int32), "gen_bits": G}
 
 
-def encode(code: dict, info: np.ndarray) -> np.ndarray:
-    """Codewords [..., n] (uint8) for information symbols [..., k]."""
+def encode(code: dict, info: np.ndarray, device=None) -> np.ndarray:
+    """Codewords [..., n] (uint8) for information symbols [..., k].
+
+    The 0/1 matrix product is exact in float32 (sums < 2^24) on any device;
+    device = a torch device runs it there (the result is identical)."""
     m, n, k = code["m"], code["n"], code["k"]
     shape = info.shape[:-1]
     flat = np.asarray(info, dtype=np.int64).reshape(-1, k)
@@ -195,6 +198,14 @@ def encode(code: dict, info: np.ndarray) -> np.ndarray:
     weights = (1 << np.arange(m)).astype(np.int64)
     G = code["gen_bits"]
     step = 16384
+    if device is not None:
+        import torch
+        Gd = torch.from_numpy(G).to(device)
+        wd = torch.from_numpy(weights).to(device)
+        for s in range(0, flat.shape[0], step):
+            cb = (torch.from_numpy(bits[s:s + step]).to(device) @ Gd).to(torch.int64) & 1
+            out[s:s + step] = (cb.reshape(-1, n, m) * wd).sum(-1).to(torch.uint8).cpu().numpy()
+        return out.reshape(*shape, n)
     for s in range(0, flat.shape[0], step):
         cb = (bits[s:s + step] @ G).astype(np.int64) & 1   # exact: 0/1 sums < 2^24
         out[s:s + step] = (cb.reshape(-1, n, m) * weights).sum(-1).astype(np.uint8)
@@ -220,22 +231,24 @@ def sigma2_from_snr(q: int, snr_db: float) -> float:
     return es(q) * 10.0 ** (-snr_db / 10.0)
 
 
-def channel_output(q: int, c: np.ndarray, perm: np.ndarray, snr_db: float, seed: int,
+def channel_output(q: int, c: np.ndarray, perm: np.ndarray, snr_db, seed: int,
                    noiseless: bool = False) -> tuple[np.ndarray, float]:
-    """y [F, n] float32 of codewords c [F, K, n] through the PAM-sum channel."""
+    """y [F, n] float32 of codewords c [F, K, n] through the PAM-sum channel.
+    snr_db: a scalar or one value per frame (then sigma2 is returned per frame)."""
     F, K, n = c.shape
-    sigma2 = sigma2_from_snr(q, snr_db)
+    sigma2 = sigma2_from_snr(q, np.asarray(snr_db, dtype=np.float64)) if np.ndim(snr_db) else sigma2_from_snr(q, snr_db)
     y = np.zeros((F, n), dtype=np.float64)
     for k in range(K):
         y[:, perm[k]] += 2.0 * c[:, k, :].astype(np.float64) - (q - 1)
     if not noiseless:
         rng = np.random.Generator(np.random.PCG64(seed))
-        y += rng.standard_normal((F, n)) * math.sqrt(sigma2)
+        scale = np.sqrt(sigma2)[:, None] if np.ndim(sigma2) else math.sqrt(sigma2)
+        y += rng.standard_normal((F, n)) * scale
     return y.astype(np.float32), sigma2
 
 
 def make_frames(code: dict, K: int, snr_db: float, F: int, seed: int, interleave: bool = True,
-                noiseless: bool = False, perm_seed: int | None = None) -> dict:
+                noiseless: bool = False, perm_seed: int | None = None, device=None) -> dict:
     """F frames of K users: uniform info symbols, codewords, channel output y (float32).
 
     Streams: info symbols from PCG64(seed), interleavers from PCG64(perm_seed or
@@ -243,7 +256,7 @@ def make_frames(code: dict, K: int, snr_db: float, F: int, seed: int, interleave
     q, n = code["q"], code["n"]
     rng = np.random.Generator(np.random.PCG64(seed))
     info = rng.integers(0, q, size=(F, K, code["k"]), dtype=np.int64)
-    c = encode(code, info)                                   # [F, K, n]
+    c = encode(code, info, device)                           # [F, K, n]
     pi = make_interleavers(n, K, seed if perm_seed is None else perm_seed, interleave)
     y, sigma2 = channel_output(q, c, pi, snr_db, seed + 1, noiseless)
     return {"c": c, "y": y, "sigma2": sigma2, "perm": pi, "snr_db": snr_db, "K": K,

@@ -23,7 +23,7 @@ FORM_AUTO, FORM_FUSED, FORM_STEP, FORM_PLAIN = 0, 1, 2, 3
 EXPORTS = [
     "jbp_context_create", "jbp_context_destroy", "jbp_create", "jbp_destroy", "jbp_decode",
     "jbp_submit", "jbp_poll", "jbp_serving_stats", "jbp_last_error", "jbp_step_channel",
-    "jbp_step_check", "jbp_step_var", "jbp_step_syndrome", "jbp_query", "jbp_decode_noalloc", "jbp_stats",
+    "jbp_step_check", "jbp_step_var", "jbp_step_syndrome", "jbp_query", "jbp_decode_noalloc", "jbp_stats", "jbp_decode_many", "jbp_tune",
 ]
 
 
@@ -50,7 +50,7 @@ class Options(C.Structure):
 class Batch(C.Structure):
     _fields_ = [("F", C.c_int32), ("y", C.c_void_p), ("hat", C.c_void_p), ("iters", C.c_void_p),
                 ("ok", C.c_void_p), ("logpost", C.c_void_p), ("on_device", C.c_int32), ("form", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("sigma2", C.c_void_p)]
 
 
 _lib = None
@@ -72,7 +72,7 @@ def lib():
             L.jbp_create.argtypes = [vp, C.POINTER(Code), i32, i32, C.POINTER(Channel), C.POINTER(vp)]
             L.jbp_destroy.argtypes = [vp]
             L.jbp_decode.argtypes = [vp, C.POINTER(Batch)]
-            L.jbp_submit.argtypes = [vp, vp, C.POINTER(u64)]
+            L.jbp_submit.argtypes = [vp, vp, C.c_double, C.POINTER(u64)]
             L.jbp_poll.argtypes = [vp, u64, vp, vp, vp]
             L.jbp_serving_stats.argtypes = [vp, C.POINTER(u64), C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.jbp_last_error.restype = C.c_char_p
@@ -81,6 +81,8 @@ def lib():
             L.jbp_step_var.argtypes = [vp, i32, vp, vp, vp, vp, vp]
             L.jbp_step_syndrome.argtypes = [vp, i32, vp, vp, vp]
             L.jbp_query.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]
+            L.jbp_decode_many.argtypes = [vp, i32, C.POINTER(vp), C.POINTER(Batch), vp]
+            L.jbp_tune.argtypes = [vp, C.POINTER(Batch), C.POINTER(i32), C.POINTER(i32)]
             L.jbp_stats.argtypes = [vp, C.POINTER(u64), C.POINTER(i32)]
             L.jbp_decode_noalloc.argtypes = [C.POINTER(Code), i32, C.POINTER(Channel), i32, i32, i32, vp, vp, vp,
                                              vp, vp]
@@ -138,6 +140,18 @@ class Context:
         check(rc)
         return {"hat": hat, "iters": int(it[0]), "ok": ok}
 
+    def decode_many(self, parts, stream=None):
+        """parts: list of (Decoder, y, hat, iters, ok[, sigma2]) device tensors; one call."""
+        n = len(parts)
+        hs = (C.c_void_p * n)(*[p[0].ptr for p in parts])
+        bs = (Batch * n)()
+        for i, p in enumerate(parts):
+            dec, y, hat, it, ok = p[:5]
+            sig = p[5] if len(p) > 5 else None
+            bs[i] = Batch(int(y.shape[0]), _addr(y), _addr(hat), _addr(it), _addr(ok), None, 1, FORM_AUTO, None,
+                          _addr(sig))
+        check(lib().jbp_decode_many(self.ptr, n, hs, bs, _stream_ptr(stream)))
+
     def serving_stats(self):
         c = C.c_uint64()
         a, b = C.c_double(), C.c_double()
@@ -185,30 +199,43 @@ class Decoder:
         return v.value
 
     # -- whole decodes --------------------------------------------------------
-    def decode(self, y, form: int = FORM_AUTO, want_post: bool = False):
-        """Host decode: y numpy [F, n] float32 -> dict of numpy outputs."""
+    def decode(self, y, form: int = FORM_AUTO, want_post: bool = False, sigma2=None):
+        """Host decode: y numpy [F, n] float32 -> dict of numpy outputs.  sigma2:
+        optional per-frame noise variance [F]."""
         y = np.ascontiguousarray(y, dtype=np.float32)
+        sig = None if sigma2 is None else np.ascontiguousarray(sigma2, dtype=np.float32)
         F = y.shape[0]
         out = {"hat": np.empty((F, self.K, self.n), dtype=np.uint8), "iters": np.empty((F,), dtype=np.int32),
                "ok": np.empty((F, self.K), dtype=np.uint8)}
         if want_post:
             out["post"] = np.empty((F, self.K, self.n, self.q), dtype=np.float32)
         b = Batch(F, _addr(y), _addr(out["hat"]), _addr(out["iters"]), _addr(out["ok"]), _addr(out.get("post")),
-                  0, int(form), None)
+                  0, int(form), None, _addr(sig))
         check(lib().jbp_decode(self.ptr, C.byref(b)))
         return out
 
-    def decode_device(self, y, hat, iters, ok, post=None, form: int = FORM_AUTO, stream=None):
+    def decode_device(self, y, hat, iters, ok, post=None, form: int = FORM_AUTO, stream=None, sigma2=None):
         """Enqueue a decode on device tensors (returns without waiting)."""
         b = Batch(int(y.shape[0]), _addr(y), _addr(hat), _addr(iters), _addr(ok), _addr(post), 1, int(form),
-                  _stream_ptr(stream))
+                  _stream_ptr(stream), _addr(sigma2))
         check(lib().jbp_decode(self.ptr, C.byref(b)))
 
+    def set_launch(self, threads: int, frames_per_cta: int = 0):
+        th, fc = C.c_int32(threads), C.c_int32(frames_per_cta)
+        check(lib().jbp_tune(self.ptr, None, C.byref(th), C.byref(fc)))
+
+    def tune(self, y, hat, iters, ok, sigma2=None, stream=None):
+        b = Batch(int(y.shape[0]), _addr(y), _addr(hat), _addr(iters), _addr(ok), None, 1, FORM_AUTO,
+                  _stream_ptr(stream), _addr(sigma2))
+        th, fc = C.c_int32(), C.c_int32()
+        check(lib().jbp_tune(self.ptr, C.byref(b), C.byref(th), C.byref(fc)))
+        return th.value, fc.value
+
     # -- serving --------------------------------------------------------------
-    def submit(self, y_frame) -> int:
+    def submit(self, y_frame, sigma2: float = 0.0) -> int:
         y = np.ascontiguousarray(y_frame, dtype=np.float32).reshape(-1)
         t = C.c_uint64()
-        check(lib().jbp_submit(self.ptr, _addr(y), C.byref(t)))
+        check(lib().jbp_submit(self.ptr, _addr(y), float(sigma2), C.byref(t)))
         return t.value
 
     # -- single steps on device tensors ---------------------------------------

@@ -329,3 +329,110 @@ def test_decode_precision_variants(env, prec):
           % (prec, ser_g, ser_o, int((diff & (ref["margin"] > 1e-3)).sum())))
     if prec == 3:
         assert not (diff & (ref["margin"] > 1e-3)).any()
+
+
+def test_per_frame_noise_variance_matches_oracle(env):
+    """jbp_batch.sigma2: each frame decoded with its own SNR equals the oracle run
+    at that SNR."""
+    jbp, O, torch = env
+    code = I.make_code(64, 4)
+    snrs = [9.0, 12.0, 15.0]
+    parts = [I.make_frames(code, 2, s, 20, seed=300 + i, perm_seed=300) for i, s in enumerate(snrs)]
+    y = np.concatenate([p["y"] for p in parts])
+    sig = np.concatenate([np.full(20, p["sigma2"], np.float32) for p in parts])
+    ctx, dec = _decoder(jbp, code, 2, 1.0, parts[0]["perm"], iters=15, early_stop=True)
+    try:
+        got = dec.decode(y, sigma2=sig)
+        got_step = dec.decode(y, sigma2=sig, form=jbp.FORM_STEP)
+    finally:
+        dec.close()
+        ctx.close()
+    for i, p in enumerate(parts):
+        ref = O.decode(code, 2, float(np.float32(p["sigma2"])), p["perm"], p["y"], 15, early_stop=True,
+                       want_margin=True)
+        for g in (got, got_step):
+            sl = slice(20 * i, 20 * (i + 1))
+            diff = g["hat"][sl] != ref["hat"]
+            assert not (diff & (ref["margin"] > 1e-6)).any()
+            assert (g["iters"][sl] == ref["iters"]).all()
+
+
+def test_decode_many_graph_replay_matches_single_decodes(env):
+    """Three decoders of different (n, K, q) -- two fused, one in the HBM step form --
+    in one jbp_decode_many call: the eager call, the captured call and a graph
+    replay all equal individual decodes, bit for bit."""
+    jbp, O, torch = env
+    specs = [(64, 4, 2, 12.0, 40), (128, 16, 3, 14.0, 25), (256, 64, 4, 14.0, 6)]
+    ctx = jbp.Context(iters=8, early_stop=True)
+    decs, parts, refs = [], [], []
+    try:
+        for n, q, K, snr, F in specs:
+            code = I.make_code(n, q)
+            fr = I.make_frames(code, K, snr, F, seed=n + q + K)
+            sig = np.full(F, fr["sigma2"], np.float32)
+            d = jbp.Decoder(ctx, code, K, fr["sigma2"], fr["perm"])
+            decs.append(d)
+            refs.append(d.decode(fr["y"], sigma2=sig))
+            t = lambda a, dt=None: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+            parts.append((d, t(fr["y"]), torch.empty((F, K, n), dtype=torch.uint8, device="cuda"),
+                          torch.empty((F,), dtype=torch.int32, device="cuda"),
+                          torch.empty((F, K), dtype=torch.uint8, device="cuda"), t(sig)))
+        assert not decs[2].fused_ok
+        for call in range(3):                  # eager, capture, replay
+            for p in parts:
+                p[2].fill_(255)
+            ctx.decode_many(parts)
+            torch.cuda.synchronize()
+            for p, r in zip(parts, refs):
+                assert np.array_equal(p[2].cpu().numpy(), r["hat"]), call
+                assert np.array_equal(p[3].cpu().numpy(), r["iters"]), call
+                assert np.array_equal(p[4].cpu().numpy(), r["ok"]), call
+    finally:
+        for d in decs:
+            d.close()
+        ctx.close()
+
+
+def test_serving_results_are_the_same_alone_and_in_the_mix(env):
+    """Requests of two decoders submitted interleaved (continuous batching over
+    concurrent launches) give, frame by frame, exactly the result of decoding that
+    frame alone; unknown or consumed tickets poll JBP_ECLOSED."""
+    jbp, O, torch = env
+    ctx = jbp.Context(iters=10, early_stop=True)
+    specs = [(64, 4, 2, 11.0, 24), (128, 16, 3, 13.0, 16)]
+    decs, frames = [], []
+    try:
+        for n, q, K, snr, F in specs:
+            code = I.make_code(n, q)
+            fr = I.make_frames(code, K, snr, F, seed=900 + n)
+            decs.append(jbp.Decoder(ctx, code, K, fr["sigma2"], fr["perm"]))
+            frames.append(fr)
+        sig = [np.full(fr["y"].shape[0], np.float32(fr["sigma2"]), np.float32) for fr in frames]
+        alone = [[d.decode(fr["y"][i:i + 1], sigma2=s[i:i + 1]) for i in range(fr["y"].shape[0])]
+                 for d, fr, s in zip(decs, frames, sig)]
+        tickets = []
+        for i in range(max(fr["y"].shape[0] for fr in frames)):
+            for j, (d, fr) in enumerate(zip(decs, frames)):
+                if i < fr["y"].shape[0]:
+                    tickets.append((j, i, d.submit(fr["y"][i], float(sig[j][i]))))
+        pending = list(tickets)
+        while pending:
+            rest = []
+            for j, i, tk in pending:
+                res = ctx.poll(tk, decs[j].n, decs[j].K)
+                if res is None:
+                    rest.append((j, i, tk))
+                    continue
+                a = alone[j][i]
+                assert np.array_equal(res["hat"], a["hat"][0]), (j, i)
+                assert res["iters"] == int(a["iters"][0]) and np.array_equal(res["ok"], a["ok"][0])
+            pending = rest
+        with pytest.raises(jbp.JBPError) as ei:
+            ctx.poll(tickets[0][2], decs[0].n, decs[0].K)
+        assert ei.value.code == jbp.ECLOSED
+        st = ctx.serving_stats()
+        assert st["completed"] == len(tickets) and st["p99_us"] >= st["p50_us"] > 0
+    finally:
+        for d in decs:
+            d.close()
+        ctx.close()
