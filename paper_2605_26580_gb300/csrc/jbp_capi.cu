@@ -17,7 +17,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "../../include/jbp.h"
+#include "jbp.h"
 #include "jbp_internal.h"
 
 using namespace jbp;

@@ -1247,22 +1247,26 @@ __device__ __forceinline__ int gf_lin(const int (&basis)[6], int x)
 }
 
 // Check node of check j of user k, thread shape, position-major layout.
-// slot_k: [E] (position*2 + d) of each edge; coef: [E] coefficients.
+// slot_k: [E] (position*2 + d) of each edge; coef: [E] coefficients.  The
+// permuted offsets pos_sym(h^{-1} x) are XORs of the basis images scaled to
+// their offsets (both maps are GF(2)-linear in x when one symbol per chunk).
 template <int Q>
 __device__ __forceinline__ void check_thread_pos(float* msg_f, int NB, int k, int j, const uint16_t* slot_k,
                                                  const uint8_t* coef, const uint8_t* gdiv)
 {
+    static_assert(PosW<Q>::W == 1, "offset XOR trick needs one symbol per chunk");
     float P[kDC][Q];
-    int base[kDC], basis[kDC][6];
+    float* base[kDC];
+    int basis[kDC][6];
 #pragma unroll
     for (int d = 0; d < kDC; ++d) {
         const int e = 4 * j + d, sl = slot_k[e], pp = sl >> 1;
-        base[d] = pos_vec<Q>((k * NB + (pp >> 5)) * 2 + (sl & 1), pp);
+        base[d] = msg_f + pos_vec<Q>((k * NB + (pp >> 5)) * 2 + (sl & 1), pp);
         const uint8_t* dv = gdiv + coef[e] * Q;
 #pragma unroll
-        for (int b = 0; b < 6; ++b) basis[d][b] = ((1 << b) < Q) ? dv[1 << b] : 0;
+        for (int b = 0; b < 6; ++b) basis[d][b] = ((1 << b) < Q) ? dv[1 << b] * kLanes : 0;
 #pragma unroll
-        for (int x = 0; x < Q; ++x) P[d][x] = msg_f[base[d] + pos_sym<Q>(gf_lin<Q>(basis[d], x))];
+        for (int x = 0; x < Q; ++x) P[d][x] = base[d][gf_lin<Q>(basis[d], x)];
     }
 #pragma unroll
     for (int d = 0; d < kDC; ++d) wht_reg<Q>(P[d]);
@@ -1281,7 +1285,7 @@ __device__ __forceinline__ void check_thread_pos(float* msg_f, int NB, int k, in
         const float mx = vmax(P[d]);
         const float fl = kRelFloor * mx, inv = 1.0f / mx;
 #pragma unroll
-        for (int x = 0; x < Q; ++x) msg_f[base[d] + pos_sym<Q>(gf_lin<Q>(basis[d], x))] = fmaxf(P[d][x], fl) * inv;
+        for (int x = 0; x < Q; ++x) base[d][gf_lin<Q>(basis[d], x)] = fmaxf(P[d][x], fl) * inv;
     }
 }
 

@@ -21,7 +21,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "../../include/jbp.h"
+#include "jbp.h"
 #include "jbp_internal.h"
 
 namespace {
