@@ -681,3 +681,210 @@ long or_brute_marginals(const or_code *code, const or_chan *ch, const float *y, 
     gf_free(&g);
     return C;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Evidence interface: Bernoulli-Gaussian denoiser, slot AMP, SIC FFT-BP    */
+/* ------------------------------------------------------------------------ */
+
+static const double OR_PI = 3.14159265358979323846;
+
+/* log of the circular complex Gaussian density phi(r; 0, v) at |r|^2 = s */
+static double log_cn(double s, double v)
+{
+    return -s / v - log(OR_PI * v);
+}
+
+/* eq. (bg_activity_prob): rho phi1 / ((1-rho) phi0 + rho phi1), in logs */
+double or_bg_log_activity(double s, double nu, double rho, double su2)
+{
+    double a1 = log(rho) + log_cn(s, nu + su2);
+    double a0 = log(1.0 - rho) + log_cn(s, nu);
+    double mx = a0 > a1 ? a0 : a1;
+    return a1 - (mx + log(exp(a0 - mx) + exp(a1 - mx)));
+}
+
+/* eq. (bg_mmse_mean): eta = p^ * su2 / (nu + su2) * r */
+double or_bg_gain(double s, double nu, double rho, double su2)
+{
+    return exp(or_bg_log_activity(s, nu, rho, su2)) * su2 / (nu + su2);
+}
+
+/* eta(r) = g(s) r with s = r conj(r): d eta / d r = g(s) + s g'(s); with
+ * log p^ = a1 - log(exp(a0) + exp(a1)), d p^/ds = p^ (1 - p^) (1/nu - 1/(nu+su2)) */
+double or_bg_deriv(double s, double nu, double rho, double su2)
+{
+    double p = exp(or_bg_log_activity(s, nu, rho, su2));
+    double c = su2 / (nu + su2);
+    double dp = p * (1.0 - p) * (1.0 / nu - 1.0 / (nu + su2));
+    return c * (p + s * dp);
+}
+
+void or_amp_dict(int Q, int ns, const double *Ar, const double *Ai, const float *y, int iters,
+                 double rho, double su2, double *S, double *R_out, double *nu_out)
+{
+    double *Ur = (double *)calloc(Q, sizeof(double)), *Ui = (double *)calloc(Q, sizeof(double));
+    double *Rr = (double *)malloc(sizeof(double) * Q), *Ri = (double *)malloc(sizeof(double) * Q);
+    double *Tr = (double *)malloc(sizeof(double) * ns), *Ti = (double *)malloc(sizeof(double) * ns);
+    double *Nr = (double *)malloc(sizeof(double) * ns), *Ni = (double *)malloc(sizeof(double) * ns);
+    for (int i = 0; i < ns; ++i) { Tr[i] = y[2 * i]; Ti[i] = y[2 * i + 1]; }
+    double nu = 0.0;
+    for (int it = 0; it <= iters; ++it) {
+        /* nu^(i) = |Ytilde^(i)|^2 / ns */
+        nu = 0.0;
+        for (int i = 0; i < ns; ++i) nu += Tr[i] * Tr[i] + Ti[i] * Ti[i];
+        nu /= ns;
+        /* eq. (amp_iter_r): R = U + A^H Ytilde */
+        for (int a = 0; a < Q; ++a) {
+            double sr = Ur[a], si = Ui[a];
+            for (int i = 0; i < ns; ++i) {
+                /* conj(A) * T */
+                sr += Ar[i * Q + a] * Tr[i] + Ai[i * Q + a] * Ti[i];
+                si += Ar[i * Q + a] * Ti[i] - Ai[i * Q + a] * Tr[i];
+            }
+            Rr[a] = sr;
+            Ri[a] = si;
+        }
+        if (it == iters) break;
+        /* eq. (amp_iter_u): U = eta(R; nu), and the Onsager sum of eta' */
+        double dsum = 0.0;
+        for (int a = 0; a < Q; ++a) {
+            double s = Rr[a] * Rr[a] + Ri[a] * Ri[a];
+            double gn = or_bg_gain(s, nu, rho, su2);
+            Ur[a] = gn * Rr[a];
+            Ui[a] = gn * Ri[a];
+            dsum += or_bg_deriv(s, nu, rho, su2);
+        }
+        /* eq. (amp_iter_res): Ytilde' = Y - A U + Ytilde / ns * sum eta' */
+        for (int i = 0; i < ns; ++i) {
+            double sr = y[2 * i], si = y[2 * i + 1];
+            for (int a = 0; a < Q; ++a) {
+                sr -= Ar[i * Q + a] * Ur[a] - Ai[i * Q + a] * Ui[a];
+                si -= Ar[i * Q + a] * Ui[a] + Ai[i * Q + a] * Ur[a];
+            }
+            Nr[i] = sr + Tr[i] * dsum / ns;
+            Ni[i] = si + Ti[i] * dsum / ns;
+        }
+        memcpy(Tr, Nr, sizeof(double) * ns);
+        memcpy(Ti, Ni, sizeof(double) * ns);
+    }
+    /* evidence interface: S = log p^(R^(I); nu^(I)) */
+    for (int a = 0; a < Q; ++a) S[a] = or_bg_log_activity(Rr[a] * Rr[a] + Ri[a] * Ri[a], nu, rho, su2);
+    if (R_out)
+        for (int a = 0; a < Q; ++a) { R_out[2 * a] = Rr[a]; R_out[2 * a + 1] = Ri[a]; }
+    if (nu_out) *nu_out = nu;
+    free(Ur); free(Ui); free(Rr); free(Ri);
+    free(Tr); free(Ti); free(Nr); free(Ni);
+}
+
+void or_amp_slot(int Q, int ns, const int *rows, const float *y, int iters, double rho,
+                 double su2, double *S, double *R_out, double *nu_out)
+{
+    /* A[i][a] = exp(-2 pi i rows[i] a / Q) / sqrt(ns), real and imaginary parts */
+    double *Ar = (double *)malloc(sizeof(double) * ns * Q);
+    double *Ai = (double *)malloc(sizeof(double) * ns * Q);
+    const double scale = 1.0 / sqrt((double)ns);
+    for (int i = 0; i < ns; ++i)
+        for (int a = 0; a < Q; ++a) {
+            long ka = ((long)rows[i] * a) % Q;
+            double ang = -2.0 * OR_PI * (double)ka / (double)Q;
+            Ar[i * Q + a] = cos(ang) * scale;
+            Ai[i * Q + a] = sin(ang) * scale;
+        }
+    or_amp_dict(Q, ns, Ar, Ai, y, iters, rho, su2, S, R_out, nu_out);
+    free(Ar); free(Ai);
+}
+
+void or_amp_evidence(int Q, int ns, int L, const int *rows, int F, const float *y, int iters,
+                     double rho, double su2, double *S, int threads)
+{
+    set_threads(threads);
+#pragma omp parallel for schedule(dynamic)
+    for (int f = 0; f < F; ++f)
+        for (int l = 0; l < L; ++l)
+            or_amp_slot(Q, ns, rows + (size_t)l * ns, y + ((size_t)f * L + l) * ns * 2, iters, rho, su2,
+                        S + ((size_t)f * L + l) * Q, NULL, NULL);
+}
+
+/* One row: the local beliefs are the channel messages of a K = 1 decode, held
+ * fixed; each iteration is check (v2c then the WHT check update), marginal,
+ * decision, syndrome. */
+static void frame_bp_prior(const graph_t *G, const gf_t *g, const double *S, const or_opts *o,
+                           uint8_t *hat, int32_t *iters, uint8_t *ok, double *post, double *margin)
+{
+    const int Q = G->Q, n = G->n;
+    const size_t sc = (size_t)G->E * Q, sv = (size_t)n * Q;
+    double *lam = (double *)malloc(sizeof(double) * (sv ? sv : 1));
+    double *c2v_old = (double *)calloc(sc ? sc : 1, sizeof(double));
+    double *c2v_new = (double *)calloc(sc ? sc : 1, sizeof(double));
+    double *pst = (double *)calloc(sv ? sv : 1, sizeof(double));
+    double *mrg = (double *)calloc(n ? n : 1, sizeof(double));
+    uint8_t *h = (uint8_t *)calloc(n ? n : 1, 1);
+    uint8_t okf = 0;
+    memcpy(lam, S, sizeof(double) * sv);
+    for (int i = 0; i < n; ++i) normalise_log(lam + (size_t)i * Q, Q, o->log_floor);
+    int t_run = 0;
+    for (int t = 1; t <= o->iters; ++t) {
+        frame_check(G, g, 1, lam, c2v_old, o->check_method, o->rel_floor, c2v_new);
+        double *sw = c2v_old; c2v_old = c2v_new; c2v_new = sw;
+        frame_var(G, 1, lam, c2v_old, pst, h, mrg);
+        frame_syndrome(G, g, 1, h, &okf);
+        t_run = t;
+        if (o->early_stop && okf) break;
+    }
+    if (hat) memcpy(hat, h, n);
+    if (iters) *iters = t_run;
+    if (ok) *ok = okf;
+    if (post) memcpy(post, pst, sizeof(double) * sv);
+    if (margin) memcpy(margin, mrg, sizeof(double) * n);
+    free(lam); free(c2v_old); free(c2v_new); free(pst); free(mrg); free(h);
+}
+
+void or_bp_prior(const or_code *code, int F, const double *S, const or_opts *o, uint8_t *hat,
+                 int32_t *iters, uint8_t *ok, double *post, double *margin)
+{
+    graph_t G;
+    gf_t g;
+    graph_make(&G, code);
+    gf_make(&g, code->m);
+    const size_t sv = (size_t)G.n * G.Q;
+    set_threads(o->threads);
+#pragma omp parallel for schedule(dynamic)
+    for (int f = 0; f < F; ++f)
+        frame_bp_prior(&G, &g, S + f * sv, o, hat ? hat + (size_t)f * G.n : NULL, iters ? iters + f : NULL,
+                       ok ? ok + f : NULL, post ? post + f * sv : NULL, margin ? margin + (size_t)f * G.n : NULL);
+    gf_free(&g);
+    graph_free(&G);
+}
+
+void or_sic_decode(const or_code *code, int K, double cancel_log, int F, const double *S,
+                   const or_opts *o, uint8_t *hat, int32_t *iters, uint8_t *ok, double *margin)
+{
+    graph_t G;
+    gf_t g;
+    graph_make(&G, code);
+    gf_make(&g, code->m);
+    const int n = G.n, Q = G.Q;
+    const size_t sv = (size_t)n * Q;
+    set_threads(o->threads);
+#pragma omp parallel for schedule(dynamic)
+    for (int f = 0; f < F; ++f) {
+        double *Sk = (double *)malloc(sizeof(double) * (sv ? sv : 1));
+        uint8_t *h = (uint8_t *)calloc(n ? n : 1, 1);
+        memcpy(Sk, S + f * sv, sizeof(double) * sv);
+        for (int k = 0; k < K; ++k) {
+            const size_t r = (size_t)f * K + k;
+            int32_t it = 0;
+            uint8_t okk = 0;
+            frame_bp_prior(&G, &g, Sk, o, h, &it, &okk, NULL, margin ? margin + r * n : NULL);
+            if (hat) memcpy(hat + r * n, h, n);
+            if (iters) iters[r] = it;
+            if (ok) ok[r] = okk;
+            /* cancel the decoded row's evidence before the next row */
+            for (int i = 0; i < n; ++i) Sk[(size_t)i * Q + h[i]] += cancel_log;
+        }
+        free(Sk);
+        free(h);
+    }
+    gf_free(&g);
+    graph_free(&G);
+}

@@ -111,6 +111,55 @@ void or_decode(const or_code *code, const or_chan *ch, int F, const float *y,
  * Returns |C|, or -1 if the case is too large. */
 long or_brute_marginals(const or_code *code, const or_chan *ch, const float *y, double *out);
 
+/* ---- evidence interface: slot-wise AMP detector and SIC FFT-BP ----
+ * The paper's own classical baseline decodes K rows from a slot-wise evidence
+ * matrix S (L x Q) produced by a fixed AMP-MMSE detector (appendix "Slot-wise
+ * AMP--MMSE detector"; appendix "Q-ary LDPC code", eq. app_ldpc_local_belief_from_S;
+ * appendix "Complexity derivation", paragraphs SIC-BP and FFT-BP). */
+
+/* Scalar Bernoulli-Gaussian channel R = U + W, W ~ CN(0, nu),
+ * U ~ (1-rho) delta_0 + rho CN(0, su2); s = |r|^2.
+ * or_bg_log_activity: log of the activity posterior, eq. (bg_activity_prob).
+ * or_bg_gain: eta(r)/r, so that eq. (bg_mmse_mean) is eta(r) = gain * r.
+ * or_bg_deriv: the complex sensitivity d eta / d r (half the divergence
+ * d Re(eta)/d Re(r) + d Im(eta)/d Im(r)), which scales the Onsager term. */
+double or_bg_log_activity(double s, double nu, double rho, double su2);
+double or_bg_gain(double s, double nu, double rho, double su2);
+double or_bg_deriv(double s, double nu, double rho, double su2);
+
+/* AMP-MMSE on one slot, eqs. (amp_iter_r), (amp_iter_u), (amp_iter_res):
+ * A = F_{rows,:} / sqrt(ns) with F_{k,a} = exp(-2 pi i k a / Q) (partial DFT,
+ * appendix "Sensing-matrix construction"), nu^(i) = |Ytilde^(i)|^2 / ns.
+ * y [2*ns] interleaved complex observation; after `iters` iterations the
+ * evidence S[a] = log p^(R^(iters)_a; nu^(iters)) (paragraph "Evidence
+ * interface").  R_out [2*Q] (final pseudo-observation) and nu_out may be NULL.
+ * Q here is any size >= 1 (not only a field size). */
+void or_amp_slot(int Q, int ns, const int *rows, const float *y, int iters, double rho,
+                 double su2, double *S, double *R_out, double *nu_out);
+/* The same iteration for any dictionary A [ns*Q] given by its real and
+ * imaginary parts (row-major, A[i*Q + a]). */
+void or_amp_dict(int Q, int ns, const double *Ar, const double *Ai, const float *y, int iters,
+                 double rho, double su2, double *S, double *R_out, double *nu_out);
+/* Batched over F frames of L slots: y [F*L*ns*2], rows [L*ns] (slot l uses
+ * rows + l*ns), S [F*L*Q]. */
+void or_amp_evidence(int Q, int ns, int L, const int *rows, int F, const float *y, int iters,
+                     double rho, double su2, double *S, int threads);
+
+/* Single-row FFT-BP with local beliefs lambda_l(a) proportional to exp(S_{l,a})
+ * (eq. app_ldpc_local_belief_from_S), max-normalised and clipped at
+ * o->log_floor; flooding: v2c (eq. app_ldpc_v2c), check (the WHT form),
+ * marginal and decision (eq. app_ldpc_marginal), early exit when the syndrome
+ * is zero.  S [F*n*Q]; outputs as or_decode with K = 1. */
+void or_bp_prior(const or_code *code, int F, const double *S, const or_opts *o, uint8_t *hat,
+                 int32_t *iters, uint8_t *ok, double *post, double *margin);
+
+/* SIC over K rows: row k is decoded by or_bp_prior from S^(k); then
+ * S^(k+1)_{l,a} = S^(k)_{l,a} + cancel_log at a = hat_k[l] (every other entry
+ * unchanged), S^(0) = S.  hat [F*K*n], iters [F*K], ok [F*K], margin
+ * [F*K*n] (NULL = not wanted). */
+void or_sic_decode(const or_code *code, int K, double cancel_log, int F, const double *S,
+                   const or_opts *o, uint8_t *hat, int32_t *iters, uint8_t *ok, double *margin);
+
 #ifdef __cplusplus
 }
 #endif

@@ -81,6 +81,16 @@ def lib():
                                        u8, i32, u8, d, d, d, d]
             _lib.or_brute_marginals.argtypes = [C.POINTER(_Code), C.POINTER(_Chan), f32, d]
             _lib.or_brute_marginals.restype = C.c_long
+            for fn in (_lib.or_bg_log_activity, _lib.or_bg_gain, _lib.or_bg_deriv):
+                fn.argtypes = [C.c_double] * 4
+                fn.restype = C.c_double
+            _lib.or_amp_slot.argtypes = [C.c_int, C.c_int, i, f32, C.c_int, C.c_double, C.c_double, d, d, d]
+            _lib.or_amp_dict.argtypes = [C.c_int, C.c_int, d, d, f32, C.c_int, C.c_double, C.c_double, d, d, d]
+            _lib.or_amp_evidence.argtypes = [C.c_int, C.c_int, C.c_int, i, C.c_int, f32, C.c_int, C.c_double,
+                                             C.c_double, d, C.c_int]
+            _lib.or_bp_prior.argtypes = [C.POINTER(_Code), C.c_int, d, C.POINTER(_Opts), u8, i32, u8, d, d]
+            _lib.or_sic_decode.argtypes = [C.POINTER(_Code), C.c_int, C.c_double, C.c_int, d, C.POINTER(_Opts),
+                                           u8, i32, u8, d]
     return _lib
 
 
@@ -227,6 +237,95 @@ def brute_marginals(code, K, sigma2, perm, y):
     if size < 0:
         raise ValueError("case too large for enumeration")
     return out, int(size)
+
+
+# ---- evidence interface: AMP detector and SIC FFT-BP ----
+
+def bg_log_activity(s, nu, rho, su2):
+    return lib().or_bg_log_activity(float(s), float(nu), float(rho), float(su2))
+
+
+def bg_gain(s, nu, rho, su2):
+    return lib().or_bg_gain(float(s), float(nu), float(rho), float(su2))
+
+
+def bg_deriv(s, nu, rho, su2):
+    return lib().or_bg_deriv(float(s), float(nu), float(rho), float(su2))
+
+
+def amp_slot(Q, rows, y, iters, rho, su2):
+    """One slot: returns (S [Q], R [Q] complex, nu)."""
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    y = np.ascontiguousarray(y, dtype=np.float32).reshape(-1)
+    S = np.empty(Q, dtype=np.float64)
+    R = np.empty(2 * Q, dtype=np.float64)
+    nu = C.c_double()
+    lib().or_amp_slot(int(Q), rows.size, _ptr(rows, C.c_int), _ptr(y, C.c_float), int(iters), float(rho),
+                      float(su2), _ptr(S, C.c_double), _ptr(R, C.c_double), C.byref(nu))
+    return S, R[0::2] + 1j * R[1::2], nu.value
+
+
+def amp_dict(A, y, iters, rho, su2):
+    """AMP with a given complex dictionary A [ns, Q]: returns (S [Q], R [Q], nu)."""
+    ns, Q = A.shape
+    Ar = np.ascontiguousarray(A.real, dtype=np.float64)
+    Ai = np.ascontiguousarray(A.imag, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float32).reshape(-1)
+    S = np.empty(Q, dtype=np.float64)
+    R = np.empty(2 * Q, dtype=np.float64)
+    nu = C.c_double()
+    lib().or_amp_dict(int(Q), int(ns), _ptr(Ar, C.c_double), _ptr(Ai, C.c_double), _ptr(y, C.c_float), int(iters),
+                      float(rho), float(su2), _ptr(S, C.c_double), _ptr(R, C.c_double), C.byref(nu))
+    return S, R[0::2] + 1j * R[1::2], nu.value
+
+
+def amp_evidence(Q, rows, y, iters, rho, su2, threads=0):
+    """y [F, L, ns, 2] float32, rows [L, ns] -> S [F, L, Q] float64."""
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    L, ns = rows.shape
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    F = y.shape[0]
+    S = np.empty((F, L, Q), dtype=np.float64)
+    lib().or_amp_evidence(int(Q), ns, L, _ptr(rows, C.c_int), F, _ptr(y, C.c_float), int(iters), float(rho),
+                          float(su2), _ptr(S, C.c_double), int(threads))
+    return S
+
+
+def _opts(iters, early_stop, check_method, rel_floor, log_floor, threads):
+    return _Opts(int(iters), int(bool(early_stop)), int(check_method), float(rel_floor), float(log_floor),
+                 int(threads))
+
+
+def bp_prior(code, S, iters, early_stop=True, check_method=CHECK_WHT, rel_floor=REL_FLOOR,
+             log_floor=LOG_FLOOR, threads=0, want_post=False):
+    """Single-row FFT-BP from evidence S [F, n, Q]."""
+    pin = _Pinned(code)
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    F, n, Q = S.shape
+    out = {"hat": np.empty((F, n), dtype=np.uint8), "iters": np.empty((F,), dtype=np.int32),
+           "ok": np.empty((F,), dtype=np.uint8), "margin": np.empty((F, n), dtype=np.float64)}
+    if want_post:
+        out["post"] = np.empty((F, n, Q), dtype=np.float64)
+    o = _opts(iters, early_stop, check_method, rel_floor, log_floor, threads)
+    lib().or_bp_prior(C.byref(pin.code), F, _ptr(S, C.c_double), C.byref(o), _ptr(out["hat"], C.c_uint8),
+                      _ptr(out["iters"], C.c_int32), _ptr(out["ok"], C.c_uint8), _ptr(out.get("post"), C.c_double),
+                      _ptr(out["margin"], C.c_double))
+    return out
+
+
+def sic_decode(code, K, S, iters, cancel_log, early_stop=True, check_method=CHECK_WHT,
+               rel_floor=REL_FLOOR, log_floor=LOG_FLOOR, threads=0):
+    """SIC over K rows from evidence S [F, n, Q]: hat [F, K, n], iters/ok [F, K], margin."""
+    pin = _Pinned(code)
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    F, n, Q = S.shape
+    out = {"hat": np.empty((F, K, n), dtype=np.uint8), "iters": np.empty((F, K), dtype=np.int32),
+           "ok": np.empty((F, K), dtype=np.uint8), "margin": np.empty((F, K, n), dtype=np.float64)}
+    o = _opts(iters, early_stop, check_method, rel_floor, log_floor, threads)
+    lib().or_sic_decode(C.byref(pin.code), int(K), float(cancel_log), F, _ptr(S, C.c_double), C.byref(o),
+                        _ptr(out["hat"], C.c_uint8), _ptr(out["iters"], C.c_int32), _ptr(out["ok"], C.c_uint8),
+                        _ptr(out["margin"], C.c_double))
+    return out
 
 
 def host_threads() -> int:

@@ -270,3 +270,84 @@ def random_log_messages(rng: np.random.Generator, shape, q: int, spread: float =
     x = rng.standard_normal(tuple(shape) + (q,)) * spread
     x -= x.max(axis=-1, keepdims=True)
     return np.maximum(x, log_floor)
+
+
+# ---------------------------------------------------------------------------
+# Evidence interface (the paper's URA slot model; appendix "Unsourced random
+# access", appendix "Simulation pipeline and channel model")
+# ---------------------------------------------------------------------------
+
+def ura_rows(L: int, q: int, ns: int, seed: int) -> np.ndarray:
+    """Partial-DFT row indices [L, ns] (int32): per slot, ns distinct rows of the
+    q x q DFT drawn uniformly from PCG64(seed) (appendix "Sensing-matrix
+    construction"; one dictionary per slot, fixed for all frames)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.stack([rng.choice(q, size=ns, replace=False) for _ in range(L)]).astype(np.int32)
+
+
+def ura_psym(code: dict, eb_db: float) -> float:
+    """Transmit power per symbol P_sym = B 10^(Eb/10) / L with B = log2(q) k info
+    bits (appendix "Simulation constants")."""
+    B = code["m"] * code["k"]
+    return B * 10.0 ** (eb_db / 10.0) / code["n"]
+
+
+def ura_detector_params(K: int, q: int, psym: float) -> dict:
+    """Detector hyper-parameters and the SIC cancellation weight, as read here
+    (the paper leaves them open): rho_BG = K / q (about K of q signatures
+    active per slot), sigma_u^2 = P_sym (power of one unit-amplitude signature
+    at the transmit scale), cancel_log = -log q (after a row is decoded, a
+    later row uses the same symbol in that slot only by collision, probability
+    1/q under uniform symbols)."""
+    return {"rho": K / q, "su2": float(psym), "cancel_log": -math.log(q)}
+
+
+def make_ura_frames(code: dict, K: int, eb_db: float, F: int, seed: int, ns: int = 24,
+                    rows_seed: int | None = None, noiseless: bool = False) -> dict:
+    """F frames of the URA slot model: K uniform messages encoded by the shared
+    code (X [F, K, L]), and per slot l the observation
+
+        Y^(l) = sqrt(P_sym) A^(l) U^(l) + eps,   U^(l) = sum_k e_{X[k, l]},
+        A^(l) = F_{R_l,:} / sqrt(ns),  F_{k,a} = exp(-2 pi i k a / q),  eps ~ CN(0, I),
+
+    returned as y [F, L, ns, 2] float32 (real, imaginary).  Streams: messages
+    from PCG64(seed), noise from PCG64(seed + 1), rows from PCG64(rows_seed or
+    the code seed + 7)."""
+    q, L = code["q"], code["n"]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    info = rng.integers(0, q, size=(F, K, code["k"]), dtype=np.int64)
+    X = encode(code, info)                                   # [F, K, L]
+    rows = ura_rows(L, q, ns, code_seed(L, q) + 7 if rows_seed is None else rows_seed)
+    psym = ura_psym(code, eb_db)
+    # dictionary columns: A[l, i, a]
+    A = np.exp(-2j * np.pi * ((rows[:, :, None].astype(np.int64) * np.arange(q)[None, None, :]) % q) / q)
+    A /= math.sqrt(ns)
+    Y = np.zeros((F, L, ns), dtype=np.complex128)
+    slot = np.arange(L)[None, :]
+    for k in range(K):
+        Y += A[slot, :, X[:, k, :].astype(np.int64)]         # column X[f, k, l] of slot l: [F, L, ns]
+    Y *= math.sqrt(psym)
+    if not noiseless:
+        nrng = np.random.Generator(np.random.PCG64(seed + 1))
+        Y += (nrng.standard_normal((F, L, ns)) + 1j * nrng.standard_normal((F, L, ns))) * math.sqrt(0.5)
+    y = np.stack([Y.real, Y.imag], axis=-1).astype(np.float32)
+    return {"X": X, "y": y, "rows": rows, "psym": psym, "K": K, "ns": ns, "eb_db": eb_db,
+            **ura_detector_params(K, q, psym)}
+
+
+def match_rows(hat: np.ndarray, X: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Row alignment of eq. (app_ura_hungarian) for small K by enumerating all K!
+    permutations: per frame the permutation with the fewest symbol errors.
+    hat, X [F, K, L] -> (symbol errors [F], codeword errors [F])."""
+    import itertools
+    F, K, L = X.shape
+    best_sym = np.full(F, K * L + 1, dtype=np.int64)
+    best_cw = np.zeros(F, dtype=np.int64)
+    for p in itertools.permutations(range(K)):
+        diff = hat != X[:, list(p), :]
+        sym = diff.sum(axis=(1, 2))
+        cw = diff.any(axis=2).sum(axis=1)
+        better = sym < best_sym
+        best_sym = np.where(better, sym, best_sym)
+        best_cw = np.where(better, cw, best_cw)
+    return best_sym, best_cw

@@ -74,3 +74,31 @@ def test_random_messages_are_max_normalised():
     m = I.random_log_messages(rng, (7, 3), 16)
     assert m.shape == (7, 3, 16)
     assert np.allclose(m.max(-1), 0.0) and m.min() >= math.log(1e-12)
+
+
+def test_ura_frames_follow_the_slot_model():
+    """Noiseless y equals sqrt(P_sym) * FFT of the activity vector at the slot's
+    rows, / sqrt(ns); rows are distinct per slot; (2,3) codes have rate 1/3."""
+    import math
+    code = I.make_code(12, 64, dv=2, dc=3)
+    assert code["P"] == 8 and code["k"] == 4
+    fr = I.make_ura_frames(code, 2, 10.0, 3, seed=1, noiseless=True)
+    assert fr["psym"] == pytest.approx(6 * 4 * 10.0 / 12)
+    for l in range(12):
+        assert len(set(fr["rows"][l].tolist())) == 24
+    for f in range(3):
+        for l in range(12):
+            u = np.zeros(64)
+            for k in range(2):
+                u[fr["X"][f, k, l]] += 1
+            want = np.fft.fft(u)[fr["rows"][l]] / math.sqrt(24) * math.sqrt(fr["psym"])
+            got = fr["y"][f, l, :, 0] + 1j * fr["y"][f, l, :, 1]
+            assert np.abs(got - want).max() < 1e-4
+
+
+def test_ura_noise_is_unit_complex_gaussian():
+    code = I.make_code(12, 64, dv=2, dc=3)
+    a = I.make_ura_frames(code, 2, 10.0, 400, seed=2)
+    b = I.make_ura_frames(code, 2, 10.0, 400, seed=2, noiseless=True)
+    w = (a["y"] - b["y"]).reshape(-1, 2).astype(np.float64)
+    assert abs(w.var(axis=0).mean() - 0.5) < 0.01
