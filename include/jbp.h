@@ -260,6 +260,70 @@ int jbp_stats(jbp_h *h, uint64_t *log_fallbacks, int32_t *tc_timeouts);
  * per-frame device state bytes, and whether one frame fits the fused form. */
 int jbp_query(jbp_h *h, int32_t *E, int64_t *state_bytes_per_frame, int32_t *fused_ok);
 
+/* ---- the paper's own classical path on the evidence interface S ----
+ *
+ * The paper's baseline decoders (appendix "Complexity derivation", paragraphs
+ * SIC-BP and FFT-BP; Table 1) decode K rows from a slot-wise evidence matrix
+ * S [n x q] (appendix "Q-ary LDPC code", eq. app_ldpc_local_belief_from_S),
+ * produced by a fixed AMP-MMSE slot detector (appendix "Slot-wise AMP--MMSE
+ * detector").  A jbp_ura handle holds one code and one detector configuration:
+ *
+ *   jbp_amp_evidence  y -> S     AMP per slot, eqs. amp_iter_r / amp_iter_u /
+ *                                amp_iter_res, Bernoulli-Gaussian denoiser
+ *                                eqs. bg_activity_prob / bg_mmse_mean, and
+ *                                S[l][a] = log p^(R_a; nu) (paragraph
+ *                                "Evidence interface")
+ *   jbp_sic_decode    S -> rows  SIC: row k is single-row FFT-BP from local
+ *                                beliefs exp(S^(k)) (max-normalised, floored at
+ *                                1e-12 of the max), flooding, WHT check
+ *                                node, early exit on a zero syndrome; then
+ *                                S^(k+1) = S^(k) + cancel_log at each slot's
+ *                                decided symbol (the paper leaves the SIC rule
+ *                                open; this is the rule built here)
+ *   jbp_ura_decode    y -> rows  both, with S kept on the device
+ *
+ * Slot model (appendix "Unsourced random access"): slot l of a frame carries
+ * y_l = A_l u_l + noise in C^ns with A_l = F_{rows_l,:} / sqrt(ns), F_{k,a} =
+ * exp(-2 pi i k a / q) (partial DFT, appendix "Sensing-matrix construction"). */
+typedef struct jbp_ura jbp_ura;
+
+/* Detector and decoder parameters.  ns: complex channel uses per slot, 1..32
+ * (and <= q).  K: rows decoded by SIC, 1..8.  amp_iters >= 0 (I_AMP).
+ * bp_iters >= 1 per row; early_stop = 1 ends a row at the first zero
+ * syndrome.  rho_bg in (0, 1) and sigma_u2 > 0: the Bernoulli-Gaussian prior of
+ * every coordinate.  cancel_log <= 0.  rows [n*ns]: slot l's partial-DFT rows at
+ * rows + l*ns, distinct values in 0..q-1; host pointer, copied. */
+typedef struct {
+    int32_t ns, K, amp_iters, bp_iters, early_stop, reserved;
+    double rho_bg, sigma_u2, cancel_log;
+    const int32_t *rows;
+} jbp_ura_params;
+
+/* Create a handle for a code (regular, dv = 2, dc = 3 or 4; q = 16, 32 or 64
+ * for the decoder, q = 32 or 64 for the detector) on ctx's device.  The code
+ * arrays and rows are copied.  Errors: JBP_EINVAL (bad code or parameters,
+ * or one frame's decoder state does not fit shared memory), JBP_ENOMEM,
+ * JBP_ECUDA. */
+int jbp_ura_create(jbp_ctx *ctx, const jbp_code *code, const jbp_ura_params *p, jbp_ura **out);
+int jbp_ura_destroy(jbp_ura *u);
+
+/* Evidence of F frames.  y [F*n*ns*2] (complex, real then imaginary per channel
+ * use, slot-major), S [F*n*q] out.  on_device = 1: device pointers, work
+ * enqueued on `stream` (NULL = the context's stream), no wait.  on_device = 0:
+ * host pointers, the call copies, runs and waits. */
+int jbp_amp_evidence(jbp_ura *u, int32_t F, const float *y, float *S, int32_t on_device, void *stream);
+
+/* SIC decode of F frames from evidence S [F*n*q]: hat [F*K*n] (row k of frame
+ * f at (f*K + k)*n), iters [F*K] (BP iterations of each row), ok [F*K] (row's
+ * syndrome zero).  Pointers and on_device as jbp_amp_evidence. */
+int jbp_sic_decode(jbp_ura *u, int32_t F, const float *S, uint8_t *hat, int32_t *iters, uint8_t *ok,
+                   int32_t on_device, void *stream);
+
+/* jbp_amp_evidence then jbp_sic_decode; S stays in the handle's device
+ * workspace (grown as needed, within the context's memory budget). */
+int jbp_ura_decode(jbp_ura *u, int32_t F, const float *y, uint8_t *hat, int32_t *iters, uint8_t *ok,
+                   int32_t on_device, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

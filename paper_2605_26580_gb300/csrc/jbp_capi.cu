@@ -1133,3 +1133,235 @@ extern "C" int jbp_serving_stats(jbp_ctx* ctx, uint64_t* completed, double* p50,
     if (p99) *p99 = b;
     return JBP_OK;
 }
+
+// ---------------------------------------------------------------------------
+// evidence interface: slot detector and SIC row decoder
+// ---------------------------------------------------------------------------
+
+struct jbp_ura {
+    jbp_ctx* ctx = nullptr;
+    UraDev u{};
+    int32_t* d_rows = nullptr;
+    float* d_tw = nullptr;
+    int32_t* d_chk_var = nullptr;
+    uint8_t* d_chk_coef = nullptr;
+    int32_t* d_var_edge = nullptr;
+    uint8_t* d_gf_mul = nullptr;
+    uint8_t* d_gf_div = nullptr;
+    int64_t table_bytes = 0;
+    std::mutex mu;
+    DevBuf S, y, hat, iters, ok;   // workspaces of the host-pointer calls and of jbp_ura_decode
+};
+
+extern "C" int jbp_ura_destroy(jbp_ura* u)
+{
+    if (!u) return fail(JBP_EINVAL, "jbp_ura_destroy: NULL handle");
+    jbp_ctx* ctx = u->ctx;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    dev_free(ctx, u->d_rows, sizeof(int32_t) * (size_t)u->u.n * u->u.ns);
+    dev_free(ctx, u->d_tw, sizeof(float) * 2 * (size_t)u->u.Q);
+    dev_free(ctx, u->d_chk_var, sizeof(int32_t) * (size_t)u->u.P * u->u.dc);
+    dev_free(ctx, u->d_chk_coef, (size_t)u->u.P * u->u.dc);
+    dev_free(ctx, u->d_var_edge, sizeof(int32_t) * 2 * (size_t)u->u.n);
+    dev_free(ctx, u->d_gf_mul, (size_t)u->u.Q * u->u.Q);
+    dev_free(ctx, u->d_gf_div, (size_t)u->u.Q * u->u.Q);
+    for (DevBuf* b : {&u->S, &u->y, &u->hat, &u->iters, &u->ok}) buf_free(ctx, *b);
+    if (u->d_gf_div) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->handles--;
+    }
+    delete u;
+    return JBP_OK;
+}
+
+extern "C" int jbp_ura_create(jbp_ctx* ctx, const jbp_code* code, const jbp_ura_params* p, jbp_ura** out)
+{
+    if (!ctx || !code || !p || !out) return fail(JBP_EINVAL, "jbp_ura_create: NULL argument");
+    const int q = code->q;
+    int m = 0;
+    while ((1 << m) < q && m < 8) ++m;
+    if ((1 << m) != q || (q != 16 && q != 32 && q != 64))
+        return fail(JBP_EINVAL, "q must be 16, 32 or 64 (got %d)", q);
+    if (code->dv != 2) return fail(JBP_EINVAL, "the row decoder is built for dv = 2 (got %d)", code->dv);
+    if (code->dc != 3 && code->dc != 4) return fail(JBP_EINVAL, "the row decoder is built for dc = 3 or 4 (got %d)", code->dc);
+    if (code->n < 1 || code->P < 1 || (int64_t)code->n * 2 != (int64_t)code->P * code->dc)
+        return fail(JBP_EINVAL, "n*dv must equal P*dc with n, P >= 1");
+    if (code->n > 32767) return fail(JBP_EINVAL, "n must be <= 32767");
+    if (!code->chk_var || !code->chk_coef || !p->rows) return fail(JBP_EINVAL, "NULL code arrays or rows");
+    if (p->ns < 1 || p->ns > 32 || p->ns > q) return fail(JBP_EINVAL, "ns must be in 1..min(32, q) (got %d)", p->ns);
+    if (p->K < 1 || p->K > 8) return fail(JBP_EINVAL, "K must be in 1..8 (got %d)", p->K);
+    if (p->amp_iters < 0 || p->bp_iters < 1) return fail(JBP_EINVAL, "amp_iters >= 0 and bp_iters >= 1 required");
+    if (!(p->rho_bg > 0.0 && p->rho_bg < 1.0)) return fail(JBP_EINVAL, "rho_bg must be in (0, 1)");
+    if (!(p->sigma_u2 > 0.0) || !std::isfinite(p->sigma_u2)) return fail(JBP_EINVAL, "sigma_u2 must be finite and > 0");
+    if (!(p->cancel_log <= 0.0) || !std::isfinite(p->cancel_log)) return fail(JBP_EINVAL, "cancel_log must be finite and <= 0");
+    const int n = code->n, P = code->P, dc = code->dc, E = P * dc;
+    std::vector<int32_t> var_edge((size_t)2 * n), fill(n, 0);
+    for (int e = 0; e < E; ++e) {
+        const int i = code->chk_var[e];
+        if (i < 0 || i >= n) return fail(JBP_EINVAL, "chk_var[%d] = %d out of range", e, i);
+        if (code->chk_coef[e] < 1 || code->chk_coef[e] >= q) return fail(JBP_EINVAL, "chk_coef[%d] = %d not in 1..q-1", e, code->chk_coef[e]);
+        if (fill[i] >= 2) return fail(JBP_EINVAL, "variable %d has more than 2 edges", i);
+        var_edge[(size_t)2 * i + fill[i]++] = e;
+    }
+    for (int i = 0; i < n; ++i)
+        if (fill[i] != 2) return fail(JBP_EINVAL, "variable %d has %d edges, expected 2", i, fill[i]);
+    for (int l = 0; l < n; ++l)
+        for (int i = 0; i < p->ns; ++i) {
+            const int r = p->rows[(size_t)l * p->ns + i];
+            if (r < 0 || r >= q) return fail(JBP_EINVAL, "rows[%d] = %d not in 0..q-1", l * p->ns + i, r);
+            for (int i2 = 0; i2 < i; ++i2)
+                if (p->rows[(size_t)l * p->ns + i2] == r) return fail(JBP_EINVAL, "slot %d repeats row %d", l, r);
+        }
+    std::vector<uint8_t> gmul((size_t)q * q), gdiv((size_t)q * q);
+    std::vector<int> inv(q, 0);
+    for (int a = 1; a < q; ++a)
+        for (int b = 1; b < q; ++b)
+            if (gf_mul_host(a, b, m) == 1) inv[a] = b;
+    for (int h = 0; h < q; ++h)
+        for (int x = 0; x < q; ++x) {
+            gmul[(size_t)h * q + x] = (uint8_t)gf_mul_host(h, x, m);
+            gdiv[(size_t)h * q + x] = (uint8_t)gf_mul_host(inv[h], x, m);
+        }
+    // twiddles exp(-2 pi i k / q) from the host's double-precision cos and sin
+    std::vector<float> tw((size_t)2 * q);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int k = 0; k < q; ++k) {
+        tw[2 * k] = (float)std::cos(two_pi * k / q);
+        tw[2 * k + 1] = (float)-std::sin(two_pi * k / q);
+    }
+    UraDev d{};
+    d.n = n; d.P = P; d.dc = dc; d.K = p->K; d.Q = q; d.ns = p->ns;
+    d.amp_iters = p->amp_iters; d.bp_iters = p->bp_iters; d.early_stop = p->early_stop ? 1 : 0;
+    d.log_odds = (float)std::log((1.0 - p->rho_bg) / p->rho_bg);
+    d.su2 = (float)p->sigma_u2;
+    d.inv_sqrt_ns = (float)(1.0 / std::sqrt((double)p->ns));
+    d.cancel_log = (float)p->cancel_log;
+    if (sic_warps_per_cta(d, ctx->di) < 1)
+        return fail(JBP_EINVAL, "n = %d, q = %d: one frame's row state does not fit shared memory", n, q);
+
+    JBP_CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    jbp_ura* u = new (std::nothrow) jbp_ura();
+    if (!u) return fail(JBP_ENOMEM, "host allocation failed");
+    u->ctx = ctx;
+    u->u = d;
+    int rc;
+    if ((rc = dev_alloc(ctx, &u->d_rows, (size_t)n * p->ns, &u->table_bytes)) ||
+        (rc = dev_alloc(ctx, &u->d_tw, (size_t)2 * q, &u->table_bytes)) ||
+        (rc = dev_alloc(ctx, &u->d_chk_var, (size_t)E, &u->table_bytes)) ||
+        (rc = dev_alloc(ctx, &u->d_chk_coef, (size_t)E, &u->table_bytes)) ||
+        (rc = dev_alloc(ctx, &u->d_var_edge, (size_t)2 * n, &u->table_bytes)) ||
+        (rc = dev_alloc(ctx, &u->d_gf_mul, (size_t)q * q, &u->table_bytes)) ||
+        (rc = dev_alloc(ctx, &u->d_gf_div, (size_t)q * q, &u->table_bytes))) {
+        jbp_ura_destroy(u);
+        return rc;
+    }
+    cudaError_t e;
+    if ((e = cudaMemcpy(u->d_rows, p->rows, sizeof(int32_t) * (size_t)n * p->ns, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(u->d_tw, tw.data(), sizeof(float) * tw.size(), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(u->d_chk_var, code->chk_var, sizeof(int32_t) * E, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(u->d_chk_coef, code->chk_coef, (size_t)E, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(u->d_var_edge, var_edge.data(), sizeof(int32_t) * var_edge.size(), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(u->d_gf_mul, gmul.data(), gmul.size(), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(u->d_gf_div, gdiv.data(), gdiv.size(), cudaMemcpyHostToDevice))) {
+        jbp_ura_destroy(u);
+        return cuda_fail(e, "jbp_ura_create: copy tables");
+    }
+    u->u.rows = u->d_rows; u->u.tw = u->d_tw; u->u.chk_var = u->d_chk_var; u->u.chk_coef = u->d_chk_coef;
+    u->u.var_edge = u->d_var_edge; u->u.gf_mul = u->d_gf_mul; u->u.gf_div = u->d_gf_div;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->handles++;
+    }
+    *out = u;
+    return JBP_OK;
+}
+
+static int ura_grow(jbp_ura* u, DevBuf& b, size_t bytes)
+{
+    bool grew = false;
+    return buf_ensure(u->ctx, b, bytes, &grew);
+}
+
+// One call of the evidence path on device pointers: what = 1 detector, 2 row
+// decoder, 3 both (S in the handle's workspace).
+static int ura_run(jbp_ura* u, int what, int F, const float* y, float* S, uint8_t* hat, int32_t* iters, uint8_t* ok,
+                   cudaStream_t s)
+{
+    const UraDev& d = u->u;
+    if ((what & 1) && d.Q != 32 && d.Q != 64) return fail(JBP_EINVAL, "the slot detector is built for q = 32 and 64");
+    if (what == 3) {
+        int rc = ura_grow(u, u->S, sizeof(float) * (size_t)F * d.n * d.Q);
+        if (rc) return rc;
+        S = P<float>(u->S);
+    }
+    cudaError_t e = cudaSuccess;
+    if (what & 1) {
+        e = launch_amp(d, u->ctx->di, F, y, S, s);
+        if (e != cudaSuccess) return cuda_fail(e, "slot detector launch");
+    }
+    if (what & 2) {
+        e = launch_sic(d, u->ctx->di, F, S, hat, iters, ok, s);
+        if (e != cudaSuccess) return cuda_fail(e, "row decoder launch");
+    }
+    return JBP_OK;
+}
+
+static int ura_call(jbp_ura* u, int what, int32_t F, const float* y, float* S_io, const float* S_in, uint8_t* hat,
+                    int32_t* iters, uint8_t* ok, int32_t on_device, void* stream)
+{
+    if (!u) return fail(JBP_EINVAL, "NULL handle");
+    if (F < 0) return fail(JBP_EINVAL, "F must be >= 0");
+    if (F == 0) return JBP_OK;
+    const UraDev& d = u->u;
+    if ((what & 1) && !y) return fail(JBP_EINVAL, "NULL y");
+    if (what == 1 && !S_io) return fail(JBP_EINVAL, "NULL S");
+    if (what == 2 && !S_in) return fail(JBP_EINVAL, "NULL S");
+    if ((what & 2) && (!hat || !iters || !ok)) return fail(JBP_EINVAL, "NULL output buffer");
+    jbp_ctx* ctx = u->ctx;
+    JBP_CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    std::lock_guard<std::mutex> lk(u->mu);
+    const size_t ybytes = sizeof(float) * (size_t)F * d.n * d.ns * 2;
+    const size_t sbytes = sizeof(float) * (size_t)F * d.n * d.Q;
+    const size_t hbytes = (size_t)F * d.K * d.n;
+    if (on_device) {
+        cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+        return ura_run(u, what, F, y, what == 1 ? S_io : const_cast<float*>(S_in), hat, iters, ok, s);
+    }
+    cudaStream_t s = ctx->stream;
+    int rc;
+    if ((what & 1) && (rc = ura_grow(u, u->y, ybytes))) return rc;
+    if (what != 3 && (rc = ura_grow(u, u->S, sbytes))) return rc;
+    if ((what & 2) && ((rc = ura_grow(u, u->hat, hbytes)) || (rc = ura_grow(u, u->iters, sizeof(int32_t) * F * d.K)) ||
+                       (rc = ura_grow(u, u->ok, (size_t)F * d.K))))
+        return rc;
+    if (what & 1) JBP_CU(cudaMemcpyAsync(P<float>(u->y), y, ybytes, cudaMemcpyHostToDevice, s), "copy y");
+    if (what == 2) JBP_CU(cudaMemcpyAsync(P<float>(u->S), S_in, sbytes, cudaMemcpyHostToDevice, s), "copy S");
+    rc = ura_run(u, what, F, P<float>(u->y), P<float>(u->S), P<uint8_t>(u->hat), P<int32_t>(u->iters), P<uint8_t>(u->ok), s);
+    if (rc) return rc;
+    if (what == 1) JBP_CU(cudaMemcpyAsync(S_io, P<float>(u->S), sbytes, cudaMemcpyDeviceToHost, s), "copy S");
+    if (what & 2) {
+        JBP_CU(cudaMemcpyAsync(hat, P<uint8_t>(u->hat), hbytes, cudaMemcpyDeviceToHost, s), "copy hat");
+        JBP_CU(cudaMemcpyAsync(iters, P<int32_t>(u->iters), sizeof(int32_t) * F * d.K, cudaMemcpyDeviceToHost, s), "copy iters");
+        JBP_CU(cudaMemcpyAsync(ok, P<uint8_t>(u->ok), (size_t)F * d.K, cudaMemcpyDeviceToHost, s), "copy ok");
+    }
+    JBP_CU(cudaStreamSynchronize(s), "evidence path");
+    return JBP_OK;
+}
+
+extern "C" int jbp_amp_evidence(jbp_ura* u, int32_t F, const float* y, float* S, int32_t on_device, void* stream)
+{
+    return ura_call(u, 1, F, y, S, nullptr, nullptr, nullptr, nullptr, on_device, stream);
+}
+
+extern "C" int jbp_sic_decode(jbp_ura* u, int32_t F, const float* S, uint8_t* hat, int32_t* iters, uint8_t* ok,
+                              int32_t on_device, void* stream)
+{
+    return ura_call(u, 2, F, nullptr, nullptr, S, hat, iters, ok, on_device, stream);
+}
+
+extern "C" int jbp_ura_decode(jbp_ura* u, int32_t F, const float* y, uint8_t* hat, int32_t* iters, uint8_t* ok,
+                              int32_t on_device, void* stream)
+{
+    return ura_call(u, 3, F, y, nullptr, nullptr, hat, iters, ok, on_device, stream);
+}

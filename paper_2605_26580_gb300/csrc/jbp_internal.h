@@ -55,6 +55,30 @@ cudaError_t launch_fused(const Graph& g, const FusedPlan& plan, int F, const flo
                          int early_stop, uint8_t* hat, int32_t* iters, uint8_t* ok, float* post,
                          cudaStream_t s);
 
+// Evidence-interface path (jbp_ura.cu): slot-wise AMP detector and SIC row
+// decoder.  Device tables and scalars of one (code, detector) pair.
+struct UraDev {
+    int n, P, dc, K, Q;          // slots = variables, checks, check degree, rows, field size
+    int ns;                      // complex channel uses per slot (rows of the partial DFT)
+    int amp_iters, bp_iters, early_stop;
+    float log_odds;              // log((1 - rho) / rho)
+    float su2;                   // variance of an active coordinate
+    float inv_sqrt_ns;           // 1 / sqrt(ns)
+    float cancel_log;            // SIC: log-evidence added to a decided symbol
+    const int32_t* rows;         // [n*ns] partial-DFT rows of each slot
+    const float* tw;             // [2*Q] exp(-2 pi i k / Q), interleaved
+    const int32_t* chk_var;      // [P*dc]
+    const uint8_t* chk_coef;     // [P*dc]
+    const int32_t* var_edge;     // [2n] the two edges of each variable
+    const uint8_t* gf_mul;       // [Q*Q]
+    const uint8_t* gf_div;       // [Q*Q]
+};
+// Warps (frames) per CTA of the SIC kernel, 0 if one frame does not fit.
+int sic_warps_per_cta(const UraDev& u, const DeviceInfo& di);
+cudaError_t launch_amp(const UraDev& u, const DeviceInfo& di, int F, const float* y, float* S, cudaStream_t s);
+cudaError_t launch_sic(const UraDev& u, const DeviceInfo& di, int F, const float* S, uint8_t* hat, int32_t* iters,
+                       uint8_t* ok, cudaStream_t s);
+
 // Record the message returned by jbp_last_error() on this thread (jbp_capi.cu).
 void set_last_error(const char* msg);
 

@@ -24,6 +24,7 @@ EXPORTS = [
     "jbp_context_create", "jbp_context_destroy", "jbp_create", "jbp_destroy", "jbp_decode",
     "jbp_submit", "jbp_poll", "jbp_serving_stats", "jbp_last_error", "jbp_step_channel",
     "jbp_step_check", "jbp_step_var", "jbp_step_syndrome", "jbp_query", "jbp_decode_noalloc", "jbp_stats", "jbp_decode_many", "jbp_tune",
+    "jbp_ura_create", "jbp_ura_destroy", "jbp_amp_evidence", "jbp_sic_decode", "jbp_ura_decode",
 ]
 
 
@@ -45,6 +46,12 @@ class Channel(C.Structure):
 class Options(C.Structure):
     _fields_ = [("iters", C.c_int32), ("early_stop", C.c_int32), ("precision", C.c_int32), ("device", C.c_int32),
                 ("mem_budget_bytes", C.c_int64), ("block_iters", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class UraParams(C.Structure):
+    _fields_ = [("ns", C.c_int32), ("K", C.c_int32), ("amp_iters", C.c_int32), ("bp_iters", C.c_int32),
+                ("early_stop", C.c_int32), ("reserved", C.c_int32), ("rho_bg", C.c_double),
+                ("sigma_u2", C.c_double), ("cancel_log", C.c_double), ("rows", C.POINTER(C.c_int32))]
 
 
 class Batch(C.Structure):
@@ -86,6 +93,11 @@ def lib():
             L.jbp_stats.argtypes = [vp, C.POINTER(u64), C.POINTER(i32)]
             L.jbp_decode_noalloc.argtypes = [C.POINTER(Code), i32, C.POINTER(Channel), i32, i32, i32, vp, vp, vp,
                                              vp, vp]
+            L.jbp_ura_create.argtypes = [vp, C.POINTER(Code), C.POINTER(UraParams), C.POINTER(vp)]
+            L.jbp_ura_destroy.argtypes = [vp]
+            L.jbp_amp_evidence.argtypes = [vp, i32, vp, vp, i32, vp]
+            L.jbp_sic_decode.argtypes = [vp, i32, vp, vp, vp, vp, i32, vp]
+            L.jbp_ura_decode.argtypes = [vp, i32, vp, vp, vp, vp, i32, vp]
             for name in EXPORTS:
                 if name != "jbp_last_error":
                     getattr(L, name).restype = C.c_int
@@ -251,3 +263,69 @@ class Decoder:
 
     def step_syndrome(self, hat, ok, stream=None):
         check(lib().jbp_step_syndrome(self.ptr, int(hat.shape[0]), _addr(hat), _addr(ok), _stream_ptr(stream)))
+
+
+class EvidenceDecoder:
+    """The paper's classical path on the evidence interface: slot-wise AMP
+    detector (y -> S) and SIC over K rows of single-row FFT-BP (S -> rows)."""
+
+    def __init__(self, ctx: Context, code: dict, K: int, rows, rho: float, su2: float, cancel_log: float,
+                 amp_iters: int = 20, bp_iters: int = 50, early_stop: bool = True):
+        self.ctx = ctx
+        self.K, self.n, self.q = int(K), int(code["n"]), int(code["q"])
+        self._chk_var = np.ascontiguousarray(code["chk_var"], dtype=np.int32)
+        self._chk_coef = np.ascontiguousarray(code["chk_coef"], dtype=np.uint8)
+        self._rows = np.ascontiguousarray(rows, dtype=np.int32)
+        self.ns = int(self._rows.shape[1])
+        dv = code.get("dv") or int(self._chk_var.size // self.n)
+        c = Code(self.n, int(code["P"]), self.q, int(dv), int(code["dc"]),
+                 self._chk_var.ctypes.data_as(C.POINTER(C.c_int32)),
+                 self._chk_coef.ctypes.data_as(C.POINTER(C.c_uint8)))
+        p = UraParams(self.ns, self.K, int(amp_iters), int(bp_iters), int(bool(early_stop)), 0, float(rho),
+                      float(su2), float(cancel_log), self._rows.ctypes.data_as(C.POINTER(C.c_int32)))
+        h = C.c_void_p()
+        check(lib().jbp_ura_create(ctx.ptr, C.byref(c), C.byref(p), C.byref(h)))
+        self.ptr = h
+
+    def close(self):
+        if self.ptr:
+            check(lib().jbp_ura_destroy(self.ptr))
+            self.ptr = None
+
+    # host arrays: the call copies, runs and waits
+    def evidence(self, y):
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        F = int(y.shape[0])
+        S = np.empty((F, self.n, self.q), dtype=np.float32)
+        check(lib().jbp_amp_evidence(self.ptr, F, _addr(y), _addr(S), 0, None))
+        return S
+
+    def sic(self, S):
+        S = np.ascontiguousarray(S, dtype=np.float32)
+        F = int(S.shape[0])
+        out = {"hat": np.empty((F, self.K, self.n), dtype=np.uint8), "iters": np.empty((F, self.K), dtype=np.int32),
+               "ok": np.empty((F, self.K), dtype=np.uint8)}
+        check(lib().jbp_sic_decode(self.ptr, F, _addr(S), _addr(out["hat"]), _addr(out["iters"]), _addr(out["ok"]),
+                                   0, None))
+        return out
+
+    def decode(self, y):
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        F = int(y.shape[0])
+        out = {"hat": np.empty((F, self.K, self.n), dtype=np.uint8), "iters": np.empty((F, self.K), dtype=np.int32),
+               "ok": np.empty((F, self.K), dtype=np.uint8)}
+        check(lib().jbp_ura_decode(self.ptr, F, _addr(y), _addr(out["hat"]), _addr(out["iters"]), _addr(out["ok"]),
+                                   0, None))
+        return out
+
+    # device tensors: enqueued on `stream`, no wait
+    def evidence_device(self, y, S, stream=None):
+        check(lib().jbp_amp_evidence(self.ptr, int(y.shape[0]), _addr(y), _addr(S), 1, _stream_ptr(stream)))
+
+    def sic_device(self, S, hat, iters, ok, stream=None):
+        check(lib().jbp_sic_decode(self.ptr, int(S.shape[0]), _addr(S), _addr(hat), _addr(iters), _addr(ok), 1,
+                                   _stream_ptr(stream)))
+
+    def decode_device(self, y, hat, iters, ok, stream=None):
+        check(lib().jbp_ura_decode(self.ptr, int(y.shape[0]), _addr(y), _addr(hat), _addr(iters), _addr(ok), 1,
+                                   _stream_ptr(stream)))
