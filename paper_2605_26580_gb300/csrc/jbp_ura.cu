@@ -305,6 +305,8 @@ __device__ __forceinline__ int team_argmax(float val, int idx, unsigned mask)
 
 }  // namespace
 
+constexpr int kSicMaxWarps = 16;   // frames (warps) per CTA of the SIC kernel
+
 // Shared memory of the SIC kernel: CTA tables, then one region per warp.
 struct SicLayout {
     int tables;     // bytes: gf_mul, gf_div [Q*Q], coef [E], chk_var, var_edge (int16)
@@ -326,7 +328,7 @@ static SicLayout sic_layout(const UraDev& u)
 namespace {
 
 template <int Q, int DC>
-__global__ void __launch_bounds__(256) k_sic(UraDev u, SicLayout lay, int F, const float* __restrict__ S,
+__global__ void __launch_bounds__(32 * kSicMaxWarps, 1) k_sic(UraDev u, SicLayout lay, int F, const float* __restrict__ S,
                                              uint8_t* __restrict__ hat, int32_t* __restrict__ iters,
                                              uint8_t* __restrict__ ok)
 {
@@ -457,17 +459,32 @@ cudaError_t launch_sic_t(const UraDev& u, const DeviceInfo& di, int F, const flo
                          int32_t* iters, uint8_t* ok, cudaStream_t s)
 {
     const SicLayout lay = sic_layout(u);
-    const int W = sic_warps_per_cta(u, di);
-    if (W < 1) return cudaErrorInvalidConfiguration;
+    static bool attr_set = false;   // the same value from every caller: a benign race
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_sic<Q, DC>, cudaFuncAttributeMaxDynamicSharedMemorySize, di.smem_optin);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    // warps (frames) per CTA: the most resident warps per SM, no wider than the
+    // batch needs to cover every SM once
+    const int w_cap = (int)std::min<long>(kSicMaxWarps, std::max<long>(1, ((long)F + di.sm_count - 1) / di.sm_count));
+    int W = 0, best = 0, per_sm_best = 0;
+    for (int w = 1; w <= w_cap; ++w) {
+        const int smem = lay.tables + w * lay.per_warp;
+        if (smem > di.smem_optin) break;
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sic<Q, DC>, 32 * w, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm * w > best) {
+            best = per_sm * w;
+            W = w;
+            per_sm_best = per_sm;
+        }
+    }
+    if (W < 1 || per_sm_best < 1) return cudaErrorInvalidConfiguration;
     const int smem = lay.tables + W * lay.per_warp;
-    cudaError_t e = cudaFuncSetAttribute(k_sic<Q, DC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sic<Q, DC>, 32 * W, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const long need = ((long)F + W - 1) / W;
-    const int grid = (int)std::min<long>(need, (long)per_sm * di.sm_count);
+    const int grid = (int)std::min<long>(need, (long)per_sm_best * di.sm_count);
     k_sic<Q, DC><<<grid, 32 * W, smem, s>>>(u, lay, F, S, hat, iters, ok);
     return cudaGetLastError();
 }
@@ -492,7 +509,7 @@ int sic_warps_per_cta(const UraDev& u, const DeviceInfo& di)
     const SicLayout lay = sic_layout(u);
     const int room = di.smem_optin - lay.tables;
     if (room < lay.per_warp) return 0;
-    return std::min(8, room / lay.per_warp);
+    return std::min(kSicMaxWarps, room / lay.per_warp);
 }
 
 cudaError_t launch_amp(const UraDev& u, const DeviceInfo& di, int F, const float* y, float* S, cudaStream_t s)
