@@ -252,8 +252,9 @@ int jbp_decode_noalloc(const jbp_code *code, int32_t K, const jbp_channel *chan,
 
 /* Counters of a handle since creation (host pointers, may be NULL):
  * log_fallbacks = channel messages whose linear-domain computation underflowed
- * and were recomputed in log space; tc_timeouts = 1 if a tensor-core completion
- * wait (bounded) ever expired.  Synchronises the device. */
+ * and were recomputed in log space; tc_timeouts = 1 if a bounded device wait
+ * (a tensor-core completion or a staged check tile) ever expired.
+ * Synchronises the device. */
 int jbp_stats(jbp_h *h, uint64_t *log_fallbacks, int32_t *tc_timeouts);
 
 /* Shape information of a handle (host pointers, any may be NULL): edges E,

@@ -676,10 +676,11 @@ extern "C" int jbp_decode(jbp_h* h, jbp_batch* b)
     if (b->logpost)
         JBP_CU(cudaMemcpyAsync(b->logpost, dpost, sizeof(float) * vs * F, cudaMemcpyDeviceToHost, s), "copy post");
     JBP_CU(cudaStreamSynchronize(s), "jbp_decode");
-    if (ctx->opt.precision != JBP_PREC_FP32) {
+    {
+        // bounded device waits (tensor-core completions, staged check tiles) record expiry here
         int err = 0;
         JBP_CU(cudaMemcpy(&err, h->d_tc_error, sizeof err, cudaMemcpyDeviceToHost), "jbp_decode: status");
-        if (err) return fail(JBP_ETIMEOUT, "a tensor-core completion wait expired");
+        if (err) return fail(JBP_ETIMEOUT, "a bounded device wait expired");
     }
     return JBP_OK;
 }

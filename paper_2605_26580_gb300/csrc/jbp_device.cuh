@@ -906,29 +906,41 @@ __device__ __forceinline__ float team_gather(const float (&r)[Shape<Q>::V], int 
     return out;
 }
 
-// Team shape (any q).  blk: check j's four edge vectors.
+// Team shape (any q), split into the loads of one check and the rest, so that
+// a team can issue the loads of several checks before computing any of them.
 template <int Q>
-__device__ void check_team(float* blk, const uint8_t* coef, const uint8_t* gmul, const uint8_t* gdiv, TeamLane L)
+struct CheckRegs {
+    float P[kDC][Shape<Q>::V];
+    int h[kDC];
+};
+
+template <int Q>
+__device__ __forceinline__ void check_team_load(const float* blk, const uint8_t* coef, const uint8_t* gdiv,
+                                                TeamLane L, CheckRegs<Q>& c)
 {
     constexpr int T = Shape<Q>::T, V = Shape<Q>::V;
-    float P[kDC][V];
-    int h[kDC];
 #pragma unroll
     for (int d = 0; d < kDC; ++d) {
-        h[d] = coef[d];
+        c.h[d] = coef[d];
 #pragma unroll
-        for (int v = 0; v < V; ++v) P[d][v] = blk[d * Q + gdiv[h[d] * Q + v * T + L.tl]];
+        for (int v = 0; v < V; ++v) c.P[d][v] = blk[d * Q + gdiv[c.h[d] * Q + v * T + L.tl]];
     }
+}
+
+template <int Q>
+__device__ __forceinline__ void check_team_finish(float* blk, CheckRegs<Q>& c, const uint8_t* gmul, TeamLane L)
+{
+    constexpr int T = Shape<Q>::T, V = Shape<Q>::V;
 #pragma unroll
-    for (int d = 0; d < kDC; ++d) wht_team<Q>(P[d], L);
+    for (int d = 0; d < kDC; ++d) wht_team<Q>(c.P[d], L);
     float R[kDC][V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        const float l01 = P[0][v] * P[1][v], r23 = P[2][v] * P[3][v];
-        R[0][v] = P[1][v] * r23;
-        R[1][v] = P[0][v] * r23;
-        R[2][v] = l01 * P[3][v];
-        R[3][v] = l01 * P[2][v];
+        const float l01 = c.P[0][v] * c.P[1][v], r23 = c.P[2][v] * c.P[3][v];
+        R[0][v] = c.P[1][v] * r23;
+        R[1][v] = c.P[0][v] * r23;
+        R[2][v] = l01 * c.P[3][v];
+        R[3][v] = l01 * c.P[2][v];
     }
     __syncwarp(L.mask);
 #pragma unroll
@@ -942,10 +954,19 @@ __device__ void check_team(float* blk, const uint8_t* coef, const uint8_t* gmul,
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const int a = v * T + L.tl;
-            const float r = team_gather<Q>(R[d], gmul[h[d] * Q + a], L);
+            const float r = team_gather<Q>(R[d], gmul[c.h[d] * Q + a], L);
             blk[d * Q + a] = fmaxf(r, fl) * inv;
         }
     }
+}
+
+// Team shape (any q).  blk: check j's four edge vectors.
+template <int Q>
+__device__ void check_team(float* blk, const uint8_t* coef, const uint8_t* gmul, const uint8_t* gdiv, TeamLane L)
+{
+    CheckRegs<Q> c;
+    check_team_load<Q>(blk, coef, gdiv, L, c);
+    check_team_finish<Q>(blk, c, gmul, L);
 }
 
 // ---------------------------------------------------------------------------

@@ -80,22 +80,264 @@ __global__ void __launch_bounds__(kStepThreads) k_channel_team(Graph g, int F, c
     }
 }
 
-// (b) check node (FP32 Walsh-Hadamard butterflies).  Team per (frame, user, check).
-template <int Q>
-__global__ void __launch_bounds__(kStepThreads) k_check(Graph g, int F, float* msg, const uint8_t* __restrict__ active)
+// (b) check node (FP32 Walsh-Hadamard butterflies), shared-memory staged: a CTA
+// takes tiles of consecutive check blocks (contiguous in HBM), brought in by one
+// TMA bulk copy each (double-buffered, completion on an mbarrier) and written
+// back by a TMA bulk store; max(1, q/16) lanes per check run the transforms,
+// 16 symbols per lane in registers.  Every wait is bounded: on expiry the CTA records the error in
+// g.tc_error, waits (bounded) for its copies in flight and returns.
+constexpr int kStageThreads = 128;   // threads per CTA; a tile holds kStageThreads / LPC checks
+constexpr long long kStageSpin = 1ll << 24;
+
+__device__ __forceinline__ uint32_t s_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar)
 {
-    constexpr int T = Shape<Q>::T;
-    __shared__ uint8_t smul[Q * Q], sdiv[Q * Q];
-    load_gf<Q>(g, smul, sdiv);
-    const int teams = blockDim.x / T, team = threadIdx.x / T;
-    const TeamLane L = team_lane<T>();
-    const long per_frame = (long)g.K * g.P, total = (long)F * per_frame;
-    for (long unit = (long)blockIdx.x * teams + team; unit < total; unit += (long)gridDim.x * teams) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_store(void* dst, uint32_t src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ bool mbar_done(uint32_t mbar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity)
+{
+    long long spins = 0;
+    bool done;
+    while (!(done = mbar_done(mbar, parity)) && ++spins < kStageSpin) {
+    }
+    return done;
+}
+
+// Check j on a block in shared memory, LPC = max(1, q/16) lanes per check,
+// lane l holding the 16 symbols x = 16 l + j (j < 16): the coefficient
+// permutation x -> h^{-1} x is GF(2)-linear, so each permuted offset is an XOR
+// of the images of the basis vectors; the transform's stages over the low four
+// bits of x run in registers and the rest across the check's lanes; the
+// leave-one-out products are formed one edge at a time (same association as
+// check_thread).
+template <int Q>
+struct StageShape {
+    static constexpr int LPC = Q > 16 ? Q / 16 : 1;   // lanes per check
+    static constexpr int W = Q / LPC;                  // symbols per lane
+};
+
+template <int Q>
+__device__ __forceinline__ void wht_lanes(float (&p)[StageShape<Q>::W], int l, unsigned mask)
+{
+    constexpr int LPC = StageShape<Q>::LPC, W = StageShape<Q>::W;
+    wht_reg<W>(p);
+#pragma unroll
+    for (int o = 1; o < LPC; o <<= 1) {
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const float t = __shfl_xor_sync(mask, p[j], o, LPC);
+            p[j] = (l & o) ? (t - p[j]) : (p[j] + t);
+        }
+    }
+}
+
+template <int Q>
+__device__ __forceinline__ void check_lanes_lin(float* blk, const uint8_t* coef, const uint8_t* gdiv, int l,
+                                                unsigned mask)
+{
+    constexpr int LPC = StageShape<Q>::LPC, W = StageShape<Q>::W;
+    float P[kDC][W];
+    int basis[kDC][4];   // images of the low four basis vectors
+    int lane_off[kDC];   // image of 16 l
+#pragma unroll
+    for (int d = 0; d < kDC; ++d) {
+        const uint8_t* dv = gdiv + coef[d] * Q;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) basis[d][b] = ((1 << b) < W) ? dv[1 << b] : 0;
+        lane_off[d] = LPC > 1 ? dv[W * l] : 0;
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            int o = lane_off[d];
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (j & (1 << b)) o ^= basis[d][b];
+            P[d][j] = blk[d * Q + o];
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < kDC; ++d) wht_lanes<Q>(P[d], l, mask);
+#pragma unroll
+    for (int d = 0; d < kDC; ++d) {
+        float R[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const float l01 = P[0][j] * P[1][j], r23 = P[2][j] * P[3][j];
+            R[j] = d == 0 ? P[1][j] * r23 : d == 1 ? P[0][j] * r23 : d == 2 ? l01 * P[3][j] : l01 * P[2][j];
+        }
+        wht_lanes<Q>(R, l, mask);
+        float mx = vmax(R);
+#pragma unroll
+        for (int o = 1; o < LPC; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(mask, mx, o, LPC));
+        const float fl = kRelFloor * mx, inv = 1.0f / mx;
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            int o = lane_off[d];
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (j & (1 << b)) o ^= basis[d][b];
+            blk[d * Q + o] = fmaxf(R[j], fl) * inv;
+        }
+    }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kStageThreads, 3) k_check_staged(Graph g, long total, float* msg,
+                                                                  const uint8_t* __restrict__ active)
+{
+    constexpr int CB = kDC * Q;   // floats per check block
+    constexpr int LPC = StageShape<Q>::LPC, kStageChecks = kStageThreads / LPC;
+    extern __shared__ __align__(128) float tiles[];   // [2][kStageChecks * CB]
+    __shared__ __align__(8) uint64_t mbar_s[2];
+    __shared__ uint8_t sdiv[Q * Q];
+    for (int i = threadIdx.x; i < Q * Q; i += blockDim.x) sdiv[i] = g.gf_div[i];
+    const uint32_t mb0 = s_addr(&mbar_s[0]), mb1 = s_addr(&mbar_s[1]);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const long ntiles = (total + kStageChecks - 1) / kStageChecks;
+    const long per_frame = (long)g.K * g.P;
+    auto tile_bytes = [&](long t) -> uint32_t {
+        const long c = total - t * kStageChecks;
+        return (uint32_t)((c < kStageChecks ? c : kStageChecks) * CB * sizeof(float));
+    };
+    auto tile_ptr = [&](long t) { return msg + (size_t)t * kStageChecks * CB; };
+    // parity of each buffer's mbarrier, and whether a load into it is in flight
+    // (or landed and not yet consumed)
+    uint32_t par0 = 0, par1 = 0;
+    bool pend0 = false, pend1 = false;
+    long tile = blockIdx.x;
+    if (tile < ntiles) {
+        if (threadIdx.x == 0) bulk_load(s_addr(tiles), tile_ptr(tile), tile_bytes(tile), mb0);
+        pend0 = true;
+    }
+    bool failed = false;
+    for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
+        const bool odd = it & 1;
+        float* buf = tiles + (odd ? (size_t)kStageChecks * CB : 0);
+        float* other = tiles + (odd ? 0 : (size_t)kStageChecks * CB);
+        const long next = tile + gridDim.x;
+        if (next < ntiles) {
+            if (threadIdx.x == 0) {
+                // the bulk store that last read the other buffer must be done reading it
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                bulk_load(s_addr(other), tile_ptr(next), tile_bytes(next), odd ? mb0 : mb1);
+            }
+            if (odd) pend0 = true;
+            else pend1 = true;
+        }
+        const bool done = mbar_wait_bounded(odd ? mb1 : mb0, odd ? par1 : par0);
+        if (__syncthreads_or(done ? 0 : 1)) {
+            failed = true;
+            break;
+        }
+        if (odd) {
+            par1 ^= 1;
+            pend1 = false;
+        } else {
+            par0 ^= 1;
+            pend0 = false;
+        }
+        const int slot = threadIdx.x / LPC, l = threadIdx.x % LPC;
+        const unsigned mask = LPC == 1 ? 0xffffffffu : (((1u << LPC) - 1u) << ((threadIdx.x & 31) & ~(LPC - 1)));
+        const long c = tile * kStageChecks + slot;
+        if (c < total && (!active || active[c / per_frame]))
+            check_lanes_lin<Q>(buf + slot * CB, g.chk_coef + kDC * (int)(c % g.P), sdiv, l, mask);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) bulk_store(tile_ptr(tile), s_addr(buf), tile_bytes(tile));
+    }
+    if (threadIdx.x == 0) {
+        if (failed) {
+            if (g.tc_error) atomicExch(g.tc_error, 1);
+            // loads still in flight land in this CTA's shared memory: wait for them (bounded)
+            if (pend0) mbar_wait_bounded(mb0, par0);
+            if (pend1) mbar_wait_bounded(mb1, par1);
+        }
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    }
+}
+
+// (c) posterior and decision, thread shape for q <= 16 and dv = 2: one thread
+// per (frame, user, variable) with 16-byte loads of the channel message and
+// of both edge messages.
+template <int Q>
+__global__ void __launch_bounds__(kStepThreads) k_var_thread(Graph g, int F, const float* __restrict__ ch2v,
+                                                             const float* __restrict__ msg, float* logpost,
+                                                             uint8_t* hat, const uint8_t* __restrict__ active)
+{
+    const long per_frame = (long)g.K * g.n, total = (long)F * per_frame;
+    const int cbs = 4 * Q;
+    for (long unit = (long)blockIdx.x * blockDim.x + threadIdx.x; unit < total; unit += (long)gridDim.x * blockDim.x) {
         const int f = (int)(unit / per_frame);
         if (active && !active[f]) continue;
-        const long fk_j = unit;   // ((f*K + k)*P + j): blocks are contiguous in this order
-        const int j = (int)(unit % g.P);
-        check_team<Q>(msg + (size_t)fk_j * 4 * Q, g.chk_coef + 4 * j, smul, sdiv, L);
+        const int rem = (int)(unit % per_frame), k = rem / g.n, i = rem % g.n;
+        const size_t fk = (size_t)f * g.K + k;
+        const float* blk = msg + fk * g.E * Q;
+        const float* c0 = ch2v + (fk * g.n + i) * Q;
+        const float* p0 = edge_ptr(blk, g.var_edge[2 * i], cbs, Q);
+        const float* p1 = edge_ptr(blk, g.var_edge[2 * i + 1], cbs, Q);
+        float b[Q], m0[Q], m1[Q];
+        if constexpr (Q >= 4) {
+#pragma unroll
+            for (int x = 0; x < Q; x += 4) {
+                const float4 u = *reinterpret_cast<const float4*>(c0 + x);
+                const float4 v = *reinterpret_cast<const float4*>(p0 + x);
+                const float4 w = *reinterpret_cast<const float4*>(p1 + x);
+                b[x] = u.x; b[x + 1] = u.y; b[x + 2] = u.z; b[x + 3] = u.w;
+                m0[x] = v.x; m0[x + 1] = v.y; m0[x + 2] = v.z; m0[x + 3] = v.w;
+                m1[x] = w.x; m1[x + 1] = w.y; m1[x + 2] = w.z; m1[x + 3] = w.w;
+            }
+        } else {
+#pragma unroll
+            for (int x = 0; x < Q; ++x) {
+                b[x] = c0[x];
+                m0[x] = p0[x];
+                m1[x] = p1[x];
+            }
+        }
+        float bv = -1.0f;
+        int bi = 0;
+#pragma unroll
+        for (int x = 0; x < Q; ++x) {
+            b[x] *= m0[x];
+            b[x] *= m1[x];
+            if (b[x] > bv) {
+                bv = b[x];
+                bi = x;
+            }
+        }
+        hat[fk * g.n + i] = (uint8_t)bi;
+        if (logpost) {
+            const float l = __logf(bv);
+#pragma unroll
+            for (int x = 0; x < Q; ++x) logpost[(fk * g.n + i) * Q + x] = __logf(b[x]) - l;
+        }
     }
 }
 
@@ -116,6 +358,69 @@ __global__ void __launch_bounds__(kStepThreads) k_var(Graph g, int F, const floa
         const size_t fk = (size_t)f * g.K + k;
         var_team<Q>(g, ch2v + fk * g.n * Q, msg + fk * g.E * Q, 4 * Q, i, logpost ? logpost + fk * g.n * Q : nullptr,
                     hat + fk * g.n, L);
+    }
+}
+
+// (c) posterior and decision for q >= 32 and dv = 2: four lanes per (frame,
+// user, variable), q/4 symbols per lane read with 16-byte loads.
+template <int Q>
+__global__ void __launch_bounds__(kStepThreads) k_var_quad(Graph g, int F, const float* __restrict__ ch2v,
+                                                           const float* __restrict__ msg, float* logpost,
+                                                           uint8_t* hat, const uint8_t* __restrict__ active)
+{
+    static_assert(Q >= 16, "four lanes of at least four symbols");
+    constexpr int W = Q / 4;
+    const int sub = threadIdx.x & 3;
+    const unsigned mask = 0xfu << ((threadIdx.x & 31) & ~3);
+    const long per_frame = (long)g.K * g.n, total = (long)F * per_frame;
+    const int cbs = 4 * Q;
+    const long first = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 2, stride = ((long)gridDim.x * blockDim.x) >> 2;
+    for (long unit = first; unit < total; unit += stride) {
+        const int f = (int)(unit / per_frame);
+        if (active && !active[f]) continue;
+        const int rem = (int)(unit % per_frame), k = rem / g.n, i = rem % g.n;
+        const size_t fk = (size_t)f * g.K + k;
+        const float* blk = msg + fk * g.E * Q;
+        const float* c0 = ch2v + (fk * g.n + i) * Q + sub * W;
+        const float* p0 = edge_ptr(blk, g.var_edge[2 * i], cbs, Q) + sub * W;
+        const float* p1 = edge_ptr(blk, g.var_edge[2 * i + 1], cbs, Q) + sub * W;
+        float b[W], m0[W], m1[W];
+#pragma unroll
+        for (int x = 0; x < W; x += 4) {
+            const float4 u = *reinterpret_cast<const float4*>(c0 + x);
+            const float4 v = *reinterpret_cast<const float4*>(p0 + x);
+            const float4 w = *reinterpret_cast<const float4*>(p1 + x);
+            b[x] = u.x; b[x + 1] = u.y; b[x + 2] = u.z; b[x + 3] = u.w;
+            m0[x] = v.x; m0[x + 1] = v.y; m0[x + 2] = v.z; m0[x + 3] = v.w;
+            m1[x] = w.x; m1[x + 1] = w.y; m1[x + 2] = w.z; m1[x + 3] = w.w;
+        }
+        float bv = -1.0f;
+        int bi = 0;
+#pragma unroll
+        for (int x = 0; x < W; ++x) {
+            b[x] *= m0[x];
+            b[x] *= m1[x];
+            if (b[x] > bv) {
+                bv = b[x];
+                bi = sub * W + x;
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < 4; o <<= 1) {
+            const float ov = __shfl_xor_sync(mask, bv, o, 4);
+            const int oi = __shfl_xor_sync(mask, bi, o, 4);
+            if (ov > bv || (ov == bv && oi < bi)) {
+                bv = ov;
+                bi = oi;
+            }
+        }
+        if (sub == 0) hat[fk * g.n + i] = (uint8_t)bi;
+        if (logpost) {
+            const float l = __logf(bv);
+            float* lp = logpost + (fk * g.n + i) * Q + sub * W;
+#pragma unroll
+            for (int x = 0; x < W; ++x) lp[x] = __logf(b[x]) - l;
+        }
     }
 }
 
@@ -214,11 +519,14 @@ cudaError_t channel_q(const Graph& g, const DeviceInfo& di, int F, const float* 
 template <int Q>
 cudaError_t check_q(const Graph& g, const DeviceInfo& di, int F, float* msg, const uint8_t* active, cudaStream_t s)
 {
-    constexpr int T = Shape<Q>::T;
     if (g.dc != kDC) return cudaErrorInvalidValue;
     const long units = (long)F * g.K * g.P;
-    const int grid = persistent_grid(k_check<Q>, kStepThreads, 0, di, kStepThreads / T, units);
-    k_check<Q><<<grid, kStepThreads, 0, s>>>(g, F, msg, active);
+    constexpr int checks_per_tile = kStageThreads / StageShape<Q>::LPC;
+    const size_t smem = 2ull * checks_per_tile * kDC * Q * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_check_staged<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = persistent_grid(k_check_staged<Q>, kStageThreads, smem, di, checks_per_tile, units);
+    k_check_staged<Q><<<grid, kStageThreads, smem, s>>>(g, units, msg, active);
     return cudaGetLastError();
 }
 
@@ -228,6 +536,16 @@ cudaError_t var_q(const Graph& g, const DeviceInfo& di, int F, const float* ch2v
 {
     constexpr int T = Shape<Q>::T;
     const long units = (long)F * g.K * g.n;
+    if (g.dv == 2) {
+        if constexpr (Q <= 16) {
+            const int grid = persistent_grid(k_var_thread<Q>, kStepThreads, 0, di, kStepThreads, units);
+            k_var_thread<Q><<<grid, kStepThreads, 0, s>>>(g, F, ch2v, msg, post, hat, active);
+        } else {
+            const int grid = persistent_grid(k_var_quad<Q>, kStepThreads, 0, di, kStepThreads / 4, units);
+            k_var_quad<Q><<<grid, kStepThreads, 0, s>>>(g, F, ch2v, msg, post, hat, active);
+        }
+        return cudaGetLastError();
+    }
     const int grid = persistent_grid(k_var<Q>, kStepThreads, 0, di, kStepThreads / T, units);
     k_var<Q><<<grid, kStepThreads, 0, s>>>(g, F, ch2v, msg, post, hat, active);
     return cudaGetLastError();
