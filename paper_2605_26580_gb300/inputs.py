@@ -121,6 +121,102 @@ def make_code(n: int, q: int, dv: int = 2, dc: int = 4, seed: int | None = None)
     return code
 
 
+def make_peg_code(n: int, q: int, dv: int = 2, dc: int = 3, seed: int | None = None) -> dict:
+    """Regular (dv, dc) GF(q) LDPC code by progressive edge growth.
+
+    Variables are placed one at a time.  A variable's first edge goes to a check
+    of the lowest current degree; each further edge goes to a check as far as
+    possible from the variable in the graph built so far (unreachable checks
+    first, else those at the largest breadth-first depth), again of the lowest
+    current degree.  Only checks below degree dc are candidates, so the code is
+    check-regular; remaining ties are broken by a seeded random draw.
+    Coefficients are i.i.d. uniform on {1, ..., q-1}.
+    """
+    m = log2_exact(q)
+    if (n * dv) % dc:
+        raise ValueError("n*dv must be a multiple of dc")
+    P = n * dv // dc
+    rng = np.random.Generator(np.random.PCG64((code_seed(n, q) + 11) if seed is None else seed))
+    var_chk = [[] for _ in range(n)]
+    chk_vars = [[] for _ in range(P)]
+    for v in range(n):
+        for k in range(dv):
+            open_ = [c for c in range(P) if len(chk_vars[c]) < dc and c not in var_chk[v]]
+            if k == 0:
+                cand = open_
+            else:
+                # breadth-first depths of the checks reachable from v
+                depth = {}
+                frontier = list(var_chk[v])
+                for c in frontier:
+                    depth[c] = 0
+                seen_v = {v}
+                d = 0
+                while frontier:
+                    nxt = []
+                    for c in frontier:
+                        for u in chk_vars[c]:
+                            if u in seen_v:
+                                continue
+                            seen_v.add(u)
+                            for c2 in var_chk[u]:
+                                if c2 not in depth:
+                                    depth[c2] = d + 1
+                                    nxt.append(c2)
+                    frontier = nxt
+                    d += 1
+                far = [c for c in open_ if c not in depth]
+                if not far:
+                    best = max(depth[c] for c in open_)
+                    far = [c for c in open_ if depth[c] == best]
+                cand = far
+            low = min(len(chk_vars[c]) for c in cand)
+            cand = [c for c in cand if len(chk_vars[c]) == low]
+            c = int(cand[int(rng.integers(0, len(cand)))])
+            var_chk[v].append(c)
+            chk_vars[c].append(v)
+    chk_var = np.array([v for c in range(P) for v in chk_vars[c]], dtype=np.int32)
+    chk_coef = rng.integers(1, q, size=P * dc).astype(np.uint8)
+    code = {"n": n, "P": P, "q": q, "m": m, "dv": dv, "dc": dc, "chk_var": chk_var, "chk_coef": chk_coef}
+    code.update(_encoder(code))
+    return code
+
+
+def girth(code: dict) -> int:
+    """Length of the shortest cycle of the Tanner graph (breadth-first from every
+    variable; 0 if the graph has no cycle)."""
+    n, P, dc = code["n"], code["P"], code["dc"]
+    cv = np.asarray(code["chk_var"]).reshape(P, dc)
+    var_chk = [[] for _ in range(n)]
+    for j in range(P):
+        for v in cv[j]:
+            var_chk[int(v)].append(j)
+    best = 0
+    for s in range(n):
+        # nodes: variables as ("v", i), checks as ("c", j); BFS with parent tracking
+        dist = {("v", s): 0}
+        parent = {("v", s): None}
+        queue = [("v", s)]
+        qi = 0
+        while qi < len(queue):
+            node = queue[qi]
+            qi += 1
+            kind, idx = node
+            nbrs = [("c", j) for j in var_chk[idx]] if kind == "v" else [("v", int(u)) for u in cv[idx]]
+            for nb in nbrs:
+                if nb == parent[node]:
+                    continue
+                if nb in dist:
+                    cyc = dist[node] + dist[nb] + 1
+                    if best == 0 or cyc < best:
+                        best = cyc
+                else:
+                    dist[nb] = dist[node] + 1
+                    parent[nb] = node
+                    queue.append(nb)
+    return best
+
+
 def code_from_edges(n: int, q: int, dc: int, chk_var, chk_coef) -> dict:
     """Wrap an explicit check-major edge list (any variable degrees)."""
     chk_var = np.asarray(chk_var, dtype=np.int32).reshape(-1)

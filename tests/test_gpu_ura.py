@@ -99,6 +99,21 @@ def test_sic_decode_matches_oracle(jbp_lib, oracle, L, eb, K):
     assert n >= 0.9 * 96 * K
 
 
+def test_sic_on_a_peg_code_matches_oracle(jbp_lib, oracle):
+    """The progressive-edge-growth code of the paper's PEG-LDPC comparison
+    shape (Q=64, L=12, K=2)."""
+    code = I.make_peg_code(12, 64)
+    fr = I.make_ura_frames(code, 2, 6.0, 96, seed=77)
+    S = oracle.amp_evidence(64, fr["rows"], fr["y"], 20, fr["rho"], fr["su2"]).astype(np.float32)
+    ref = oracle.sic_decode(code, 2, S.astype(np.float64), 50, fr["cancel_log"])
+    ctx = _ctx(jbp_lib)
+    dec = jbp_lib.EvidenceDecoder(ctx, code, 2, fr["rows"], fr["rho"], fr["su2"], fr["cancel_log"])
+    got = dec.sic(S)
+    dec.close()
+    ctx.close()
+    assert _compare_sic(got, ref, 2) >= 0.9 * 192
+
+
 def test_sic_other_fields_and_degrees(jbp_lib, oracle):
     """q = 16 with dc = 4 and q = 32 with dc = 3, random evidence, K = 2."""
     for q, dc, n in [(16, 4, 24), (32, 3, 18)]:

@@ -102,3 +102,27 @@ def test_ura_noise_is_unit_complex_gaussian():
     b = I.make_ura_frames(code, 2, 10.0, 400, seed=2, noiseless=True)
     w = (a["y"] - b["y"]).reshape(-1, 2).astype(np.float64)
     assert abs(w.var(axis=0).mean() - 0.5) < 0.01
+
+
+def test_girth_of_known_graphs():
+    # two variables on the same two checks: a 4-cycle
+    four = I.code_from_edges(4, 4, 2, [0, 1, 0, 1, 2, 3], [1, 1, 1, 1, 1, 1])
+    assert I.girth(four) == 4
+    # two checks of degree 3 sharing one variable: no cycle
+    tree = I.code_from_edges(5, 4, 3, [0, 1, 2, 2, 3, 4], [1, 2, 3, 2, 1, 3])
+    assert I.girth(tree) == 0
+    # a 6-cycle: v0-c0-v1-c1-v2-c2-v0
+    six = I.code_from_edges(3, 4, 2, [0, 1, 1, 2, 2, 0], [1, 1, 1, 1, 1, 1])
+    assert I.girth(six) == 6
+
+
+@pytest.mark.parametrize("L", [12, 24, 48])
+def test_peg_codes_are_regular_with_larger_girth(L):
+    c = I.make_peg_code(L, 64)
+    assert c["P"] == 2 * L // 3 and c["k"] == L // 3
+    assert set(np.bincount(c["chk_var"], minlength=L).tolist()) == {2}
+    for j in range(c["P"]):
+        assert len(set(c["chk_var"][3 * j:3 * j + 3].tolist())) == 3
+    assert I.girth(c) > I.girth(I.make_code(L, 64, dv=2, dc=3))
+    again = I.make_peg_code(L, 64)
+    assert np.array_equal(c["chk_var"], again["chk_var"]) and np.array_equal(c["chk_coef"], again["chk_coef"])
