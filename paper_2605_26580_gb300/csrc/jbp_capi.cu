@@ -1,6 +1,7 @@
 // jbp_capi.cu -- the C ABI (include/jbp.h): contexts, decoder handles, the three
 // launch forms, single-step entry points and the continuous-batching serving loop.
 #include <algorithm>
+#include <memory>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -122,20 +123,36 @@ struct Result {
     int32_t iters = 0;
 };
 
-struct Slot {
+// Resident pool of the serving loop: step-form state of up to `cap` frame slots
+// of one decoder, kept in HBM across blocks of iterations.
+struct ServePool {
+    jbp_h* h = nullptr;
+    int cap = 0;                   // frame slots
+    int hi = 0;                    // 1 + highest slot in use
+    int n_active = 0;              // slots holding a frame that has not been harvested
+    bool running = false;          // a block is in flight
+    double last_used = 0;
+    int64_t bytes = 0;             // device bytes held
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
-    Workspace ws;
-    size_t host_cap = 0;   // bytes of each pinned array below
-    float* h_y = nullptr;
-    float* h_sig = nullptr;
-    uint8_t* h_hat = nullptr;
+    DevBuf msg, ch2v, y, sig, active, t, unsat, ok, hat, fin, adm_slot, adm_y, adm_sig, count;
+    // pinned staging of an admission, and the harvest count of the last block
+    int32_t* h_adm_slot = nullptr;
+    float* h_adm_y = nullptr;
+    float* h_adm_sig = nullptr;
+    int32_t* h_count = nullptr;
+    // harvest area: host-mapped, written by the device (h_*: host view, d_*: device view)
+    int32_t* h_slot = nullptr;
     int32_t* h_iters = nullptr;
     uint8_t* h_ok = nullptr;
-    bool busy = false;
-    jbp_h* h = nullptr;          // decoder of the batch in flight (set under the context lock)
-    std::vector<Request> reqs;
-    int64_t state_bytes = 0;
+    uint8_t* h_hat = nullptr;
+    int32_t* d_slot = nullptr;
+    int32_t* d_iters = nullptr;
+    uint8_t* d_ok = nullptr;
+    uint8_t* d_hat = nullptr;
+    std::vector<Request> req;      // [cap] the request each used slot holds
+    std::vector<uint8_t> used;     // [cap]
+    std::vector<int> free_list;
 };
 
 }  // namespace
@@ -161,8 +178,9 @@ struct jbp_ctx {
     bool stop = false;
     bool server_started = false;
     std::thread server;
-    std::vector<Slot> slots;
-    int64_t inflight_bytes = 0;
+    std::vector<std::unique_ptr<ServePool>> serve_pools;   // touched by the server thread only
+    int64_t pool_bytes = 0;                                 // device bytes of the pools (server thread)
+    std::unordered_map<const jbp_h*, int> pool_of;          // decoders that own a pool (under mu)
     int handles = 0;
 
     // multi-part decodes: stream pool, fork/join events, graphs keyed by arguments
@@ -198,6 +216,7 @@ struct jbp_h {
     int tune_threads = 0, tune_fpc = 0;   // fused launch shape chosen by the autotuner (0 = default)
     bool tuned = false;
     uint64_t ws_gen = 0;                  // bumped whenever h->ws is reallocated (invalidates graphs)
+    bool closing = false;                 // jbp_destroy in progress (under ctx->mu)
 
     Graph graph() const
     {
@@ -382,6 +401,7 @@ static int decode_device(jbp_h* h, Workspace& w, int form, int F, const float* y
 // ---------------------------------------------------------------------------
 
 static void server_main(jbp_ctx* ctx);
+static void pool_destroy(jbp_ctx* ctx, ServePool* p);
 
 extern "C" int jbp_context_create(const jbp_options* opt, jbp_ctx** out)
 {
@@ -423,13 +443,9 @@ extern "C" int jbp_context_destroy(jbp_ctx* ctx)
     ctx->cv.notify_all();
     if (ctx->server.joinable()) ctx->server.join();
     cudaSetDevice(ctx->device);
-    for (Slot& s : ctx->slots) {
-        if (s.stream) cudaStreamSynchronize(s.stream);
-        ws_release(ctx, s.ws);
-        if (s.done) cudaEventDestroy(s.done);
-        if (s.stream) cudaStreamDestroy(s.stream);
-        cudaFreeHost(s.h_y); cudaFreeHost(s.h_hat); cudaFreeHost(s.h_iters); cudaFreeHost(s.h_ok);
-        cudaFreeHost(s.h_sig);
+    while (!ctx->serve_pools.empty()) {
+        pool_destroy(ctx, ctx->serve_pools.back().get());
+        ctx->serve_pools.pop_back();
     }
     for (auto& kv : ctx->graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -572,11 +588,10 @@ extern "C" int jbp_destroy(jbp_h* h)
                 ++it;
             }
         }
-        ctx->cv_idle.wait(lk, [&] {
-            for (const Slot& s : ctx->slots)
-                if (s.busy && s.h == h) return false;
-            return true;
-        });
+        h->closing = true;
+        ctx->cv.notify_all();
+        // the server finishes the handle's frames in flight, then frees its pool
+        ctx->cv_idle.wait(lk, [&] { return ctx->pool_of.count(h) == 0; });
         if (counted) ctx->handles--;
     }
     cudaSetDevice(ctx->device);
@@ -902,168 +917,411 @@ extern "C" int jbp_step_syndrome(jbp_h* h, int32_t F, const uint8_t* hat, uint8_
 }
 
 // ---------------------------------------------------------------------------
-// serving: continuous batching across concurrent launches
+// serving: resident pools re-batched every block of iterations
 // ---------------------------------------------------------------------------
 //
-// jbp_submit queues one frame.  A server thread repeatedly (1) retires finished
-// launches, publishing their results, and (2) admits queued frames into a free
-// launch slot (its own stream, pinned staging and device workspace) as long as
-// the message state of everything in flight stays within the memory budget.
-// Frames of one handle that are queued together share a launch; launches of
-// different slots overlap on the device.  Each frame's arithmetic does not
-// depend on which other frames share its launch.
+// jbp_submit queues one frame.  A server thread keeps, for every decoder with
+// work, a resident pool: the step-form message state of up to `cap` frame slots
+// in HBM.  It repeatedly (1) retires each pool whose block finished: the frames
+// that finished during it come back through host-mapped memory and are
+// published to jbp_poll, and their slots free up; (2) admits queued frames into
+// the free slots of their decoder's pool, creating the pool when the memory
+// budget allows (idle pools are evicted first); (3) launches the next block
+// (ctx->opt.block_iters iterations, each frame stopping at its own early stop
+// or at T) of every pool with frames, on the pool's stream, so the pools'
+// blocks overlap on the device.  A frame's arithmetic does not depend on the
+// other frames of its pool, so each result equals the frame decoded alone in
+// the step form.
 
-static constexpr int kSlots = 16;
-static constexpr int kMaxServeBatch = 8192;
+static constexpr int kPoolMinCap = 32;
+static constexpr int kPoolMaxCap = 1024;
 
-static int slot_prepare(jbp_ctx* ctx, Slot& s, jbp_h* h, int F)
+// device bytes of one frame slot of a pool
+static int64_t pool_frame_bytes(const jbp_h* h)
 {
-    if (!s.stream) {
-        JBP_CU(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking), "slot stream");
-        JBP_CU(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming), "slot event");
-    }
-    const size_t need = std::max<size_t>({sizeof(float) * (size_t)F * h->n, (size_t)F * h->K * h->n,
-                                          sizeof(int32_t) * (size_t)F, (size_t)F * h->K});
-    if (need > s.host_cap) {
-        cudaFreeHost(s.h_y); cudaFreeHost(s.h_hat); cudaFreeHost(s.h_iters); cudaFreeHost(s.h_ok);
-        cudaFreeHost(s.h_sig);
-        s.h_y = nullptr; s.h_hat = nullptr; s.h_iters = nullptr; s.h_ok = nullptr; s.h_sig = nullptr; s.host_cap = 0;
-        const size_t cap = std::max(need, (size_t)(1 << 16));
-        JBP_CU(cudaMallocHost((void**)&s.h_y, cap), "pinned y");
-        JBP_CU(cudaMallocHost((void**)&s.h_sig, cap), "pinned sigma2");
-        JBP_CU(cudaMallocHost((void**)&s.h_hat, cap), "pinned hat");
-        JBP_CU(cudaMallocHost((void**)&s.h_iters, cap), "pinned iters");
-        JBP_CU(cudaMallocHost((void**)&s.h_ok, cap), "pinned ok");
-        s.host_cap = cap;
-    }
-    return ws_io(ctx, h, s.ws, F, false);
+    return state_bytes(h->graph()) + 8ll * h->n + 24 + 3ll * h->K + (int64_t)h->K * h->n;
 }
 
-static int slot_launch(jbp_ctx* ctx, Slot& s)
+static PoolState pool_state(const ServePool& p)
 {
-    jbp_h* h = s.h;
-    const int F = (int)s.reqs.size();
-    for (int f = 0; f < F; ++f) {
-        memcpy(s.h_y + (size_t)f * h->n, s.reqs[f].y.data(), sizeof(float) * h->n);
-        s.h_sig[f] = s.reqs[f].sigma2 > 0.0f ? s.reqs[f].sigma2 : (float)h->sigma2;
+    const jbp_h* h = p.h;
+    PoolState st;
+    st.n = h->n;
+    st.K = h->K;
+    st.msg_floats = (long long)h->K * h->E * h->Q;
+    st.msg = P<float>(p.msg);
+    st.y = P<float>(p.y);
+    st.sig = P<float>(p.sig);
+    st.active = P<uint8_t>(p.active);
+    st.t = P<int32_t>(p.t);
+    st.unsat = P<uint8_t>(p.unsat);
+    st.ok = P<uint8_t>(p.ok);
+    st.hat = P<uint8_t>(p.hat);
+    st.fin = P<uint8_t>(p.fin);
+    return st;
+}
+
+static void pool_destroy(jbp_ctx* ctx, ServePool* p)
+{
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    for (DevBuf* b : {&p->msg, &p->ch2v, &p->y, &p->sig, &p->active, &p->t, &p->unsat, &p->ok, &p->hat, &p->fin,
+                      &p->adm_slot, &p->adm_y, &p->adm_sig, &p->count})
+        buf_free(ctx, *b);
+    cudaFreeHost(p->h_adm_slot); cudaFreeHost(p->h_adm_y); cudaFreeHost(p->h_adm_sig); cudaFreeHost(p->h_count);
+    cudaFreeHost(p->h_slot); cudaFreeHost(p->h_iters); cudaFreeHost(p->h_ok); cudaFreeHost(p->h_hat);
+    if (p->done) cudaEventDestroy(p->done);
+    if (p->stream) cudaStreamDestroy(p->stream);
+    ctx->pool_bytes -= p->bytes;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->pool_of.erase(p->h);
     }
-    float* dy = P<float>(s.ws.y);
-    float* dsig = P<float>(s.ws.sig);
-    uint8_t* dhat = P<uint8_t>(s.ws.hat);
-    int32_t* dit = P<int32_t>(s.ws.iters);
-    uint8_t* dok = P<uint8_t>(s.ws.ok);
-    JBP_CU(cudaMemcpyAsync(dy, s.h_y, sizeof(float) * (size_t)F * h->n, cudaMemcpyHostToDevice, s.stream), "serve copy y");
-    JBP_CU(cudaMemcpyAsync(dsig, s.h_sig, sizeof(float) * (size_t)F, cudaMemcpyHostToDevice, s.stream), "serve copy sigma2");
-    int rc = decode_device(h, s.ws, JBP_FORM_AUTO, F, dy, dhat, dit, dok, nullptr, dsig, s.stream);
-    if (rc) return rc;
-    JBP_CU(cudaMemcpyAsync(s.h_hat, dhat, (size_t)F * h->K * h->n, cudaMemcpyDeviceToHost, s.stream), "serve copy hat");
-    JBP_CU(cudaMemcpyAsync(s.h_iters, dit, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s.stream), "serve copy iters");
-    JBP_CU(cudaMemcpyAsync(s.h_ok, dok, (size_t)F * h->K, cudaMemcpyDeviceToHost, s.stream), "serve copy ok");
-    JBP_CU(cudaEventRecord(s.done, s.stream), "serve event");
+    ctx->cv_idle.notify_all();
+}
+
+template <class T>
+static int mapped_alloc(T** host, T** dev, size_t count)
+{
+    JBP_CU(cudaHostAlloc((void**)host, std::max<size_t>(count * sizeof(T), 16), cudaHostAllocMapped), "pinned mapped");
+    JBP_CU(cudaHostGetDevicePointer((void**)dev, *host, 0), "mapped device pointer");
     return JBP_OK;
+}
+
+static int pool_create(jbp_ctx* ctx, jbp_h* h, int cap, ServePool** out)
+{
+    std::unique_ptr<ServePool> p(new ServePool());
+    p->h = h;
+    p->cap = cap;
+    const size_t F = (size_t)cap, K = h->K, n = h->n, E = h->E, Q = h->Q;
+    bool g = false;
+    const int64_t before = ctx->used.load();
+    int rc;
+    if ((rc = buf_ensure(ctx, p->msg, sizeof(float) * F * K * E * Q, &g)) ||
+        (rc = buf_ensure(ctx, p->ch2v, sizeof(float) * F * K * n * Q, &g)) ||
+        (rc = buf_ensure(ctx, p->y, sizeof(float) * F * n, &g)) || (rc = buf_ensure(ctx, p->sig, sizeof(float) * F, &g)) ||
+        (rc = buf_ensure(ctx, p->active, F, &g)) || (rc = buf_ensure(ctx, p->t, sizeof(int32_t) * F, &g)) ||
+        (rc = buf_ensure(ctx, p->unsat, F * K, &g)) || (rc = buf_ensure(ctx, p->ok, F * K, &g)) ||
+        (rc = buf_ensure(ctx, p->hat, F * K * n, &g)) || (rc = buf_ensure(ctx, p->fin, F, &g)) ||
+        (rc = buf_ensure(ctx, p->adm_slot, sizeof(int32_t) * F, &g)) ||
+        (rc = buf_ensure(ctx, p->adm_y, sizeof(float) * F * n, &g)) ||
+        (rc = buf_ensure(ctx, p->adm_sig, sizeof(float) * F, &g)) || (rc = buf_ensure(ctx, p->count, sizeof(int32_t), &g))) {
+        p->bytes = ctx->used.load() - before;
+        ctx->pool_bytes += p->bytes;
+        pool_destroy(ctx, p.get());
+        return rc;
+    }
+    p->bytes = ctx->used.load() - before;
+    ctx->pool_bytes += p->bytes;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->pool_of[h] = 1;
+    }
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking)) ||
+        (e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming)) ||
+        (e = cudaMallocHost((void**)&p->h_adm_slot, sizeof(int32_t) * F)) ||
+        (e = cudaMallocHost((void**)&p->h_adm_y, sizeof(float) * F * n)) ||
+        (e = cudaMallocHost((void**)&p->h_adm_sig, sizeof(float) * F)) ||
+        (e = cudaMallocHost((void**)&p->h_count, sizeof(int32_t)))) {
+        pool_destroy(ctx, p.get());
+        return cuda_fail(e, "serving pool setup");
+    }
+    if ((rc = mapped_alloc(&p->h_slot, &p->d_slot, F)) || (rc = mapped_alloc(&p->h_iters, &p->d_iters, F)) ||
+        (rc = mapped_alloc(&p->h_ok, &p->d_ok, F * K)) || (rc = mapped_alloc(&p->h_hat, &p->d_hat, F * K * n))) {
+        pool_destroy(ctx, p.get());
+        return rc;
+    }
+    if ((e = cudaMemsetAsync(p->active.p, 0, F, p->stream)) || (e = cudaMemsetAsync(p->fin.p, 0, F, p->stream)) ||
+        (e = cudaStreamSynchronize(p->stream))) {
+        pool_destroy(ctx, p.get());
+        return cuda_fail(e, "serving pool clear");
+    }
+    p->req.resize(F);
+    p->used.assign(F, 0);
+    for (int s2 = cap - 1; s2 >= 0; --s2) p->free_list.push_back(s2);
+    *out = p.release();
+    return JBP_OK;
+}
+
+// Publish results; called without the context lock held.
+static void publish(jbp_ctx* ctx, std::vector<std::pair<uint64_t, Result>>& out, std::vector<double>& lat)
+{
+    if (out.empty()) return;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    for (auto& r : out) {
+        ctx->done[r.first] = std::move(r.second);
+        ctx->pending.erase(r.first);
+    }
+    ctx->latencies.insert(ctx->latencies.end(), lat.begin(), lat.end());
+    ctx->completed += out.size();
+    out.clear();
+    lat.clear();
+}
+
+static void pool_free_slot(ServePool& p, int slot)
+{
+    p.used[slot] = 0;
+    p.req[slot] = Request();
+    p.free_list.push_back(slot);
+    p.n_active--;
+    while (p.hi > 0 && !p.used[p.hi - 1]) p.hi--;
+}
+
+// A block of the pool has completed (q = its status): hand out the frames it finished.
+static void pool_retire(jbp_ctx* ctx, ServePool& p, cudaError_t q)
+{
+    const double now = now_us();
+    jbp_h* h = p.h;
+    std::vector<std::pair<uint64_t, Result>> out;
+    std::vector<double> lat;
+    if (q != cudaSuccess) {
+        cudaGetLastError();
+        for (int s2 = 0; s2 < p.cap; ++s2) {
+            if (!p.used[s2]) continue;
+            Result r;
+            r.iters = -1;
+            r.hat.assign((size_t)h->K * h->n, 0);
+            r.ok.assign((size_t)h->K, 0);
+            out.emplace_back(p.req[s2].ticket, std::move(r));
+            lat.push_back(now - p.req[s2].t_submit);
+            pool_free_slot(p, s2);
+        }
+        cudaMemsetAsync(p.active.p, 0, (size_t)p.cap, p.stream);
+        cudaMemsetAsync(p.fin.p, 0, (size_t)p.cap, p.stream);
+        cudaStreamSynchronize(p.stream);
+    } else {
+        const int cnt = *reinterpret_cast<volatile int32_t*>(p.h_count);
+        const size_t KN = (size_t)h->K * h->n;
+        for (int i = 0; i < cnt; ++i) {
+            const int s2 = p.h_slot[i];
+            if (s2 < 0 || s2 >= p.cap || !p.used[s2]) continue;
+            Result r;
+            r.iters = p.h_iters[i];
+            r.ok.assign(p.h_ok + (size_t)i * h->K, p.h_ok + (size_t)(i + 1) * h->K);
+            r.hat.assign(p.h_hat + i * KN, p.h_hat + (i + 1) * KN);
+            out.emplace_back(p.req[s2].ticket, std::move(r));
+            lat.push_back(now - p.req[s2].t_submit);
+            pool_free_slot(p, s2);
+        }
+    }
+    publish(ctx, out, lat);
+}
+
+// Stage `take` into free slots and launch the pool's next block.
+static int pool_launch(jbp_ctx* ctx, ServePool& p, std::vector<Request>& take)
+{
+    jbp_h* h = p.h;
+    const int m = (int)take.size();
+    for (int i = 0; i < m; ++i) {
+        const int s2 = p.free_list.back();
+        p.free_list.pop_back();
+        Request& r = take[i];
+        p.h_adm_slot[i] = s2;
+        memcpy(p.h_adm_y + (size_t)i * h->n, r.y.data(), sizeof(float) * h->n);
+        p.h_adm_sig[i] = r.sigma2 > 0.0f ? r.sigma2 : (float)h->sigma2;
+        r.y.clear();
+        r.y.shrink_to_fit();
+        p.req[s2] = std::move(r);
+        p.used[s2] = 1;
+        p.n_active++;
+        p.hi = std::max(p.hi, s2 + 1);
+    }
+    take.clear();
+    cudaStream_t s = p.stream;
+    const PoolState st = pool_state(p);
+    if (m > 0) {
+        JBP_CU(cudaMemcpyAsync(p.adm_slot.p, p.h_adm_slot, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s), "admit slots");
+        JBP_CU(cudaMemcpyAsync(p.adm_y.p, p.h_adm_y, sizeof(float) * (size_t)m * h->n, cudaMemcpyHostToDevice, s), "admit y");
+        JBP_CU(cudaMemcpyAsync(p.adm_sig.p, p.h_adm_sig, sizeof(float) * m, cudaMemcpyHostToDevice, s), "admit sigma2");
+        JBP_CU(launch_pool_admit(m, P<int32_t>(p.adm_slot), P<float>(p.adm_y), P<float>(p.adm_sig), st, s), "admit");
+    }
+    Graph g = h->graph();
+    g.sigma2_f = P<float>(p.sig);
+    const DeviceInfo& di = ctx->di;
+    const int F = p.hi;
+    float* msg = P<float>(p.msg);
+    float* ch2v = P<float>(p.ch2v);
+    const uint8_t* act = P<uint8_t>(p.active);
+    for (int it = 0; it < ctx->opt.block_iters; ++it) {
+        JBP_CU(launch_channel(g, di, F, P<float>(p.y), msg, ch2v, act, s), "pool channel");
+        JBP_CU(launch_check(g, di, F, msg, act, ctx->opt.precision, s), "pool check");
+        JBP_CU(launch_var(g, di, F, ch2v, msg, nullptr, P<uint8_t>(p.hat), act, s), "pool var");
+        JBP_CU(launch_syndrome(g, di, F, P<uint8_t>(p.hat), P<uint8_t>(p.unsat), act, s), "pool syndrome");
+        JBP_CU(launch_pool_finalize(F, ctx->opt.iters, ctx->opt.early_stop, st, s), "pool finalize");
+    }
+    JBP_CU(cudaMemsetAsync(p.count.p, 0, sizeof(int32_t), s), "harvest clear");
+    JBP_CU(launch_pool_harvest(F, st, P<int32_t>(p.count), p.d_slot, p.d_iters, p.d_ok, p.d_hat, s), "harvest");
+    JBP_CU(cudaMemcpyAsync(p.h_count, p.count.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "harvest count");
+    JBP_CU(cudaEventRecord(p.done, s), "pool event");
+    p.running = true;
+    p.last_used = now_us();
+    return JBP_OK;
+}
+
+static ServePool* find_pool(jbp_ctx* ctx, const jbp_h* h)
+{
+    for (auto& up : ctx->serve_pools)
+        if (up->h == h) return up.get();
+    return nullptr;
+}
+
+// Free device memory for a new pool: destroy idle pools, least recently used first.
+static void evict_idle(jbp_ctx* ctx, int64_t need)
+{
+    while (ctx->pool_bytes + need > ctx->budget / 2) {
+        int victim = -1;
+        for (int i = 0; i < (int)ctx->serve_pools.size(); ++i) {
+            const ServePool& p = *ctx->serve_pools[i];
+            if (p.running || p.n_active > 0) continue;
+            if (victim < 0 || p.last_used < ctx->serve_pools[victim]->last_used) victim = i;
+        }
+        if (victim < 0) return;
+        pool_destroy(ctx, ctx->serve_pools[victim].get());
+        ctx->serve_pools.erase(ctx->serve_pools.begin() + victim);
+    }
+}
+
+static void fail_requests(jbp_ctx* ctx, std::vector<Request>& reqs)
+{
+    std::vector<std::pair<uint64_t, Result>> out;
+    std::vector<double> lat;
+    const double now = now_us();
+    for (Request& r : reqs) {
+        Result res;
+        res.iters = -1;
+        res.hat.assign((size_t)r.h->K * r.h->n, 0);
+        res.ok.assign((size_t)r.h->K, 0);
+        out.emplace_back(r.ticket, std::move(res));
+        lat.push_back(now - r.t_submit);
+    }
+    reqs.clear();
+    publish(ctx, out, lat);
 }
 
 static void server_main(jbp_ctx* ctx)
 {
     cudaSetDevice(ctx->device);
-    std::vector<std::pair<uint64_t, Result>> finished;
-    std::vector<double> lat;
     while (true) {
-        bool any_busy = false;
-        // (1) retire finished launches: CUDA queries and copies outside the lock
-        for (Slot& s : ctx->slots) {
-            if (!s.busy) continue;
-            cudaError_t q = cudaEventQuery(s.done);
+        bool any_running = false;
+        // (1) retire the pools whose block completed
+        for (auto& up : ctx->serve_pools) {
+            ServePool& p = *up;
+            if (!p.running) continue;
+            const cudaError_t q = cudaEventQuery(p.done);
             if (q == cudaErrorNotReady) {
-                any_busy = true;
+                any_running = true;
                 continue;
             }
-            const double t = now_us();
-            jbp_h* h = s.h;
-            finished.clear();
-            lat.clear();
-            for (size_t f = 0; f < s.reqs.size(); ++f) {
-                Result r;
-                r.hat.assign(s.h_hat + f * h->K * h->n, s.h_hat + (f + 1) * h->K * h->n);
-                r.ok.assign(s.h_ok + f * h->K, s.h_ok + (f + 1) * h->K);
-                r.iters = q == cudaSuccess ? s.h_iters[f] : -1;
-                finished.emplace_back(s.reqs[f].ticket, std::move(r));
-                lat.push_back(t - s.reqs[f].t_submit);
-            }
-            {
-                std::lock_guard<std::mutex> lk(ctx->mu);
-                for (auto& fr : finished) {
-                    ctx->done[fr.first] = std::move(fr.second);
-                    ctx->pending.erase(fr.first);
-                }
-                ctx->latencies.insert(ctx->latencies.end(), lat.begin(), lat.end());
-                ctx->completed += finished.size();
-                ctx->inflight_bytes -= s.state_bytes;
-                s.reqs.clear();
-                s.busy = false;
-            }
-            ctx->cv_idle.notify_all();
+            p.running = false;
+            pool_retire(ctx, p, q);
         }
-        // (2) admit queued frames into free slots: take the batch under the lock,
-        //     stage and launch outside it
-        while (true) {
-            Slot* free_slot = nullptr;
-            jbp_h* h = nullptr;
-            std::vector<Request> batch;
-            int64_t bytes = 0;
+        // (2) decoders with queued frames, in queue order
+        std::vector<std::pair<jbp_h*, int>> want;
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            for (const Request& r : ctx->queue) {
+                auto it = std::find_if(want.begin(), want.end(), [&](const std::pair<jbp_h*, int>& w) { return w.first == r.h; });
+                if (it == want.end()) want.emplace_back(r.h, 1);
+                else it->second++;
+            }
+        }
+        for (auto& w : want) {
+            jbp_h* h = w.first;
+            ServePool* p = find_pool(ctx, h);
+            if (p && !p->running && p->n_active == 0 && w.second > p->cap && p->cap < kPoolMaxCap) {
+                // grow an idle pool that is too small for the queue
+                pool_destroy(ctx, p);
+                ctx->serve_pools.erase(std::find_if(ctx->serve_pools.begin(), ctx->serve_pools.end(),
+                                                    [&](const std::unique_ptr<ServePool>& u) { return u.get() == p; }));
+                p = nullptr;
+            }
+            if (!p) {
+                const int64_t per = pool_frame_bytes(h);
+                int cap = kPoolMinCap;
+                while (cap < kPoolMaxCap && cap < 2 * w.second) cap *= 2;
+                evict_idle(ctx, per * cap);
+                const int64_t room = ctx->budget / 2 - ctx->pool_bytes;
+                cap = (int)std::min<int64_t>(cap, room / per);
+                if (cap < 1) {
+                    if (ctx->serve_pools.empty()) {
+                        // one frame of this decoder does not fit the serving budget
+                        std::vector<Request> drop;
+                        {
+                            std::lock_guard<std::mutex> lk(ctx->mu);
+                            for (auto it = ctx->queue.begin(); it != ctx->queue.end();)
+                                if (it->h == h) {
+                                    drop.push_back(std::move(*it));
+                                    it = ctx->queue.erase(it);
+                                } else {
+                                    ++it;
+                                }
+                        }
+                        fail_requests(ctx, drop);
+                    }
+                    continue;   // wait for pools to drain
+                }
+                if (pool_create(ctx, h, cap, &p) != JBP_OK) {
+                    p = nullptr;
+                    continue;
+                }
+                ctx->serve_pools.emplace_back(p);
+            }
+            if (p->running || p->free_list.empty()) continue;
+            std::vector<Request> take;
             {
                 std::lock_guard<std::mutex> lk(ctx->mu);
-                if (ctx->queue.empty()) break;
-                for (Slot& s : ctx->slots)
-                    if (!s.busy) {
-                        free_slot = &s;
-                        break;
-                    }
-                if (!free_slot) break;
-                h = ctx->queue.front().h;
-                const int64_t per_frame = state_bytes(h->graph()) + (int64_t)h->n * 4 + (int64_t)h->K * (h->n + 1) + 8;
-                for (auto it = ctx->queue.begin(); it != ctx->queue.end() && (int)batch.size() < kMaxServeBatch;) {
-                    if (it->h == h && ctx->inflight_bytes + bytes + per_frame <= ctx->budget / 2) {
-                        bytes += per_frame;
-                        batch.push_back(std::move(*it));
+                for (auto it = ctx->queue.begin(); it != ctx->queue.end() && take.size() < p->free_list.size();)
+                    if (it->h == h) {
+                        take.push_back(std::move(*it));
                         it = ctx->queue.erase(it);
                     } else {
                         ++it;
                     }
-                }
-                if (batch.empty()) break;   // over budget: wait for a launch to retire
-                free_slot->busy = true;
-                free_slot->h = h;
-                free_slot->reqs = std::move(batch);
-                free_slot->state_bytes = bytes;
-                ctx->inflight_bytes += bytes;
             }
-            Slot& s = *free_slot;
-            int rc = slot_prepare(ctx, s, h, (int)s.reqs.size());
-            if (!rc) rc = slot_launch(ctx, s);
-            any_busy = true;
-            if (rc) {
-                std::lock_guard<std::mutex> lk(ctx->mu);
-                for (const Request& r : s.reqs) {
-                    Result res;
-                    res.iters = -1;
-                    res.hat.assign((size_t)h->K * h->n, 0);
-                    res.ok.assign((size_t)h->K, 0);
-                    ctx->done[r.ticket] = std::move(res);
-                    ctx->pending.erase(r.ticket);
-                }
-                s.reqs.clear();
-                s.busy = false;
-                ctx->inflight_bytes -= s.state_bytes;
+            if (take.empty() && p->n_active == 0) continue;
+            if (pool_launch(ctx, *p, take) != JBP_OK) {
+                fail_requests(ctx, take);
                 cudaGetLastError();
+            }
+            any_running = any_running || p->running;
+        }
+        // (3) pools with frames in flight and nothing new: next block
+        for (auto& up : ctx->serve_pools) {
+            ServePool& p = *up;
+            if (p.running || p.n_active == 0) continue;
+            std::vector<Request> none;
+            if (pool_launch(ctx, p, none) != JBP_OK) cudaGetLastError();
+            any_running = any_running || p.running;
+        }
+        // (4) pools of decoders being destroyed, once drained
+        for (size_t i = 0; i < ctx->serve_pools.size();) {
+            ServePool& p = *ctx->serve_pools[i];
+            bool closing;
+            {
+                std::lock_guard<std::mutex> lk(ctx->mu);
+                closing = p.h->closing;
+            }
+            if (closing && !p.running && p.n_active == 0) {
+                pool_destroy(ctx, &p);
+                ctx->serve_pools.erase(ctx->serve_pools.begin() + i);
+            } else {
+                ++i;
             }
         }
         std::unique_lock<std::mutex> lk(ctx->mu);
-        if (ctx->stop && !any_busy && ctx->queue.empty()) break;
-        if (any_busy)
+        if (ctx->stop && !any_running && ctx->queue.empty()) break;
+        if (any_running) {
             ctx->cv.wait_for(lk, std::chrono::microseconds(50));
-        else
-            ctx->cv.wait(lk, [&] { return ctx->stop || !ctx->queue.empty(); });
+        } else {
+            bool closing_pool = false;
+            for (auto& up : ctx->serve_pools) closing_pool = closing_pool || up->h->closing;
+            if (!closing_pool) ctx->cv.wait(lk, [&] {
+                if (ctx->stop || !ctx->queue.empty()) return true;
+                for (auto& up : ctx->serve_pools)
+                    if (up->h->closing) return true;
+                return false;
+            });
+        }
     }
 }
 
@@ -1081,7 +1339,6 @@ extern "C" int jbp_submit(jbp_h* h, const float* y_frame, double sigma2, uint64_
         std::lock_guard<std::mutex> lk(ctx->mu);
         if (ctx->stop) return fail(JBP_ECLOSED, "context is shutting down");
         if (!ctx->server_started) {
-            ctx->slots.resize(kSlots);
             ctx->server = std::thread(server_main, ctx);
             ctx->server_started = true;
         }

@@ -41,6 +41,27 @@ cudaError_t launch_check_tc(const Graph& g, const DeviceInfo& di, int F, float* 
                             int precision, cudaStream_t s);
 cudaError_t launch_ok_from_unsat(int F, int K, const uint8_t* unsat, uint8_t* ok, cudaStream_t s);
 
+// Resident pool of the serving loop: the step-form state of up to F frame
+// slots of one decoder, kept in HBM across blocks of iterations (jbp_step.cu).
+struct PoolState {
+    int n, K;
+    long long msg_floats;   // K*E*q per frame
+    float* msg;             // [F][K][E][q]
+    float* y;               // [F][n]
+    float* sig;             // [F] noise variance of each frame
+    uint8_t* active;        // [F] 1 while the frame iterates
+    int32_t* t;             // [F] iterations run
+    uint8_t* unsat;         // [F*K]
+    uint8_t* ok;            // [F*K]
+    uint8_t* hat;           // [F*K*n]
+    uint8_t* fin;           // [F] finished during the current block, not yet harvested
+};
+cudaError_t launch_pool_admit(int m, const int32_t* slot, const float* adm_y, const float* adm_sig,
+                              const PoolState& p, cudaStream_t s);
+cudaError_t launch_pool_finalize(int F, int T, int early_stop, const PoolState& p, cudaStream_t s);
+cudaError_t launch_pool_harvest(int F, const PoolState& p, int32_t* count, int32_t* out_slot, int32_t* out_iters,
+                                uint8_t* out_ok, uint8_t* out_hat, cudaStream_t s);
+
 // Fused shared-memory form (jbp_fused.cu).
 struct FusedPlan {
     int frames_per_cta;   // frames resident in one CTA

@@ -612,6 +612,105 @@ cudaError_t launch_finalize(int F, int K, int t, int early_stop, StepCtl ctl, cu
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// resident pools (serving): admission, per-frame finalisation, harvest
+// ---------------------------------------------------------------------------
+
+// Frame i of an admission goes to pool slot slot[i]: its channel output and
+// noise variance are copied in, every message starts uniform (all ones), its
+// iteration count and syndrome flags are cleared and it becomes active.
+__global__ void k_pool_admit(int m, const int32_t* __restrict__ slot, const float* __restrict__ adm_y,
+                             const float* __restrict__ adm_sig, PoolState p)
+{
+    const size_t per = (size_t)p.msg_floats;
+    for (int i = blockIdx.y; i < m; i += gridDim.y) {
+        const int f = slot[i];
+        float* msg = p.msg + (size_t)f * per;
+        for (size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x; j < per; j += (size_t)gridDim.x * blockDim.x)
+            msg[j] = 1.0f;
+        if (blockIdx.x == 0) {
+            for (int j = threadIdx.x; j < p.n; j += blockDim.x) p.y[(size_t)f * p.n + j] = adm_y[(size_t)i * p.n + j];
+            for (int k = threadIdx.x; k < p.K; k += blockDim.x) p.unsat[(size_t)f * p.K + k] = 0;
+            if (threadIdx.x == 0) {
+                p.sig[f] = adm_sig[i];
+                p.t[f] = 0;
+                p.fin[f] = 0;
+                p.active[f] = 1;
+            }
+        }
+    }
+}
+
+// After one iteration of the pool: every active frame counts it, records its
+// syndrome flags and stops (fin = 1) at a zero syndrome (early stop) or at T.
+__global__ void k_pool_finalize(int F, int T, int early_stop, PoolState p)
+{
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < F; f += gridDim.x * blockDim.x) {
+        if (!p.active[f]) continue;
+        bool all = true;
+        for (int k = 0; k < p.K; ++k) {
+            const bool okk = p.unsat[(size_t)f * p.K + k] == 0;
+            p.ok[(size_t)f * p.K + k] = okk ? 1 : 0;
+            p.unsat[(size_t)f * p.K + k] = 0;
+            all = all && okk;
+        }
+        const int t = ++p.t[f];
+        if ((early_stop && all) || t >= T) {
+            p.active[f] = 0;
+            p.fin[f] = 1;
+        }
+    }
+}
+
+// Frames that finished during the block are packed, in any order, into the
+// harvest area (host-mapped memory): slot, iterations, K syndrome flags and K*n
+// decisions each.  count is a device counter cleared before the launch.
+__global__ void k_pool_harvest(int F, PoolState p, int32_t* count, int32_t* out_slot, int32_t* out_iters,
+                               uint8_t* out_ok, uint8_t* out_hat)
+{
+    __shared__ int idx;
+    const int KN = p.K * p.n;
+    for (int f = blockIdx.x; f < F; f += gridDim.x) {
+        if (!p.fin[f]) continue;   // uniform across the block
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            idx = atomicAdd(count, 1);
+            out_slot[idx] = f;
+            out_iters[idx] = p.t[f];
+            p.fin[f] = 0;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < p.K; k += blockDim.x) out_ok[(size_t)idx * p.K + k] = p.ok[(size_t)f * p.K + k];
+        for (int j = threadIdx.x; j < KN; j += blockDim.x) out_hat[(size_t)idx * KN + j] = p.hat[(size_t)f * KN + j];
+    }
+}
+
+cudaError_t launch_pool_admit(int m, const int32_t* slot, const float* adm_y, const float* adm_sig,
+                              const PoolState& p, cudaStream_t s)
+{
+    if (m <= 0) return cudaSuccess;
+    const int gx = (int)std::min<size_t>(((size_t)p.msg_floats + 255) / 256, 64);
+    const dim3 grid(gx, std::min(m, 4096));
+    k_pool_admit<<<grid, 256, 0, s>>>(m, slot, adm_y, adm_sig, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pool_finalize(int F, int T, int early_stop, const PoolState& p, cudaStream_t s)
+{
+    if (F <= 0) return cudaSuccess;
+    const int threads = 256, grid = std::min((F + threads - 1) / threads, 4096);
+    k_pool_finalize<<<grid, threads, 0, s>>>(F, T, early_stop, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pool_harvest(int F, const PoolState& p, int32_t* count, int32_t* out_slot, int32_t* out_iters,
+                                uint8_t* out_ok, uint8_t* out_hat, cudaStream_t s)
+{
+    if (F <= 0) return cudaSuccess;
+    k_pool_harvest<<<std::min(F, 4096), 128, 0, s>>>(F, p, count, out_slot, out_iters, out_ok, out_hat);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fill(float* p, size_t count, float value, cudaStream_t s)
 {
     if (count == 0) return cudaSuccess;

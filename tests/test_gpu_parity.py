@@ -394,9 +394,10 @@ def test_decode_many_graph_replay_matches_single_decodes(env):
 
 
 def test_serving_results_are_the_same_alone_and_in_the_mix(env):
-    """Requests of two decoders submitted interleaved (continuous batching over
-    concurrent launches) give, frame by frame, exactly the result of decoding that
-    frame alone; unknown or consumed tickets poll JBP_ECLOSED."""
+    """Requests of two decoders submitted interleaved (resident pools re-batched
+    every block of iterations, the two pools' blocks overlapping) give, frame by
+    frame, exactly the result of decoding that frame alone in the step form;
+    unknown or consumed tickets poll JBP_ECLOSED."""
     jbp, O, torch = env
     ctx = jbp.Context(iters=10, early_stop=True)
     specs = [(64, 4, 2, 11.0, 24), (128, 16, 3, 13.0, 16)]
@@ -408,7 +409,7 @@ def test_serving_results_are_the_same_alone_and_in_the_mix(env):
             decs.append(jbp.Decoder(ctx, code, K, fr["sigma2"], fr["perm"]))
             frames.append(fr)
         sig = [np.full(fr["y"].shape[0], np.float32(fr["sigma2"]), np.float32) for fr in frames]
-        alone = [[d.decode(fr["y"][i:i + 1], sigma2=s[i:i + 1]) for i in range(fr["y"].shape[0])]
+        alone = [[d.decode(fr["y"][i:i + 1], form=jbp.FORM_STEP, sigma2=s[i:i + 1]) for i in range(fr["y"].shape[0])]
                  for d, fr, s in zip(decs, frames, sig)]
         tickets = []
         for i in range(max(fr["y"].shape[0] for fr in frames)):
@@ -435,4 +436,34 @@ def test_serving_results_are_the_same_alone_and_in_the_mix(env):
     finally:
         for d in decs:
             d.close()
+        ctx.close()
+
+
+def test_serving_admits_frames_between_blocks(env):
+    """Frames submitted while earlier frames of the same decoder are part-way
+    through their iterations join the resident pool at the next block boundary;
+    every result equals the frame decoded alone (step form), and the iteration
+    counts show the early frames were not restarted."""
+    import time
+    jbp, O, torch = env
+    ctx = jbp.Context(iters=30, early_stop=False, block_iters=2)
+    code = I.make_code(256, 16)
+    fr = I.make_frames(code, 4, 10.0, 48, seed=1234)
+    dec = jbp.Decoder(ctx, code, 4, fr["sigma2"], fr["perm"])
+    try:
+        alone = [dec.decode(fr["y"][i:i + 1], form=jbp.FORM_STEP) for i in range(48)]
+        first = [dec.submit(fr["y"][i]) for i in range(16)]
+        time.sleep(0.002)
+        second = [dec.submit(fr["y"][i]) for i in range(16, 48)]
+        for i, tk in enumerate(first + second):
+            while True:
+                res = ctx.poll(tk, 256, 4)
+                if res is not None:
+                    break
+                time.sleep(0.0005)
+            assert np.array_equal(res["hat"], alone[i]["hat"][0]), i
+            assert res["iters"] == 30 and np.array_equal(res["ok"], alone[i]["ok"][0])
+        assert ctx.serving_stats()["completed"] == 48
+    finally:
+        dec.close()
         ctx.close()
