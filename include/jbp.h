@@ -300,7 +300,7 @@ typedef struct {
     const int32_t *rows;
 } jbp_ura_params;
 
-/* Create a handle for a code (regular, dv = 2, dc = 3 or 4; q = 16, 32 or 64
+/* Create a handle for a code (regular, (dv, dc) = (2, 3), (2, 4) or (3, 6); q = 16, 32 or 64
  * for the decoder, q = 32 or 64 for the detector) on ctx's device.  The code
  * arrays and rows are copied.  Errors: JBP_EINVAL (bad code or parameters,
  * or one frame's decoder state does not fit shared memory), JBP_ENOMEM,

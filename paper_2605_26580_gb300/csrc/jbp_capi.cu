@@ -1421,7 +1421,7 @@ extern "C" int jbp_ura_destroy(jbp_ura* u)
     dev_free(ctx, u->d_tw, sizeof(float) * 2 * (size_t)u->u.Q);
     dev_free(ctx, u->d_chk_var, sizeof(int32_t) * (size_t)u->u.P * u->u.dc);
     dev_free(ctx, u->d_chk_coef, (size_t)u->u.P * u->u.dc);
-    dev_free(ctx, u->d_var_edge, sizeof(int32_t) * 2 * (size_t)u->u.n);
+    dev_free(ctx, u->d_var_edge, sizeof(int32_t) * (size_t)u->u.dv * u->u.n);
     dev_free(ctx, u->d_gf_mul, (size_t)u->u.Q * u->u.Q);
     dev_free(ctx, u->d_gf_div, (size_t)u->u.Q * u->u.Q);
     for (DevBuf* b : {&u->S, &u->y, &u->hat, &u->iters, &u->ok}) buf_free(ctx, *b);
@@ -1441,9 +1441,10 @@ extern "C" int jbp_ura_create(jbp_ctx* ctx, const jbp_code* code, const jbp_ura_
     while ((1 << m) < q && m < 8) ++m;
     if ((1 << m) != q || (q != 16 && q != 32 && q != 64))
         return fail(JBP_EINVAL, "q must be 16, 32 or 64 (got %d)", q);
-    if (code->dv != 2) return fail(JBP_EINVAL, "the row decoder is built for dv = 2 (got %d)", code->dv);
-    if (code->dc != 3 && code->dc != 4) return fail(JBP_EINVAL, "the row decoder is built for dc = 3 or 4 (got %d)", code->dc);
-    if (code->n < 1 || code->P < 1 || (int64_t)code->n * 2 != (int64_t)code->P * code->dc)
+    if (!((code->dv == 2 && (code->dc == 3 || code->dc == 4)) || (code->dv == 3 && code->dc == 6)))
+        return fail(JBP_EINVAL, "the row decoder is built for (dv, dc) = (2, 3), (2, 4) or (3, 6) (got (%d, %d))",
+                    code->dv, code->dc);
+    if (code->n < 1 || code->P < 1 || (int64_t)code->n * code->dv != (int64_t)code->P * code->dc)
         return fail(JBP_EINVAL, "n*dv must equal P*dc with n, P >= 1");
     if (code->n > 32767) return fail(JBP_EINVAL, "n must be <= 32767");
     if (!code->chk_var || !code->chk_coef || !p->rows) return fail(JBP_EINVAL, "NULL code arrays or rows");
@@ -1453,17 +1454,17 @@ extern "C" int jbp_ura_create(jbp_ctx* ctx, const jbp_code* code, const jbp_ura_
     if (!(p->rho_bg > 0.0 && p->rho_bg < 1.0)) return fail(JBP_EINVAL, "rho_bg must be in (0, 1)");
     if (!(p->sigma_u2 > 0.0) || !std::isfinite(p->sigma_u2)) return fail(JBP_EINVAL, "sigma_u2 must be finite and > 0");
     if (!(p->cancel_log <= 0.0) || !std::isfinite(p->cancel_log)) return fail(JBP_EINVAL, "cancel_log must be finite and <= 0");
-    const int n = code->n, P = code->P, dc = code->dc, E = P * dc;
-    std::vector<int32_t> var_edge((size_t)2 * n), fill(n, 0);
+    const int n = code->n, P = code->P, dc = code->dc, dv = code->dv, E = P * dc;
+    std::vector<int32_t> var_edge((size_t)dv * n), fill(n, 0);
     for (int e = 0; e < E; ++e) {
         const int i = code->chk_var[e];
         if (i < 0 || i >= n) return fail(JBP_EINVAL, "chk_var[%d] = %d out of range", e, i);
         if (code->chk_coef[e] < 1 || code->chk_coef[e] >= q) return fail(JBP_EINVAL, "chk_coef[%d] = %d not in 1..q-1", e, code->chk_coef[e]);
-        if (fill[i] >= 2) return fail(JBP_EINVAL, "variable %d has more than 2 edges", i);
-        var_edge[(size_t)2 * i + fill[i]++] = e;
+        if (fill[i] >= dv) return fail(JBP_EINVAL, "variable %d has more than dv = %d edges", i, dv);
+        var_edge[(size_t)dv * i + fill[i]++] = e;
     }
     for (int i = 0; i < n; ++i)
-        if (fill[i] != 2) return fail(JBP_EINVAL, "variable %d has %d edges, expected 2", i, fill[i]);
+        if (fill[i] != dv) return fail(JBP_EINVAL, "variable %d has %d edges, expected dv = %d", i, fill[i], dv);
     for (int l = 0; l < n; ++l)
         for (int i = 0; i < p->ns; ++i) {
             const int r = p->rows[(size_t)l * p->ns + i];
@@ -1489,7 +1490,7 @@ extern "C" int jbp_ura_create(jbp_ctx* ctx, const jbp_code* code, const jbp_ura_
         tw[2 * k + 1] = (float)-std::sin(two_pi * k / q);
     }
     UraDev d{};
-    d.n = n; d.P = P; d.dc = dc; d.K = p->K; d.Q = q; d.ns = p->ns;
+    d.n = n; d.P = P; d.dc = dc; d.dv = dv; d.K = p->K; d.Q = q; d.ns = p->ns;
     d.amp_iters = p->amp_iters; d.bp_iters = p->bp_iters; d.early_stop = p->early_stop ? 1 : 0;
     d.log_odds = (float)std::log((1.0 - p->rho_bg) / p->rho_bg);
     d.su2 = (float)p->sigma_u2;
@@ -1508,7 +1509,7 @@ extern "C" int jbp_ura_create(jbp_ctx* ctx, const jbp_code* code, const jbp_ura_
         (rc = dev_alloc(ctx, &u->d_tw, (size_t)2 * q, &u->table_bytes)) ||
         (rc = dev_alloc(ctx, &u->d_chk_var, (size_t)E, &u->table_bytes)) ||
         (rc = dev_alloc(ctx, &u->d_chk_coef, (size_t)E, &u->table_bytes)) ||
-        (rc = dev_alloc(ctx, &u->d_var_edge, (size_t)2 * n, &u->table_bytes)) ||
+        (rc = dev_alloc(ctx, &u->d_var_edge, (size_t)dv * n, &u->table_bytes)) ||
         (rc = dev_alloc(ctx, &u->d_gf_mul, (size_t)q * q, &u->table_bytes)) ||
         (rc = dev_alloc(ctx, &u->d_gf_div, (size_t)q * q, &u->table_bytes))) {
         jbp_ura_destroy(u);

@@ -79,7 +79,7 @@ cudaError_t launch_fused(const Graph& g, const FusedPlan& plan, int F, const flo
 // Evidence-interface path (jbp_ura.cu): slot-wise AMP detector and SIC row
 // decoder.  Device tables and scalars of one (code, detector) pair.
 struct UraDev {
-    int n, P, dc, K, Q;          // slots = variables, checks, check degree, rows, field size
+    int n, P, dc, dv, K, Q;      // slots = variables, checks, check and variable degree, rows, field size
     int ns;                      // complex channel uses per slot (rows of the partial DFT)
     int amp_iters, bp_iters, early_stop;
     float log_odds;              // log((1 - rho) / rho)
@@ -90,7 +90,7 @@ struct UraDev {
     const float* tw;             // [2*Q] exp(-2 pi i k / Q), interleaved
     const int32_t* chk_var;      // [P*dc]
     const uint8_t* chk_coef;     // [P*dc]
-    const int32_t* var_edge;     // [2n] the two edges of each variable
+    const int32_t* var_edge;     // [dv*n] the edges of each variable
     const uint8_t* gf_mul;       // [Q*Q]
     const uint8_t* gf_div;       // [Q*Q]
 };

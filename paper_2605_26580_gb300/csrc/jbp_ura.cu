@@ -16,7 +16,8 @@
 //  * k_sic: SIC over K rows (appendix "Complexity derivation", paragraphs
 //    SIC-BP and FFT-BP; appendix "Q-ary LDPC code", eqs.
 //    app_ldpc_local_belief_from_S, app_ldpc_v2c, app_ldpc_c2v,
-//    app_ldpc_marginal).  One warp per frame keeps one row's BP state in
+//    app_ldpc_marginal), codes with (dv, dc) = (2, 3), (2, 4) or (3, 6).
+//    One warp per frame keeps one row's BP state in
 //    shared memory: local beliefs lambda (max 1, floored at kRelFloor) and one
 //    message per edge (v2c before a check update, c2v after it), as
 //    probabilities scaled to max 1.  Each iteration: the check update in the
@@ -309,7 +310,7 @@ constexpr int kSicMaxWarps = 16;   // frames (warps) per CTA of the SIC kernel
 
 // Shared memory of the SIC kernel: CTA tables, then one region per warp.
 struct SicLayout {
-    int tables;     // bytes: gf_mul, gf_div [Q*Q], coef [E], chk_var, var_edge (int16)
+    int tables;     // bytes: gf_mul, gf_div [Q*Q], coef [E], chk_var [E], var_edge [dv*n] (int16)
     int per_warp;   // bytes: msg [E*Q] + lambda [n*Q] floats, decisions [K*n]
 };
 
@@ -319,7 +320,7 @@ static SicLayout sic_layout(const UraDev& u)
     SicLayout s;
     int t = 2 * u.Q * u.Q + E;
     t = (t + 3) & ~3;
-    t += 2 * E + 2 * 2 * u.n;
+    t += 2 * E + 2 * u.dv * u.n;
     s.tables = (t + 15) & ~15;
     s.per_warp = 4 * (E + u.n) * u.Q + ((u.K * u.n + 15) & ~15);
     return s;
@@ -327,7 +328,7 @@ static SicLayout sic_layout(const UraDev& u)
 
 namespace {
 
-template <int Q, int DC>
+template <int Q, int DC, int DV>
 __global__ void __launch_bounds__(32 * kSicMaxWarps, 1) k_sic(UraDev u, SicLayout lay, int F, const float* __restrict__ S,
                                              uint8_t* __restrict__ hat, int32_t* __restrict__ iters,
                                              uint8_t* __restrict__ ok)
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(32 * kSicMaxWarps, 1) k_sic(UraDev u, SicLayou
         s_coef[i] = u.chk_coef[i];
         s_cv[i] = (int16_t)u.chk_var[i];
     }
-    for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) s_ve[i] = (int16_t)u.var_edge[i];
+    for (int i = threadIdx.x; i < DV * n; i += blockDim.x) s_ve[i] = (int16_t)u.var_edge[i];
     __syncthreads();
 
     const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -374,14 +375,13 @@ __global__ void __launch_bounds__(32 * kSicMaxWarps, 1) k_sic(UraDev u, SicLayou
                     mx = fmaxf(mx, x[v]);
                 }
                 mx = team_max<T>(mx, L.mask);
-                const int e0 = s_ve[2 * i], e1 = s_ve[2 * i + 1];
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     const int a = v * T + L.tl;
                     const float lv = fmaxf(expf(x[v] - mx), kRelFloor);
                     lam[(size_t)i * Q + a] = lv;
-                    msg[(size_t)e0 * Q + a] = lv;
-                    msg[(size_t)e1 * Q + a] = lv;
+#pragma unroll
+                    for (int d = 0; d < DV; ++d) msg[(size_t)s_ve[DV * i + d] * Q + a] = lv;
                 }
             }
             __syncwarp();
@@ -392,34 +392,45 @@ __global__ void __launch_bounds__(32 * kSicMaxWarps, 1) k_sic(UraDev u, SicLayou
                     check_team_dc<Q, DC>(msg + (size_t)j * DC * Q, s_coef + j * DC, s_mul, s_div, L);
                 __syncwarp();
                 for (int i = team; i < n; i += TPW) {
-                    const int e0 = s_ve[2 * i], e1 = s_ve[2 * i + 1];
-                    float v0[V], v1[V];
-                    float best = -1.0f, m0 = 0.0f, m1 = 0.0f;
+                    // marginal lambda * prod_d c_d and, per edge d, v2c_d = lambda * prod_{d' != d} c_d'
+                    int e[DV];
+#pragma unroll
+                    for (int d = 0; d < DV; ++d) e[d] = s_ve[DV * i + d];
+                    float vo[DV][V], mo[DV];
+#pragma unroll
+                    for (int d = 0; d < DV; ++d) mo[d] = 0.0f;
+                    float best = -1.0f;
                     int bi = 0;
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
                         const int a = v * T + L.tl;
                         const float l = lam[(size_t)i * Q + a];
-                        const float c0 = msg[(size_t)e0 * Q + a], c1 = msg[(size_t)e1 * Q + a];
-                        const float b = l * c0 * c1;
+                        float c[DV];
+#pragma unroll
+                        for (int d = 0; d < DV; ++d) c[d] = msg[(size_t)e[d] * Q + a];
+                        float b = l;
+#pragma unroll
+                        for (int d = 0; d < DV; ++d) b *= c[d];
                         if (b > best) {
                             best = b;
                             bi = a;
                         }
-                        v0[v] = l * c1;
-                        v1[v] = l * c0;
-                        m0 = fmaxf(m0, v0[v]);
-                        m1 = fmaxf(m1, v1[v]);
+#pragma unroll
+                        for (int d = 0; d < DV; ++d) {
+                            float w = l;
+#pragma unroll
+                            for (int d2 = 0; d2 < DV; ++d2)
+                                if (d2 != d) w *= c[d2];
+                            vo[d][v] = w;
+                            mo[d] = fmaxf(mo[d], w);
+                        }
                     }
                     const int dec = team_argmax<T>(best, bi, L.mask);
-                    m0 = team_max<T>(m0, L.mask);
-                    m1 = team_max<T>(m1, L.mask);
-                    const float i0 = 1.0f / m0, i1 = 1.0f / m1;
 #pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        const int a = v * T + L.tl;
-                        msg[(size_t)e0 * Q + a] = v0[v] * i0;
-                        msg[(size_t)e1 * Q + a] = v1[v] * i1;
+                    for (int d = 0; d < DV; ++d) {
+                        const float inv = 1.0f / team_max<T>(mo[d], L.mask);
+#pragma unroll
+                        for (int v = 0; v < V; ++v) msg[(size_t)e[d] * Q + v * T + L.tl] = vo[d][v] * inv;
                     }
                     if (L.tl == 0) hs[k * n + i] = (uint8_t)dec;
                 }
@@ -454,14 +465,14 @@ __global__ void __launch_bounds__(32 * kSicMaxWarps, 1) k_sic(UraDev u, SicLayou
     }
 }
 
-template <int Q, int DC>
+template <int Q, int DC, int DV>
 cudaError_t launch_sic_t(const UraDev& u, const DeviceInfo& di, int F, const float* S, uint8_t* hat,
                          int32_t* iters, uint8_t* ok, cudaStream_t s)
 {
     const SicLayout lay = sic_layout(u);
     static bool attr_set = false;   // the same value from every caller: a benign race
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_sic<Q, DC>, cudaFuncAttributeMaxDynamicSharedMemorySize, di.smem_optin);
+        cudaError_t e = cudaFuncSetAttribute(k_sic<Q, DC, DV>, cudaFuncAttributeMaxDynamicSharedMemorySize, di.smem_optin);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -473,7 +484,7 @@ cudaError_t launch_sic_t(const UraDev& u, const DeviceInfo& di, int F, const flo
         const int smem = lay.tables + w * lay.per_warp;
         if (smem > di.smem_optin) break;
         int per_sm = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sic<Q, DC>, 32 * w, smem);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sic<Q, DC, DV>, 32 * w, smem);
         if (e != cudaSuccess) return e;
         if (per_sm * w > best) {
             best = per_sm * w;
@@ -485,7 +496,7 @@ cudaError_t launch_sic_t(const UraDev& u, const DeviceInfo& di, int F, const flo
     const int smem = lay.tables + W * lay.per_warp;
     const long need = ((long)F + W - 1) / W;
     const int grid = (int)std::min<long>(need, (long)per_sm_best * di.sm_count);
-    k_sic<Q, DC><<<grid, 32 * W, smem, s>>>(u, lay, F, S, hat, iters, ok);
+    k_sic<Q, DC, DV><<<grid, 32 * W, smem, s>>>(u, lay, F, S, hat, iters, ok);
     return cudaGetLastError();
 }
 
@@ -526,10 +537,11 @@ cudaError_t launch_sic(const UraDev& u, const DeviceInfo& di, int F, const float
                        uint8_t* ok, cudaStream_t s)
 {
     if (F <= 0) return cudaSuccess;
-#define JBP_SIC_CASE(QQ, DD) \
-    if (u.Q == QQ && u.dc == DD) return launch_sic_t<QQ, DD>(u, di, F, S, hat, iters, ok, s);
-    JBP_SIC_CASE(16, 3) JBP_SIC_CASE(16, 4) JBP_SIC_CASE(32, 3) JBP_SIC_CASE(32, 4)
-    JBP_SIC_CASE(64, 3) JBP_SIC_CASE(64, 4)
+#define JBP_SIC_CASE(QQ, DD, VV) \
+    if (u.Q == QQ && u.dc == DD && u.dv == VV) return launch_sic_t<QQ, DD, VV>(u, di, F, S, hat, iters, ok, s);
+    JBP_SIC_CASE(16, 3, 2) JBP_SIC_CASE(16, 4, 2) JBP_SIC_CASE(16, 6, 3)
+    JBP_SIC_CASE(32, 3, 2) JBP_SIC_CASE(32, 4, 2) JBP_SIC_CASE(32, 6, 3)
+    JBP_SIC_CASE(64, 3, 2) JBP_SIC_CASE(64, 4, 2) JBP_SIC_CASE(64, 6, 3)
 #undef JBP_SIC_CASE
     return cudaErrorInvalidValue;
 }

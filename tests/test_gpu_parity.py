@@ -467,3 +467,23 @@ def test_serving_admits_frames_between_blocks(env):
     finally:
         dec.close()
         ctx.close()
+
+
+@pytest.mark.parametrize("form", ["auto", "step"])
+def test_variable_degree_three_matches_oracle(env, form):
+    """A regular (3, 4) code: every variable has three checks, so the channel
+    node's incoming message is the product of three c2v and each v2c leaves one
+    of three out (the step form's team path and generic variable node)."""
+    jbp, O, torch = env
+    code = I.make_code(64, 16, dv=3, dc=4)
+    fr = I.make_frames(code, 3, 12.0, 24, seed=31)
+    ctx, dec = _decoder(jbp, code, 3, fr["sigma2"], fr["perm"], iters=15, early_stop=True)
+    try:
+        got = dec.decode(fr["y"], form=jbp.FORM_STEP if form == "step" else jbp.FORM_AUTO)
+    finally:
+        dec.close()
+        ctx.close()
+    ref = O.decode(code, 3, fr["sigma2"], fr["perm"], fr["y"], 15, early_stop=True, want_margin=True)
+    bad, _ = _margin_mismatch(got, ref)
+    assert bad == 0
+    assert (got["iters"] == ref["iters"]).all()

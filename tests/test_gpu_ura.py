@@ -130,6 +130,28 @@ def test_sic_other_fields_and_degrees(jbp_lib, oracle):
         assert _compare_sic(got, ref, 2) >= 0.8 * 80
 
 
+@pytest.mark.parametrize("q,n,bias", [(16, 96, 3.5), (64, 128, 4.5)])
+def test_sic_variable_degree_three_matches_oracle(jbp_lib, oracle, q, n, bias):
+    """A regular (3, 6) code (rate 1/2): three checks per variable, so each v2c
+    leaves one of three incoming messages out and the check node has degree 6."""
+    code = I.make_code(n, q, dv=3, dc=6)
+    rng = np.random.default_rng(n)
+    # evidence that favours one codeword, as a detector would give at moderate SNR
+    # (at these strengths most rows converge, some only after many iterations)
+    info = rng.integers(0, q, size=(24, code["k"]))
+    c = I.encode(code, info)
+    S = (rng.standard_normal((24, n, q)) * 1.5).astype(np.float32)
+    S[np.arange(24)[:, None], np.arange(n)[None, :], c] += bias
+    ref = oracle.sic_decode(code, 1, S.astype(np.float64), 30, -math.log(q))
+    ctx = _ctx(jbp_lib)
+    dec = jbp_lib.EvidenceDecoder(ctx, code, 1, np.zeros((n, 4), dtype=np.int32) + np.arange(4), 0.1, 1.0,
+                                  -math.log(q), bp_iters=30)
+    got = dec.sic(S)
+    dec.close()
+    ctx.close()
+    assert _compare_sic(got, ref, 1) >= 0.8 * 24
+
+
 def test_ura_decode_is_detector_then_decoder_and_matches_oracle_ser(jbp_lib, oracle):
     import torch
     code = I.make_code(24, 64, dv=2, dc=3)
