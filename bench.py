@@ -810,7 +810,15 @@ def wl_ura(args):
         t_e2e = time.perf_counter() - t0
         g = hat.cpu().numpy()
         iters = it.cpu().numpy()
-        sym, cw = I.match_rows(g, X)
+        # row-aligned errors on the GPU (jbp_match_rows), checked against the host on a sample
+        Xd = torch.from_numpy(X).to(dev)
+        sym_d = torch.empty((F,), dtype=torch.int32, device=dev)
+        cw_d = torch.empty((F,), dtype=torch.int32, device=dev)
+        ctx.match_rows_device(hat, Xd, sym_d, cw_d, stream=st)
+        st.synchronize()
+        sym, cw = sym_d.cpu().numpy(), cw_d.cpu().numpy()
+        hs, hc = I.match_rows(g[:4096], X[:4096])
+        match_ok = bool(np.array_equal(hs, sym[:4096]) and np.array_equal(hc, cw[:4096]))
         P = code["P"]
         fl_sic = float(iters.sum()) * sic_flops_per_row_iter(L, P, 3, q)
         fl_amp = float(F) * L * 21 * amp_flops_per_slot_iter(q)
@@ -831,7 +839,7 @@ def wl_ura(args):
             "sic_ms_per_sample_amortised": 1e3 * t_sic / F, "sic_latency_ms_single_frame": 1e3 * t_one,
             "pipeline_latency_ms_single_frame": 1e3 * t_one_all,
             "paper_fft_bp_ms_per_sample": PAPER_FFT_BP_MS[L] if family == "random" else PAPER_PEG_FFT_BP_MS,
-            "ser": float(sym.sum() / X.size), "cer": float(cw.sum() / (F * K)),
+            "ser": float(sym.sum() / X.size), "cer": float(cw.sum() / (F * K)), "gpu_matching_equals_host": match_ok,
             "mean_bp_iters_per_row": [float(v) for v in iters.mean(0)], "rows_ok": float(ok.float().mean().item()),
             "sic_roofline": {"bound": "alu", "achieved": fl_sic / t_sic / 1e12, "peak": peak, "unit": "TFLOP/s",
                              "frac": fl_sic / t_sic / 1e12 / peak},

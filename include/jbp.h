@@ -325,6 +325,17 @@ int jbp_sic_decode(jbp_ura *u, int32_t F, const float *S, uint8_t *hat, int32_t 
 int jbp_ura_decode(jbp_ura *u, int32_t F, const float *y, uint8_t *hat, int32_t *iters, uint8_t *ok,
                    int32_t on_device, void *stream);
 
+/* Symbol and codeword errors after row alignment (eq. app_ura_hungarian): for
+ * each of F frames, the assignment of decoded rows to true rows (a permutation
+ * of K <= 8 rows) with the fewest symbol mismatches; among equally good ones
+ * the first in lexicographic order.  hat, truth [F*K*n] symbols (row k of frame
+ * f at (f*K + k)*n); sym_err [F] mismatched symbols and cw_err [F] mismatched
+ * rows under that assignment.  on_device = 1: device pointers, work enqueued on
+ * `stream` (NULL = the context's stream), no wait; 0: host pointers, the call
+ * copies, runs and waits.  An evaluation helper; it does not change a decode. */
+int jbp_match_rows(jbp_ctx *ctx, int32_t F, int32_t K, int32_t n, const uint8_t *hat, const uint8_t *truth,
+                   int32_t *sym_err, int32_t *cw_err, int32_t on_device, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1624,3 +1624,40 @@ extern "C" int jbp_ura_decode(jbp_ura* u, int32_t F, const float* y, uint8_t* ha
 {
     return ura_call(u, 3, F, y, nullptr, nullptr, hat, iters, ok, on_device, stream);
 }
+
+extern "C" int jbp_match_rows(jbp_ctx* ctx, int32_t F, int32_t K, int32_t n, const uint8_t* hat, const uint8_t* truth,
+                              int32_t* sym_err, int32_t* cw_err, int32_t on_device, void* stream)
+{
+    if (!ctx) return fail(JBP_EINVAL, "jbp_match_rows: NULL context");
+    if (F < 0 || K < 1 || K > 8 || n < 1) return fail(JBP_EINVAL, "jbp_match_rows: need F >= 0, K in 1..8, n >= 1");
+    if (F == 0) return JBP_OK;
+    if (!hat || !truth || !sym_err || !cw_err) return fail(JBP_EINVAL, "jbp_match_rows: NULL buffer");
+    JBP_CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (on_device) {
+        cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+        JBP_CU(launch_match_rows(ctx->di, F, K, n, hat, truth, sym_err, cw_err, s), "row matching");
+        return JBP_OK;
+    }
+    const size_t hb = (size_t)F * K * n;
+    DevBuf dh, dx, ds, dc;
+    bool g = false;
+    int rc;
+    if ((rc = buf_ensure(ctx, dh, hb, &g)) || (rc = buf_ensure(ctx, dx, hb, &g)) ||
+        (rc = buf_ensure(ctx, ds, sizeof(int32_t) * F, &g)) || (rc = buf_ensure(ctx, dc, sizeof(int32_t) * F, &g))) {
+        for (DevBuf* b : {&dh, &dx, &ds, &dc}) buf_free(ctx, *b);
+        return rc;
+    }
+    cudaStream_t s = ctx->stream;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(dh.p, hat, hb, cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(dx.p, truth, hb, cudaMemcpyHostToDevice, s)) ||
+        (e = launch_match_rows(ctx->di, F, K, n, P<uint8_t>(dh), P<uint8_t>(dx), P<int32_t>(ds), P<int32_t>(dc), s)) ||
+        (e = cudaMemcpyAsync(sym_err, ds.p, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaMemcpyAsync(cw_err, dc.p, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s))) {
+        for (DevBuf* b : {&dh, &dx, &ds, &dc}) buf_free(ctx, *b);
+        return cuda_fail(e, "row matching");
+    }
+    for (DevBuf* b : {&dh, &dx, &ds, &dc}) buf_free(ctx, *b);
+    return JBP_OK;
+}

@@ -97,6 +97,8 @@ struct UraDev {
 // Warps (frames) per CTA of the SIC kernel, 0 if one frame does not fit.
 int sic_warps_per_cta(const UraDev& u, const DeviceInfo& di);
 cudaError_t launch_amp(const UraDev& u, const DeviceInfo& di, int F, const float* y, float* S, cudaStream_t s);
+cudaError_t launch_match_rows(const DeviceInfo& di, int F, int K, int n, const uint8_t* hat, const uint8_t* truth,
+                              int32_t* sym_err, int32_t* cw_err, cudaStream_t s);
 cudaError_t launch_sic(const UraDev& u, const DeviceInfo& di, int F, const float* S, uint8_t* hat, int32_t* iters,
                        uint8_t* ok, cudaStream_t s);
 

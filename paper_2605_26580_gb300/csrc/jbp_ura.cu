@@ -470,12 +470,9 @@ cudaError_t launch_sic_t(const UraDev& u, const DeviceInfo& di, int F, const flo
                          int32_t* iters, uint8_t* ok, cudaStream_t s)
 {
     const SicLayout lay = sic_layout(u);
-    static bool attr_set = false;   // the same value from every caller: a benign race
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_sic<Q, DC, DV>, cudaFuncAttributeMaxDynamicSharedMemorySize, di.smem_optin);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    // per launch: the attribute belongs to the current device
+    cudaError_t e = cudaFuncSetAttribute(k_sic<Q, DC, DV>, cudaFuncAttributeMaxDynamicSharedMemorySize, di.smem_optin);
+    if (e != cudaSuccess) return e;
     // warps (frames) per CTA: the most resident warps per SM, no wider than the
     // batch needs to cover every SM once
     const int w_cap = (int)std::min<long>(kSicMaxWarps, std::max<long>(1, ((long)F + di.sm_count - 1) / di.sm_count));
@@ -484,7 +481,7 @@ cudaError_t launch_sic_t(const UraDev& u, const DeviceInfo& di, int F, const flo
         const int smem = lay.tables + w * lay.per_warp;
         if (smem > di.smem_optin) break;
         int per_sm = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sic<Q, DC, DV>, 32 * w, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sic<Q, DC, DV>, 32 * w, smem);
         if (e != cudaSuccess) return e;
         if (per_sm * w > best) {
             best = per_sm * w;
@@ -513,6 +510,86 @@ cudaError_t launch_amp_t(const UraDev& u, const DeviceInfo& di, int F, const flo
     return cudaGetLastError();
 }
 
+// Row alignment of eq. (app_ura_hungarian): one warp per frame builds the K x K
+// matrix of symbol mismatches between decoded row k and true row j, then scans
+// all K! assignments in lexicographic order (Lehmer codes split across the
+// lanes) and keeps the first one with the fewest mismatches; it reports that
+// assignment's symbol errors and codeword (row) errors.  K <= 8.
+constexpr int kMatchMaxK = 8;
+
+__global__ void __launch_bounds__(256) k_match_rows(int F, int K, int n, const uint8_t* __restrict__ hat,
+                                                    const uint8_t* __restrict__ truth, int32_t* sym_err,
+                                                    int32_t* cw_err)
+{
+    __shared__ int cost_s[8][kMatchMaxK * kMatchMaxK];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int* cost = cost_s[warp];
+    int fact = 1;
+    for (int i = 2; i <= K; ++i) fact *= i;
+    for (long f = (long)blockIdx.x * (blockDim.x >> 5) + warp; f < F; f += (long)gridDim.x * (blockDim.x >> 5)) {
+        const uint8_t* h = hat + (size_t)f * K * n;
+        const uint8_t* x = truth + (size_t)f * K * n;
+        for (int pr = 0; pr < K * K; ++pr) {
+            const int k = pr / K, j = pr % K;
+            int c = 0;
+            for (int i = lane; i < n; i += 32) c += h[(size_t)k * n + i] != x[(size_t)j * n + i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            if (lane == 0) cost[pr] = c;
+        }
+        __syncwarp();
+        int best = 0x7fffffff, best_r = 0x7fffffff;
+        for (int r = lane; r < fact; r += 32) {
+            // r-th permutation in lexicographic order (factorial number system)
+            int avail = (1 << K) - 1, rem = r, sum = 0, div = fact;
+            for (int k = 0; k < K; ++k) {
+                div /= (K - k);
+                int idx = rem / div;
+                rem %= div;
+                int j = 0;
+                for (;; ++j)
+                    if ((avail >> j) & 1) {
+                        if (idx == 0) break;
+                        --idx;
+                    }
+                avail &= ~(1 << j);
+                sum += cost[k * K + j];
+            }
+            if (sum < best) {
+                best = sum;
+                best_r = r;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int ob = __shfl_xor_sync(0xffffffffu, best, o), orr = __shfl_xor_sync(0xffffffffu, best_r, o);
+            if (ob < best || (ob == best && orr < best_r)) {
+                best = ob;
+                best_r = orr;
+            }
+        }
+        if (lane == 0) {
+            int avail = (1 << K) - 1, rem = best_r, div = fact, cw = 0;
+            for (int k = 0; k < K; ++k) {
+                div /= (K - k);
+                int idx = rem / div;
+                rem %= div;
+                int j = 0;
+                for (;; ++j)
+                    if ((avail >> j) & 1) {
+                        if (idx == 0) break;
+                        --idx;
+                    }
+                avail &= ~(1 << j);
+                cw += cost[k * K + j] > 0;
+            }
+            sym_err[f] = best;
+            cw_err[f] = cw;
+        }
+        __syncwarp();
+    }
+}
+
 }  // namespace
 
 int sic_warps_per_cta(const UraDev& u, const DeviceInfo& di)
@@ -521,6 +598,16 @@ int sic_warps_per_cta(const UraDev& u, const DeviceInfo& di)
     const int room = di.smem_optin - lay.tables;
     if (room < lay.per_warp) return 0;
     return std::min(kSicMaxWarps, room / lay.per_warp);
+}
+
+cudaError_t launch_match_rows(const DeviceInfo& di, int F, int K, int n, const uint8_t* hat, const uint8_t* truth,
+                              int32_t* sym_err, int32_t* cw_err, cudaStream_t s)
+{
+    if (F <= 0) return cudaSuccess;
+    if (K < 1 || K > kMatchMaxK || n < 1) return cudaErrorInvalidValue;
+    const int grid = (int)std::min<long>(((long)F + 7) / 8, (long)di.sm_count * 8);
+    k_match_rows<<<grid, 256, 0, s>>>(F, K, n, hat, truth, sym_err, cw_err);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_amp(const UraDev& u, const DeviceInfo& di, int F, const float* y, float* S, cudaStream_t s)

@@ -24,7 +24,7 @@ EXPORTS = [
     "jbp_context_create", "jbp_context_destroy", "jbp_create", "jbp_destroy", "jbp_decode",
     "jbp_submit", "jbp_poll", "jbp_serving_stats", "jbp_last_error", "jbp_step_channel",
     "jbp_step_check", "jbp_step_var", "jbp_step_syndrome", "jbp_query", "jbp_decode_noalloc", "jbp_stats", "jbp_decode_many", "jbp_tune",
-    "jbp_ura_create", "jbp_ura_destroy", "jbp_amp_evidence", "jbp_sic_decode", "jbp_ura_decode",
+    "jbp_ura_create", "jbp_ura_destroy", "jbp_amp_evidence", "jbp_sic_decode", "jbp_ura_decode", "jbp_match_rows",
 ]
 
 
@@ -93,6 +93,7 @@ def lib():
             L.jbp_stats.argtypes = [vp, C.POINTER(u64), C.POINTER(i32)]
             L.jbp_decode_noalloc.argtypes = [C.POINTER(Code), i32, C.POINTER(Channel), i32, i32, i32, vp, vp, vp,
                                              vp, vp]
+            L.jbp_match_rows.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, i32, vp]
             L.jbp_ura_create.argtypes = [vp, C.POINTER(Code), C.POINTER(UraParams), C.POINTER(vp)]
             L.jbp_ura_destroy.argtypes = [vp]
             L.jbp_amp_evidence.argtypes = [vp, i32, vp, vp, i32, vp]
@@ -163,6 +164,21 @@ class Context:
             bs[i] = Batch(int(y.shape[0]), _addr(y), _addr(hat), _addr(it), _addr(ok), None, 1, FORM_AUTO, None,
                           _addr(sig))
         check(lib().jbp_decode_many(self.ptr, n, hs, bs, _stream_ptr(stream)))
+
+    def match_rows(self, hat, truth):
+        """Row-aligned errors (host arrays [F, K, n]): (symbol errors [F], row errors [F])."""
+        hat = np.ascontiguousarray(hat, dtype=np.uint8)
+        truth = np.ascontiguousarray(truth, dtype=np.uint8)
+        F, K, n = truth.shape
+        sym = np.empty(F, dtype=np.int32)
+        cw = np.empty(F, dtype=np.int32)
+        check(lib().jbp_match_rows(self.ptr, F, K, n, _addr(hat), _addr(truth), _addr(sym), _addr(cw), 0, None))
+        return sym, cw
+
+    def match_rows_device(self, hat, truth, sym, cw, stream=None):
+        F, K, n = truth.shape
+        check(lib().jbp_match_rows(self.ptr, int(F), int(K), int(n), _addr(hat), _addr(truth), _addr(sym), _addr(cw),
+                                   1, _stream_ptr(stream)))
 
     def serving_stats(self):
         c = C.c_uint64()

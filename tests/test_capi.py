@@ -45,6 +45,7 @@ def test_null_arguments_are_rejected(jbp_lib):
     assert lib.jbp_amp_evidence(None, 1, None, None, 0, None) == jbp_lib.EINVAL
     assert lib.jbp_sic_decode(None, 1, None, None, None, None, 0, None) == jbp_lib.EINVAL
     assert lib.jbp_ura_decode(None, 1, None, None, None, None, 0, None) == jbp_lib.EINVAL
+    assert lib.jbp_match_rows(None, 1, 2, 3, None, None, None, None, 0, None) == jbp_lib.EINVAL
 
 
 def test_bad_options_are_rejected_before_touching_the_gpu(jbp_lib):

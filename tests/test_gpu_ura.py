@@ -210,3 +210,22 @@ def test_evidence_path_edge_cases(jbp_lib):
         jbp_lib.EvidenceDecoder(ctx, big, 2, np.tile(np.arange(24, dtype=np.int32), (512, 1)), 0.03, 20.0,
                                 -4.0)
     ctx.close()
+
+
+@pytest.mark.parametrize("K,n,F", [(1, 12, 40), (2, 12, 64), (3, 1, 64), (5, 300, 20), (8, 24, 6)])
+def test_gpu_row_matching_equals_host_alignment(jbp_lib, K, n, F):
+    """jbp_match_rows gives the same row-aligned symbol and row errors as the
+    host's exhaustive alignment, including its tie rule (a four-letter alphabet
+    makes ties common)."""
+    rng = np.random.default_rng(K * 1000 + n)
+    truth = rng.integers(0, 4, size=(F, K, n)).astype(np.uint8)
+    hat = truth[:, rng.permutation(K), :].copy()
+    flip = rng.random((F, K, n)) < 0.3
+    hat[flip] = rng.integers(0, 4, size=int(flip.sum())).astype(np.uint8)
+    ctx = _ctx(jbp_lib)
+    try:
+        sym, cw = ctx.match_rows(hat, truth)
+    finally:
+        ctx.close()
+    hsym, hcw = I.match_rows(hat, truth)
+    assert np.array_equal(sym, hsym) and np.array_equal(cw, hcw)
