@@ -589,7 +589,7 @@ __host__ __device__ __forceinline__ int blk_pad(int Q) { return Q + Q + 48; }
 // max 1; mode 1: normalise to max 1 and floor at kRelFloor.  Returns the team
 // max before scaling.
 template <int T, bool AREV>
-__device__ __noinline__ float team_corr(float* Y, int L, const float* A, int NT, const float* X, int xoff, int mode,
+__device__ __forceinline__ float team_corr(float* Y, int L, const float* A, int NT, const float* X, int xoff, int mode,
                                         TeamLane Lr)
 {
     const int nb = (L + kBR - 1) / kBR;
