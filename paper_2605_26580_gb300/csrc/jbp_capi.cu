@@ -1,6 +1,7 @@
 // jbp_capi.cu -- the C ABI (include/jbp.h): contexts, decoder handles, the three
 // launch forms, single-step entry points and the continuous-batching serving loop.
 #include <algorithm>
+#include <array>
 #include <memory>
 #include <atomic>
 #include <chrono>
@@ -209,6 +210,7 @@ struct jbp_h {
     int32_t* d_pos_of = nullptr;
     int* d_tc_error = nullptr;
     uint16_t* d_slot = nullptr;
+    uint16_t* d_chk_order = nullptr;
     int64_t table_bytes = 0;
     Workspace ws;
     std::mutex ws_mu;
@@ -230,6 +232,7 @@ struct jbp_h {
         g.slot = d_slot;
         g.tc_error = d_tc_error;
         g.sigma2_f = nullptr;
+        g.chk_order = d_chk_order;
         return g;
     }
 };
@@ -461,6 +464,86 @@ extern "C" int jbp_context_destroy(jbp_ctx* ctx)
 // handles
 // ---------------------------------------------------------------------------
 
+// Order of the K*P check units (k, j) in the fused kernel's check phase.  A
+// warp runs 32 consecutive units, and the d-th edge message of unit (k, j) lives
+// in shared-memory bank (position mod 32) of that edge, so the d-th loads of a
+// warp cost as many wavefronts as the largest number of its units sharing that
+// bank.  Greedy fill of each run of 32 with units whose banks are still free,
+// then pairwise swaps between runs that do not raise the sum over runs and edge
+// ranks of the largest bank count.  Deterministic (fixed-seed xorshift); the
+// order does not change any result.
+static std::vector<uint16_t> check_order(int K, int P, int E, const std::vector<uint16_t>& slot)
+{
+    const int N = K * P, R = (N + 31) / 32;
+    std::vector<std::array<uint8_t, kDC>> col(N);
+    for (int u = 0; u < N; ++u) {
+        const int k = u / P, j = u % P;
+        for (int d = 0; d < kDC; ++d) col[u][d] = (uint8_t)((slot[(size_t)k * E + kDC * j + d] >> 1) & 31);
+    }
+    uint64_t x = 0x9e3779b97f4a7c15ull;
+    auto rnd = [&]() {
+        x ^= x << 13;
+        x ^= x >> 7;
+        x ^= x << 17;
+        return x;
+    };
+    std::vector<int> rem(N);
+    for (int u = 0; u < N; ++u) rem[u] = u;
+    for (int i = N - 1; i > 0; --i) std::swap(rem[i], rem[rnd() % (uint64_t)(i + 1)]);
+    std::vector<int> order;
+    order.reserve(N);
+    std::vector<std::array<std::array<int, 32>, kDC>> cnt(R);
+    for (int r = 0; r < R; ++r) {
+        for (auto& a : cnt[r]) a.fill(0);
+        const int want = std::min(32, N - r * 32);
+        int got = 0;
+        for (int pass = 0; pass < 2 && got < want; ++pass)
+            for (size_t i = 0; i < rem.size() && got < want;) {
+                const int u = rem[i];
+                bool free_all = true;
+                for (int d = 0; d < kDC; ++d) free_all = free_all && cnt[r][d][col[u][d]] == 0;
+                if (pass == 1 || free_all) {
+                    for (int d = 0; d < kDC; ++d) cnt[r][d][col[u][d]]++;
+                    order.push_back(u);
+                    rem.erase(rem.begin() + i);
+                    ++got;
+                } else {
+                    ++i;
+                }
+            }
+    }
+    auto run_cost = [&](int r) {
+        int c = 0;
+        for (int d = 0; d < kDC; ++d) c += *std::max_element(cnt[r][d].begin(), cnt[r][d].end());
+        return c;
+    };
+    if (R > 1) {
+        const long iters = 400l * N;
+        for (long it = 0; it < iters; ++it) {
+            const int i1 = (int)(rnd() % (uint64_t)N), i2 = (int)(rnd() % (uint64_t)N);
+            const int r1 = i1 / 32, r2 = i2 / 32;
+            if (r1 == r2) continue;
+            const int u1 = order[i1], u2 = order[i2];
+            const int before = run_cost(r1) + run_cost(r2);
+            for (int d = 0; d < kDC; ++d) {
+                cnt[r1][d][col[u1][d]]--; cnt[r1][d][col[u2][d]]++;
+                cnt[r2][d][col[u2][d]]--; cnt[r2][d][col[u1][d]]++;
+            }
+            if (run_cost(r1) + run_cost(r2) <= before) {
+                std::swap(order[i1], order[i2]);
+            } else {
+                for (int d = 0; d < kDC; ++d) {
+                    cnt[r1][d][col[u1][d]]++; cnt[r1][d][col[u2][d]]--;
+                    cnt[r2][d][col[u2][d]]++; cnt[r2][d][col[u1][d]]--;
+                }
+            }
+        }
+    }
+    std::vector<uint16_t> out(N);
+    for (int i = 0; i < N; ++i) out[i] = (uint16_t)order[i];
+    return out;
+}
+
 extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t q, const jbp_channel* chan,
                           jbp_h** out)
 {
@@ -512,6 +595,12 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
                 const int rank = var_edge[(size_t)i * dv] == e ? 0 : 1;
                 slot[(size_t)k * E + e] = (uint16_t)(pos_of[(size_t)k * n + i] * 2 + rank);
             }
+    // only where the fused position-major form can run (K <= 4, q <= 16, one
+    // frame's state in shared memory)
+    const bool want_order = want_slot && dc == kDC && K <= 4 && q <= 16 &&
+                            4ll * K * (E + n) * q <= (int64_t)ctx->di.smem_optin;
+    std::vector<uint16_t> chk_order;
+    if (want_order) chk_order = check_order(K, P, E, slot);
     std::vector<uint8_t> gmul((size_t)q * q), gdiv((size_t)q * q);
     std::vector<int> inv(q, 0);
     for (int a = 1; a < q; ++a)
@@ -542,7 +631,8 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
         (rc = dev_alloc(ctx, &h->d_fallbacks, (size_t)1, &h->table_bytes)) ||
         (rc = dev_alloc(ctx, &h->d_pos_of, (size_t)K * n, &h->table_bytes)) ||
         (rc = dev_alloc(ctx, &h->d_tc_error, (size_t)1, &h->table_bytes)) ||
-        (want_slot && (rc = dev_alloc(ctx, &h->d_slot, (size_t)K * E, &h->table_bytes)))) {
+        (want_slot && (rc = dev_alloc(ctx, &h->d_slot, (size_t)K * E, &h->table_bytes))) ||
+        (want_order && (rc = dev_alloc(ctx, &h->d_chk_order, (size_t)K * P, &h->table_bytes)))) {
         jbp_destroy(h);
         return rc;
     }
@@ -557,7 +647,9 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
         (e = cudaMemset(h->d_tc_error, 0, sizeof(int))) ||
         (e = cudaMemcpy(h->d_pos_of, pos_of.data(), sizeof(int32_t) * pos_of.size(), cudaMemcpyHostToDevice)) ||
         (want_slot &&
-         (e = cudaMemcpy(h->d_slot, slot.data(), sizeof(uint16_t) * slot.size(), cudaMemcpyHostToDevice)))) {
+         (e = cudaMemcpy(h->d_slot, slot.data(), sizeof(uint16_t) * slot.size(), cudaMemcpyHostToDevice))) ||
+        (want_order && (e = cudaMemcpy(h->d_chk_order, chk_order.data(), sizeof(uint16_t) * chk_order.size(),
+                                       cudaMemcpyHostToDevice)))) {
         jbp_destroy(h);
         return cuda_fail(e, "jbp_create: copy tables");
     }
@@ -623,6 +715,7 @@ extern "C" int jbp_destroy(jbp_h* h)
     dev_free(ctx, h->d_pos_of, sizeof(int32_t) * (size_t)h->K * h->n);
     dev_free(ctx, h->d_tc_error, sizeof(int));
     if (h->d_slot) dev_free(ctx, h->d_slot, sizeof(uint16_t) * (size_t)h->K * h->E);
+    if (h->d_chk_order) dev_free(ctx, h->d_chk_order, sizeof(uint16_t) * (size_t)h->K * h->P);
     delete h;
     return JBP_OK;
 }

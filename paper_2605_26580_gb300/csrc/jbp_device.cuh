@@ -46,6 +46,7 @@ struct Graph {
     const uint16_t* slot;     // [K*E]   pi_k(var of e)*2 + (e's rank in its var) (fused layout)
     int* tc_error;            // set to 1 if a tensor-core wait expired (may be null: FP32 only)
     const float* sigma2_f;    // [F]     per-frame noise variance of this batch (may be null)
+    const uint16_t* chk_order;  // [K*P] order of the check units in the fused check phase (may be null)
 };
 
 // 1 / sigma2 of frame f

@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kFusedMaxThreads) k_fused(Graph g, int F, int 
 // four edges through slot (the only irregular access of an iteration).
 
 struct PosLayout {
-    size_t msg, ch2v, y, hat, unsat, active, slot, coef, gmul, gdiv, total;
+    size_t msg, ch2v, y, hat, unsat, active, slot, order, coef, gmul, gdiv, total;
 };
 
 __host__ __device__ inline PosLayout pos_layout(const Graph& g, int G)
@@ -211,6 +211,7 @@ __host__ __device__ inline PosLayout pos_layout(const Graph& g, int G)
     L.unsat = o;  o = align16(o + (size_t)G * g.K);
     L.active = o; o = align16(o + (size_t)G);
     L.slot = o;   o = align16(o + sizeof(uint16_t) * (size_t)g.K * g.E);
+    L.order = o;  o = align16(o + sizeof(uint16_t) * (size_t)g.K * g.P);
     L.coef = o;   o = align16(o + (size_t)g.E);
     L.gmul = o;   o = align16(o + (size_t)g.Q * g.Q);
     L.gdiv = o;   o = align16(o + (size_t)g.Q * g.Q);
@@ -239,6 +240,7 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
     uint8_t* s_unsat = sm + lay.unsat;
     uint8_t* s_active = sm + lay.active;
     uint16_t* s_slot = reinterpret_cast<uint16_t*>(sm + lay.slot);
+    uint16_t* s_order = reinterpret_cast<uint16_t*>(sm + lay.order);
     uint8_t* s_coef = sm + lay.coef;
     uint8_t* s_mul = sm + lay.gmul;
     uint8_t* s_div = sm + lay.gdiv;
@@ -250,6 +252,7 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
         s_div[i] = g.gf_div[i];
     }
     for (int i = threadIdx.x; i < K * E; i += blockDim.x) s_slot[i] = g.slot[i];
+    for (int i = threadIdx.x; i < K * P; i += blockDim.x) s_order[i] = g.chk_order ? g.chk_order[i] : (uint16_t)i;
     for (int i = threadIdx.x; i < E; i += blockDim.x) s_coef[i] = g.chk_coef[i];
 
     const int groups = (F + G - 1) / G;
@@ -281,9 +284,9 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
                 }
             }
             __syncthreads();
-            // (B) check nodes
+            // (B) check nodes, in the bank-spreading order of chk_order
             for (int unit = threadIdx.x; unit < gc * K * P; unit += blockDim.x) {
-                const int gi = unit / (K * P), rem = unit % (K * P), k = rem / P, j = rem % P;
+                const int gi = unit / (K * P), rem = s_order[unit % (K * P)], k = rem / P, j = rem % P;
                 if (!s_active[gi]) continue;
                 check_thread_pos<Q>(s_msg + gi * fs, NB, k, j, s_slot + k * E, s_coef, s_div);
             }

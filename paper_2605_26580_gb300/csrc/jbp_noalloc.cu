@@ -185,6 +185,7 @@ extern "C" int jbp_decode_noalloc(const jbp_code* code, int32_t K, const jbp_cha
     g.slot = nullptr;
     g.tc_error = nullptr;
     g.sigma2_f = nullptr;
+    g.chk_order = nullptr;
     float* msg = reinterpret_cast<float*>(D + o_msg);
     float* ch2v = reinterpret_cast<float*>(D + o_ch2v);
     uint8_t* active = D + o_act;
