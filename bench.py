@@ -207,7 +207,8 @@ def cpu_baseline_leg() -> dict:
     O.build()
     from paper_2605_26580_gb300 import inputs as I
     cores = os.cpu_count() or 1
-    S = max(8, cores)
+    # about 10-20 s of CPU work on the host's cores (one frame is ~1.1 s of one core)
+    S = max(16, 12 * cores)
     code = I.make_code(N_SYM, Q)
     fr = I.make_frames(code, K_USERS, 10.0, S, seed=frame_seed(2, 0))
     t0 = time.perf_counter()

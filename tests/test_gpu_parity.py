@@ -487,3 +487,45 @@ def test_variable_degree_three_matches_oracle(env, form):
     bad, _ = _margin_mismatch(got, ref)
     assert bad == 0
     assert (got["iters"] == ref["iters"]).all()
+
+
+@pytest.mark.timeout(120)
+def test_serving_destroy_with_frames_in_flight(env):
+    """jbp_destroy of a decoder whose frames are queued or part-way through
+    their iterations returns once its pool has drained; a frame it cancelled
+    polls JBP_ECLOSED, one it finished polls its result; another decoder's
+    frames are unaffected and the context then closes."""
+    jbp, O, torch = env
+    ctx = jbp.Context(iters=50, early_stop=False, block_iters=5)
+    code_a = I.make_code(512, 16)
+    fr_a = I.make_frames(code_a, 6, 10.0, 64, seed=71)
+    code_b = I.make_code(64, 4)
+    fr_b = I.make_frames(code_b, 2, 12.0, 8, seed=72)
+    dec_a = jbp.Decoder(ctx, code_a, 6, fr_a["sigma2"], fr_a["perm"])
+    dec_b = jbp.Decoder(ctx, code_b, 2, fr_b["sigma2"], fr_b["perm"])
+    try:
+        alone_b = [dec_b.decode(fr_b["y"][i:i + 1], form=jbp.FORM_STEP) for i in range(8)]
+        ta = [dec_a.submit(fr_a["y"][i]) for i in range(64)]
+        tb = [dec_b.submit(fr_b["y"][i]) for i in range(8)]
+        dec_a.close()
+        done = cancelled = 0
+        for tk in ta:
+            try:
+                res = ctx.poll(tk, 512, 6)
+            except jbp.JBPError as e:
+                assert e.code == jbp.ECLOSED
+                cancelled += 1
+                continue
+            assert res is not None and res["iters"] == 50
+            done += 1
+        assert done + cancelled == 64
+        for i, tk in enumerate(tb):
+            while True:
+                res = ctx.poll(tk, 64, 2)
+                if res is not None:
+                    break
+            assert np.array_equal(res["hat"], alone_b[i]["hat"][0])
+    finally:
+        dec_a.close()
+        dec_b.close()
+        ctx.close()
