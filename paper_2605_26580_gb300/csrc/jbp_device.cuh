@@ -1116,10 +1116,15 @@ __device__ __forceinline__ void sstore(float* base, const float (&v)[Q])
 }
 
 // Channel node of use p, thread shape, position-major layout.  msg_f / ch2v_f:
-// the frame's blocks; NB = ceil(n / 32).
+// the frame's blocks; NB = ceil(n / 32).  hat_f (may be null): before the
+// channel messages are replaced, the previous iteration's posterior
+// ch2v * c2v_0 * c2v_1 of each variable on this use (eq. app_ldpc_marginal) is
+// formed from the messages already loaded here and its decision (ties -> lowest
+// symbol) stored at hat_f[k*NB*32 + p]: the decision phase of the previous
+// iteration, folded into this one.
 template <int K, int Q>
 __device__ __forceinline__ void chan_thread_pos(const Graph& g, float* msg_f, float* ch2v_f, int NB, float y,
-                                                float inv_s2, int p)
+                                                float inv_s2, int p, uint8_t* hat_f = nullptr)
 {
     float mu[K][Q];
 #pragma unroll
@@ -1130,6 +1135,21 @@ __device__ __forceinline__ void chan_thread_pos(const Graph& g, float* msg_f, fl
         sload<Q>(msg_f + pos_vec<Q>(row + 1, p), a1);
 #pragma unroll
         for (int a = 0; a < Q; ++a) a0[a] *= a1[a];
+        if (hat_f) {
+            float b[Q];
+            sload<Q>(ch2v_f + pos_vec<Q>(k * NB + (p >> 5), p), b);
+            float bv = b[0] * a0[0];
+            int bi = 0;
+#pragma unroll
+            for (int a = 1; a < Q; ++a) {
+                const float v = b[a] * a0[a];
+                if (v > bv) {
+                    bv = v;
+                    bi = a;
+                }
+            }
+            hat_f[k * NB * 32 + p] = (uint8_t)bi;
+        }
         const float inv = 1.0f / vmax(a0);
 #pragma unroll
         for (int a = 0; a < Q; ++a) mu[k][a] = a0[a] * inv;

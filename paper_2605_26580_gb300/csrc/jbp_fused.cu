@@ -264,34 +264,13 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
         for (int i = threadIdx.x; i < G; i += blockDim.x) s_active[i] = i < gc ? 1 : 0;
         __syncthreads();
 
-        for (int t = 1; t <= T_it; ++t) {
-            // (A) channel nodes, v2c in place
-            if constexpr (PAIR && K == 4) {
-                const int half = threadIdx.x & 1;
-                const unsigned pmask = 3u << (threadIdx.x & 30);
-                for (int unit = threadIdx.x >> 1; unit < gc * n; unit += blockDim.x >> 1) {
-                    const int gi = unit / n, p = unit % n;
-                    if (!s_active[gi]) continue;
-                    chan_pair_pos<Q>(g, s_msg + gi * fs, s_ch2v + gi * vs, NB, s_y[gi * NB * 32 + p],
-                                     frame_inv_s2(g, f0 + gi), p, half, pmask);
-                }
-            } else {
-                for (int unit = threadIdx.x; unit < gc * n; unit += blockDim.x) {
-                    const int gi = unit / n, p = unit % n;
-                    if (!s_active[gi]) continue;
-                    chan_thread_pos<K, Q>(g, s_msg + gi * fs, s_ch2v + gi * vs, NB, s_y[gi * NB * 32 + p],
-                                          frame_inv_s2(g, f0 + gi), p);
-                }
-            }
-            __syncthreads();
-            // (B) check nodes, in the bank-spreading order of chk_order
-            for (int unit = threadIdx.x; unit < gc * K * P; unit += blockDim.x) {
-                const int gi = unit / (K * P), rem = s_order[unit % (K * P)], k = rem / P, j = rem % P;
-                if (!s_active[gi]) continue;
-                check_thread_pos<Q>(s_msg + gi * fs, NB, k, j, s_slot + k * E, s_coef, s_div);
-            }
-            __syncthreads();
-            // (C) posterior and decisions (position order)
+        // Without a log-posterior output the decision phase of iteration t is
+        // folded into the channel phase of iteration t + 1 (which loads the same
+        // messages), and its syndromes and stop test run between that channel
+        // phase and the next check phase; a final pass decides after the last
+        // iteration.
+        const bool fold = !PAIR && logpost == nullptr;
+        auto phase_decide = [&]() {
             for (int unit = threadIdx.x; unit < gc * K * n; unit += blockDim.x) {
                 const int gi = unit / (K * n), rem = unit % (K * n), k = rem / n, p = rem % n;
                 if (!s_active[gi]) continue;
@@ -300,8 +279,9 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
                 s_hat[gi * hs + k * NB * 32 + p] = (uint8_t)var_thread_pos<Q>(s_msg + gi * fs, s_ch2v + gi * vs,
                                                                               NB, k, p, lp);
             }
-            __syncthreads();
-            // (D) syndromes
+        };
+        // syndromes and the per-frame stop after iteration t; returns the frames still active
+        auto phase_stop = [&](int t) {
             for (int w = threadIdx.x; w < gc * K * P; w += blockDim.x) {
                 const int gi = w / (K * P), rem = w % (K * P), k = rem / P, j = rem % P;
                 if (!s_active[gi]) continue;
@@ -316,7 +296,6 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
             }
             if (threadIdx.x == 0) s_nactive = 0;
             __syncthreads();
-            // (E) per-frame stop
             for (int gi = threadIdx.x; gi < gc; gi += blockDim.x) {
                 if (!s_active[gi]) continue;
                 bool all = true;
@@ -331,7 +310,56 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
                 else atomicAdd(&s_nactive, 1);
             }
             __syncthreads();
-            if (s_nactive == 0) break;
+            return s_nactive;
+        };
+        bool all_stopped = false;
+        for (int t = 1; t <= T_it; ++t) {
+            // (A) channel nodes, v2c in place (and, folded, the decisions of iteration t - 1)
+            if constexpr (PAIR && K == 4) {
+                const int half = threadIdx.x & 1;
+                const unsigned pmask = 3u << (threadIdx.x & 30);
+                for (int unit = threadIdx.x >> 1; unit < gc * n; unit += blockDim.x >> 1) {
+                    const int gi = unit / n, p = unit % n;
+                    if (!s_active[gi]) continue;
+                    chan_pair_pos<Q>(g, s_msg + gi * fs, s_ch2v + gi * vs, NB, s_y[gi * NB * 32 + p],
+                                     frame_inv_s2(g, f0 + gi), p, half, pmask);
+                }
+            } else {
+                const bool dec = fold && t > 1;
+                for (int unit = threadIdx.x; unit < gc * n; unit += blockDim.x) {
+                    const int gi = unit / n, p = unit % n;
+                    if (!s_active[gi]) continue;
+                    chan_thread_pos<K, Q>(g, s_msg + gi * fs, s_ch2v + gi * vs, NB, s_y[gi * NB * 32 + p],
+                                          frame_inv_s2(g, f0 + gi), p, dec ? s_hat + gi * hs : nullptr);
+                }
+            }
+            __syncthreads();
+            if (fold && t > 1 && phase_stop(t - 1) == 0) {
+                all_stopped = true;
+                break;
+            }
+            // (B) check nodes, in the bank-spreading order of chk_order
+            for (int unit = threadIdx.x; unit < gc * K * P; unit += blockDim.x) {
+                const int gi = unit / (K * P), rem = s_order[unit % (K * P)], k = rem / P, j = rem % P;
+                if (!s_active[gi]) continue;
+                check_thread_pos<Q>(s_msg + gi * fs, NB, k, j, s_slot + k * E, s_coef, s_div);
+            }
+            __syncthreads();
+            if (!fold) {
+                // (C) posterior and decisions (position order), (D) syndromes, (E) per-frame stop
+                phase_decide();
+                __syncthreads();
+                if (phase_stop(t) == 0) {
+                    all_stopped = true;
+                    break;
+                }
+            }
+        }
+        if (fold && !all_stopped) {
+            // decisions, syndromes and stop of the last iteration
+            phase_decide();
+            __syncthreads();
+            phase_stop(T_it);
         }
         // decisions back to variable order
         for (int w = threadIdx.x; w < gc * K * n; w += blockDim.x) {
