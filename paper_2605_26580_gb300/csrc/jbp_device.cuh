@@ -577,6 +577,13 @@ __device__ bool chan_trellis(const Graph& g, const float* msg_f, size_t ustride,
 
 constexpr int kBR = 9;
 
+// outputs per lane for a field size: 9 at q = 64, 7 below (measured faster
+// there); both odd, and both within the 48-float right pad (overrun <= 2 BR + 1)
+template <int Q>
+struct CorrBlock {
+    static constexpr int BR = Q >= 64 ? 9 : 7;
+};
+
 template <int Q>
 struct BlkPad {
     static constexpr int L = Q;            // left zero pad (prefix convolutions read X(s - (q-1)))
@@ -586,14 +593,14 @@ struct BlkPad {
 __host__ __device__ __forceinline__ int blk_pad(int Q) { return Q + Q + 48; }
 
 // Y(o) for o < L at Y[o]; A(t) at A[t] (t < NT; AREV: A(NT-1-t)); X(i) at X[i]
-// (i may run kBR + q beyond the data, into zero pads).  mode 0: rescale Y to
+// (i may run BR + q beyond the data, into zero pads; BR outputs per lane).  mode 0: rescale Y to
 // max 1; mode 1: normalise to max 1 and floor at kRelFloor.  Returns the team
 // max before scaling.
-template <int T, bool AREV>
+template <int T, bool AREV, int BR = kBR>
 __device__ __forceinline__ float team_corr(float* Y, int L, const float* A, int NT, const float* X, int xoff, int mode,
                                         TeamLane Lr)
 {
-    const int nb = (L + kBR - 1) / kBR;
+    const int nb = (L + BR - 1) / BR;
     int C = 1;
     while (C * 2 * nb <= T) C *= 2;
     const int passes = (nb + T - 1) / T;  // only when C == 1 and nb > T
@@ -604,53 +611,53 @@ __device__ __forceinline__ float team_corr(float* Y, int L, const float* A, int 
         const int ob = (C == 1) ? (Lr.tl + ps * T) : (Lr.tl / C);
         const int c = (C == 1) ? 0 : (Lr.tl % C);
         const bool active = ob < nb;
-        const int o0 = ob * kBR;
+        const int o0 = ob * BR;
         const int tb = min(NT, c * tc), te = min(NT, tb + tc);
-        float acc[kBR];
+        float acc[BR];
 #pragma unroll
-        for (int r = 0; r < kBR; ++r) acc[r] = 0.0f;
+        for (int r = 0; r < BR; ++r) acc[r] = 0.0f;
         if (active && tb < te) {
-            float xw[2 * kBR];
+            float xw[2 * BR];
             const float* xp = X + o0 + tb + xoff;
 #pragma unroll
-            for (int i = 0; i < 2 * kBR - 1; ++i) xw[i] = xp[i];
+            for (int i = 0; i < 2 * BR - 1; ++i) xw[i] = xp[i];
             const float* ap = AREV ? A + (NT - 1 - tb) : A + tb;
             int t0 = tb;
-            // full groups of kBR taps
-            for (; t0 + kBR <= te; t0 += kBR) {
+            // full groups of BR taps
+            for (; t0 + BR <= te; t0 += BR) {
 #pragma unroll
-                for (int j = 0; j < kBR; ++j) {
+                for (int j = 0; j < BR; ++j) {
                     const float a = AREV ? ap[-(t0 - tb) - j] : ap[(t0 - tb) + j];
 #pragma unroll
-                    for (int r = 0; r < kBR; ++r) acc[r] = fmaf(a, xw[r + j], acc[r]);
+                    for (int r = 0; r < BR; ++r) acc[r] = fmaf(a, xw[r + j], acc[r]);
                 }
-                if (t0 + kBR < te) {
+                if (t0 + BR < te) {
 #pragma unroll
-                    for (int i = 0; i < kBR - 1; ++i) xw[i] = xw[i + kBR];
-                    const float* xn = xp + (t0 - tb) + 2 * kBR - 1;
+                    for (int i = 0; i < BR - 1; ++i) xw[i] = xw[i + BR];
+                    const float* xn = xp + (t0 - tb) + 2 * BR - 1;
 #pragma unroll
-                    for (int i = 0; i < kBR; ++i) xw[kBR - 1 + i] = xn[i];
+                    for (int i = 0; i < BR; ++i) xw[BR - 1 + i] = xn[i];
                 }
             }
             // tail
             if (t0 < te) {
 #pragma unroll
-                for (int j = 0; j < kBR; ++j) {
+                for (int j = 0; j < BR; ++j) {
                     if (t0 + j < te) {
                         const float a = AREV ? ap[-(t0 - tb) - j] : ap[(t0 - tb) + j];
 #pragma unroll
-                        for (int r = 0; r < kBR; ++r) acc[r] = fmaf(a, xw[r + j], acc[r]);
+                        for (int r = 0; r < BR; ++r) acc[r] = fmaf(a, xw[r + j], acc[r]);
                     }
                 }
             }
         }
         for (int off = 1; off < C; off <<= 1)
 #pragma unroll
-            for (int r = 0; r < kBR; ++r) acc[r] += __shfl_xor_sync(Lr.mask, acc[r], off, T);
+            for (int r = 0; r < BR; ++r) acc[r] += __shfl_xor_sync(Lr.mask, acc[r], off, T);
         float lmx = kNegInf;
         if (active && c == 0) {
 #pragma unroll
-            for (int r = 0; r < kBR; ++r)
+            for (int r = 0; r < BR; ++r)
                 if (o0 + r < L) {
                     lmx = fmaxf(lmx, acc[r]);
                     Y[o0 + r] = acc[r];
@@ -734,7 +741,7 @@ __device__ bool chan_blocked(const Graph& g, const float* msg_f, size_t ustride,
     for (int s = Lr.tl; s <= S; s += T) B[s] = __expf(gt.expo(s));
     __syncwarp(Lr.mask);
     for (int j = 1; j + 1 < K; ++j) {
-        const float m = team_corr<T, true>(Fb + blk_prefix_offset(j + 1, Q) + PL, (j + 1) * D + 1, mu + j * Q, Q,
+        const float m = team_corr<T, true, CorrBlock<Q>::BR>(Fb + blk_prefix_offset(j + 1, Q) + PL, (j + 1) * D + 1, mu + j * Q, Q,
                                            Fb + blk_prefix_offset(j, Q) + PL, -(Q - 1), 0, Lr);
         if (!(m > 0.0f)) bad = true;
     }
@@ -749,9 +756,9 @@ __device__ bool chan_blocked(const Graph& g, const float* msg_f, size_t ustride,
             __syncwarp(Lr.mask);
         } else {
             const float* Fk = Fb + blk_prefix_offset(k, Q) + PL;
-            const float m = team_corr<T, false>(res + k * Q, Q, Fk, k * D + 1, B, 0, 1, Lr);
+            const float m = team_corr<T, false, CorrBlock<Q>::BR>(res + k * Q, Q, Fk, k * D + 1, B, 0, 1, Lr);
             if (!(m >= kFallbackMax)) bad = true;
-            const float m2 = team_corr<T, false>(Bn, k * D + 1, mu + k * Q, Q, B, 0, 0, Lr);
+            const float m2 = team_corr<T, false, CorrBlock<Q>::BR>(Bn, k * D + 1, mu + k * Q, Q, B, 0, 0, Lr);
             if (!(m2 > 0.0f)) bad = true;
             float* t = B;
             B = Bn;
