@@ -280,20 +280,19 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
                                                                               NB, k, p, lp);
             }
         };
-        // syndromes and the per-frame stop after iteration t; returns the frames still active
-        auto phase_stop = [&](int t) {
-            for (int w = threadIdx.x; w < gc * K * P; w += blockDim.x) {
-                const int gi = w / (K * P), rem = w % (K * P), k = rem / P, j = rem % P;
-                if (!s_active[gi]) continue;
-                const uint8_t* hk = s_hat + gi * hs + k * NB * 32;
-                int sy = 0;
+        // syndrome of check j of user k in frame gi (eq. app_ldpc_check_eq)
+        auto unit_syndrome = [&](int gi, int k, int j) {
+            const uint8_t* hk = s_hat + gi * hs + k * NB * 32;
+            int sy = 0;
 #pragma unroll
-                for (int d = 0; d < kDC; ++d) {
-                    const int e = 4 * j + d;
-                    sy ^= s_mul[s_coef[e] * Q + hk[s_slot[k * E + e] >> 1]];
-                }
-                if (sy) s_unsat[gi * K + k] = 1;
+            for (int d = 0; d < kDC; ++d) {
+                const int e = 4 * j + d;
+                sy ^= s_mul[s_coef[e] * Q + hk[s_slot[k * E + e] >> 1]];
             }
+            if (sy) s_unsat[gi * K + k] = 1;
+        };
+        // per-frame stop after iteration t (syndromes already recorded); returns the frames still active
+        auto phase_finish = [&](int t) {
             if (threadIdx.x == 0) s_nactive = 0;
             __syncthreads();
             for (int gi = threadIdx.x; gi < gc; gi += blockDim.x) {
@@ -311,6 +310,14 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
             }
             __syncthreads();
             return s_nactive;
+        };
+        auto phase_stop = [&](int t) {
+            for (int w = threadIdx.x; w < gc * K * P; w += blockDim.x) {
+                const int gi = w / (K * P), rem = w % (K * P);
+                if (!s_active[gi]) continue;
+                unit_syndrome(gi, rem / P, rem % P);
+            }
+            return phase_finish(t);
         };
         bool all_stopped = false;
         for (int t = 1; t <= T_it; ++t) {
@@ -334,17 +341,20 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
                 }
             }
             __syncthreads();
-            if (fold && t > 1 && phase_stop(t - 1) == 0) {
-                all_stopped = true;
-                break;
-            }
-            // (B) check nodes, in the bank-spreading order of chk_order
+            // (B) check nodes, in the bank-spreading order of chk_order; folded, each
+            // unit also tests its check against the decisions of iteration t - 1
+            const bool syn = fold && t > 1;
             for (int unit = threadIdx.x; unit < gc * K * P; unit += blockDim.x) {
                 const int gi = unit / (K * P), rem = s_order[unit % (K * P)], k = rem / P, j = rem % P;
                 if (!s_active[gi]) continue;
+                if (syn) unit_syndrome(gi, k, j);
                 check_thread_pos<Q>(s_msg + gi * fs, NB, k, j, s_slot + k * E, s_coef, s_div);
             }
             __syncthreads();
+            if (syn && phase_finish(t - 1) == 0) {
+                all_stopped = true;
+                break;
+            }
             if (!fold) {
                 // (C) posterior and decisions (position order), (D) syndromes, (E) per-frame stop
                 phase_decide();
