@@ -25,7 +25,10 @@
 namespace jbp {
 
 constexpr float kRelFloor = 1e-12f;
-constexpr float kFallbackMax = 1e-30f;   // linear channel output below this: redo in log space
+// linear channel output whose maximum is below this: redo in log space.  At
+// 1e-24 every entry down to the 1e-12 floor (relative to the maximum) is still a
+// normal FP32 number, so no entry the floor keeps is lost to underflow.
+constexpr float kFallbackMax = 1e-24f;
 constexpr int kMaxDv = 8;
 constexpr int kMaxK = 16;
 constexpr int kDC = 4;                   // check degree of the kernels

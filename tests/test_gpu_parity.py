@@ -529,3 +529,38 @@ def test_serving_destroy_with_frames_in_flight(env):
         dec_a.close()
         dec_b.close()
         ctx.close()
+
+
+@pytest.mark.parametrize("T,snr", [(1, 20.0), (2, 20.0), (4, 16.0), (12, 16.0)])
+def test_fused_iteration_boundaries_and_early_stop(env, T, snr):
+    """The fused form folds each iteration's decisions into the next channel
+    phase and its syndromes into the next check phase; at T = 1 and T = 2 and
+    with frames stopping at different iterations, iteration counts and syndrome
+    flags equal the oracle's (and the step form's) for every frame, and the
+    decisions of every frame the oracle decodes to codewords are bit-exact
+    where the FP64 margin exceeds 1e-6.  Frames that never converge at this SNR
+    are compared on iterations and flags only: their BP trajectory is chaotic,
+    and the FP32 transform's rounding grows by a factor of about 2-10 per
+    iteration until, after a dozen iterations, a final decision can flip."""
+    jbp, O, torch = env
+    code = I.make_code(64, 4)
+    fr = I.make_frames(code, 2, snr, 200, seed=4252)
+    ctx, dec = _decoder(jbp, code, 2, fr["sigma2"], fr["perm"], iters=T, early_stop=True)
+    try:
+        fused = dec.decode(fr["y"], form=jbp.FORM_FUSED)
+        step = dec.decode(fr["y"], form=jbp.FORM_STEP)
+    finally:
+        dec.close()
+        ctx.close()
+    ref = O.decode(code, 2, fr["sigma2"], fr["perm"], fr["y"], T, early_stop=True, want_margin=True)
+    conv = ref["ok"].all(axis=1)
+    for got in (fused, step):
+        assert (got["iters"] == ref["iters"]).all()
+        assert (got["ok"] == ref["ok"]).all()
+        sure = ref["margin"] > 1e-6
+        if T > 4:
+            sure &= conv[:, None, None]
+        assert int(((got["hat"] != ref["hat"]) & sure).sum()) == 0
+    print("T=%d: iterations run %s, converged %d" % (T, np.bincount(ref["iters"]).tolist(), int(conv.sum())))
+    if T == 12:
+        assert conv.sum() > 10 and len(set(ref["iters"].tolist())) > 4   # frames stop at many iterations
