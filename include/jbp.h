@@ -207,7 +207,7 @@ const char *jbp_last_error(void);
  * Layouts: msg [F*K*E*q] holds, per edge, the check-to-variable message
  * (before jbp_step_channel, after jbp_step_check) or the variable-to-check
  * message (after jbp_step_channel), as probabilities scaled to max 1 (the
- * uniform start is all ones); ch2v [F*K*n*q] likewise; post [F*K*n*q]
+ * uniform start is all ones), 16-byte aligned; ch2v [F*K*n*q] likewise; post [F*K*n*q]
  * max-normalised log-posterior; hat [F*K*n]; ok [F*K]; E = P*dc. ---- */
 
 /* (a) channel node for every channel use of F frames: reads the c2v messages in
@@ -216,7 +216,9 @@ const char *jbp_last_error(void);
 int jbp_step_channel(jbp_h *h, int32_t F, const float *y, float *msg, float *ch2v, void *stream);
 
 /* (b) check node for every check: replaces the v2c messages in msg by the new
- * c2v messages (eq. app_ldpc_c2v in the WHT domain); precision: jbp_precision. */
+ * c2v messages (eq. app_ldpc_c2v in the WHT domain); precision: jbp_precision.
+ * msg must be 16-byte aligned (JBP_EINVAL otherwise): the kernel moves tiles of
+ * it with bulk copies. */
 int jbp_step_check(jbp_h *h, int32_t F, float *msg, int32_t precision, void *stream);
 
 /* (c) variable node: post = ch2v + sum of the variable's c2v (max-normalised;

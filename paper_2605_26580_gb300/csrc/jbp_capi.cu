@@ -974,6 +974,8 @@ static cudaStream_t pick_stream(jbp_h* h, void* s) { return s ? (cudaStream_t)s 
 extern "C" int jbp_step_channel(jbp_h* h, int32_t F, const float* y, float* msg, float* ch2v, void* stream)
 {
     if (!h || F < 0 || (F > 0 && (!y || !msg || !ch2v))) return fail(JBP_EINVAL, "jbp_step_channel: bad argument");
+    if (reinterpret_cast<uintptr_t>(msg) % 16 || reinterpret_cast<uintptr_t>(ch2v) % 16)
+        return fail(JBP_EINVAL, "jbp_step_channel: msg and ch2v must be 16-byte aligned");
     JBP_CU(cudaSetDevice(h->ctx->device), "cudaSetDevice");
     JBP_CU(launch_channel(h->graph(), h->ctx->di, F, y, msg, ch2v, nullptr, pick_stream(h, stream)), "channel kernel");
     return JBP_OK;
@@ -983,6 +985,9 @@ extern "C" int jbp_step_check(jbp_h* h, int32_t F, float* msg, int32_t precision
 {
     if (!h || F < 0 || (F > 0 && !msg)) return fail(JBP_EINVAL, "jbp_step_check: bad argument");
     if (precision < 0 || precision > 3) return fail(JBP_EINVAL, "bad precision %d", precision);
+    // the check kernel moves tiles of msg with bulk copies, which need 16-byte alignment
+    if (reinterpret_cast<uintptr_t>(msg) % 16)
+        return fail(JBP_EINVAL, "jbp_step_check: msg must be 16-byte aligned");
     JBP_CU(cudaSetDevice(h->ctx->device), "cudaSetDevice");
     JBP_CU(launch_check(h->graph(), h->ctx->di, F, msg, nullptr, precision, pick_stream(h, stream)), "check kernel");
     return JBP_OK;
@@ -992,6 +997,8 @@ extern "C" int jbp_step_var(jbp_h* h, int32_t F, const float* ch2v, const float*
                             void* stream)
 {
     if (!h || F < 0 || (F > 0 && (!ch2v || !msg || !hat))) return fail(JBP_EINVAL, "jbp_step_var: bad argument");
+    if (reinterpret_cast<uintptr_t>(msg) % 16 || reinterpret_cast<uintptr_t>(ch2v) % 16)
+        return fail(JBP_EINVAL, "jbp_step_var: msg and ch2v must be 16-byte aligned");
     JBP_CU(cudaSetDevice(h->ctx->device), "cudaSetDevice");
     JBP_CU(launch_var(h->graph(), h->ctx->di, F, ch2v, msg, post, hat, nullptr, pick_stream(h, stream)), "var kernel");
     return JBP_OK;

@@ -564,3 +564,28 @@ def test_fused_iteration_boundaries_and_early_stop(env, T, snr):
     print("T=%d: iterations run %s, converged %d" % (T, np.bincount(ref["iters"]).tolist(), int(conv.sum())))
     if T == 12:
         assert conv.sum() > 10 and len(set(ref["iters"].tolist())) > 4   # frames stop at many iterations
+
+
+def test_step_entry_points_refuse_misaligned_buffers(env):
+    """The step kernels move messages with 16-byte loads and bulk copies; a
+    misaligned device pointer is refused on the host with JBP_EINVAL."""
+    jbp, O, torch = env
+    code = I.make_code(64, 16)
+    fr = I.make_frames(code, 2, 10.0, 2, seed=3)
+    ctx, dec = _decoder(jbp, code, 2, fr["sigma2"], fr["perm"])
+    try:
+        dev = torch.device("cuda:0")
+        E = code["P"] * 4
+        big = torch.ones(2 * 2 * E * 16 + 1, dtype=torch.float32, device=dev)
+        msg = big[1:].view(2, 2, E, 16)            # 4 bytes off a 16-byte boundary
+        ch2v = torch.empty((2, 2, 64, 16), dtype=torch.float32, device=dev)
+        y = torch.from_numpy(fr["y"]).to(dev)
+        for call in (lambda: dec.step_check(msg), lambda: dec.step_channel(y, msg, ch2v),
+                     lambda: dec.step_var(ch2v, msg, None, torch.empty((2, 2, 64), dtype=torch.uint8, device=dev))):
+            with pytest.raises(jbp.JBPError) as ei:
+                call()
+            assert ei.value.code == jbp.EINVAL
+        torch.cuda.synchronize()
+    finally:
+        dec.close()
+        ctx.close()
