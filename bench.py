@@ -237,7 +237,10 @@ def main() -> None:
                          "for the other workloads")
     ap.add_argument("--frac", type=float, default=1.0, help="fraction of the uneven/serving workload (tests)")
     ap.add_argument("--launch", default="auto", help="fused launch shape: auto (autotune), default, or THREADS,FPC")
-    ap.add_argument("--variants", default="0,3,1,2", help="precision workload: check-node variants to run")
+    ap.add_argument("--variants", default="0,d0,3,1,2",
+                    help="precision workload: check-node variants to run (dP: with the DFT channel node)")
+    ap.add_argument("--channel-legs", type=int, default=1, help="precision workload: time the channel node alone")
+    ap.add_argument("--channel-frames", type=int, default=4096, help="precision workload: frames of that leg")
     ap.add_argument("--oracle-sample", type=int, default=16, help="precision workload: oracle frames")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -536,20 +539,25 @@ def wl_precision(args):
     variants = {}
     names = {0: "fp32_butterfly", 3: "bf16x3_tensor", 1: "bf16x2_tensor", 2: "bf16_tensor"}
     fp32_hat = None
-    for prec in [int(v) for v in args.variants.split(",")]:
-        ctx = jbp.Context(iters=50, early_stop=True, precision=prec)
+    for spec in args.variants.split(","):
+        # "P": check-node precision P with the trellis channel node; "dP": the same with
+        # the tensor-core (DFT) channel node
+        dft = spec.startswith("d")
+        prec = int(spec[1:] if dft else spec)
+        ctx = jbp.Context(iters=50, early_stop=True, precision=prec,
+                          channel_node=jbp.CHAN_DFT if dft else jbp.CHAN_TRELLIS)
         dec = jbp.Decoder(ctx, code, K, fr["sigma2"], fr["perm"])
         dec.decode_device(y, hat, it, ok, form=jbp.FORM_STEP, stream=st)
         sec = _timed(torch, st, lambda: dec.decode_device(y, hat, it, ok, form=jbp.FORM_STEP, stream=st), 1)
         g = hat.cpu().numpy()
-        if prec == 0:
+        if prec == 0 and not dft:
             fp32_hat = g
         m = torch.from_numpy(v2c).to(dev)
         dec.step_check(m, precision=prec, stream=st)
         st.synchronize()
         c2v_g = np.log(m.cpu().numpy().astype(np.float64))
         rho = np.exp(c2v_o)
-        variants[names[prec]] = {
+        variants[("dft_channel+" if dft else "") + names[prec]] = {
             "frames_per_s": F / sec, "ms_per_batch": sec * 1e3, "mean_iters": float(it.float().mean().item()),
             "ser": float((g != fr["c"]).mean()),
             "ser_delta_vs_fp32": (float((g != fr["c"]).mean() - (fp32_hat != fr["c"]).mean())
@@ -564,12 +572,59 @@ def wl_precision(args):
             "tc_timeouts": dec.tc_timeouts()}
         dec.close()
         ctx.close()
+    chan = channel_legs(jbp, torch, dev, O, I, code, K, q, n, fr, st, args) if args.channel_legs else None
     return {"metric": METRIC, "value": max(v["frames_per_s"] for v in variants.values()), "unit": "frames/s",
             "config": {"workload": "K=4 users, GF(64) regular (2,4) LDPC, n=512, SNR 14 dB, 50 iterations with "
                                    "syndrome early stop, %d frames, step form (messages in HBM)" % F},
-            "dtype": "f32 messages; check transform per variant", "variants": variants,
+            "dtype": "f32 messages; check transform per variant", "variants": variants, "channel_node": chan,
             "cpu_baseline": ({"value": S / t_or, "unit": "frames/s", "cores": cores, "kind": "oracle",
                               "sample": "first %d frames, 50 iterations" % S} if S > 0 else None)}
+
+
+def channel_legs(jbp, torch, dev, O, I, code, K, q, n, fr, st, args):
+    """The channel node alone (one step over Fs frames, messages resident in HBM):
+    FP32 trellis vs the tensor-core DFT form, time per channel use, bytes moved,
+    the share of channel uses the DFT form hands to the trellis, and its error
+    against the FP64 oracle on a 2-frame sample."""
+    Fs = min(int(fr["y"].shape[0]), args.channel_frames)
+    E = code["P"] * 4
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(11)
+    x = torch.randn((Fs, K, E, q), generator=gen, device=dev) * 3.0
+    msg0 = torch.exp(x - x.amax(-1, keepdim=True)).clamp_min_(1e-12)
+    del x
+    y = torch.from_numpy(fr["y"][:Fs]).to(dev)
+    ch2v = torch.empty((Fs, K, n, q), dtype=torch.float32, device=dev)
+    uses = Fs * n
+    algo_bytes = uses * (5 * K * q * 4 + 4)    # c2v of both edges in, ch2v out, v2c of both edges out, y in
+    out = {"frames": Fs, "channel_uses": uses, "algorithmic_bytes": algo_bytes}
+    for name, node in (("trellis", jbp.CHAN_TRELLIS), ("dft", jbp.CHAN_DFT)):
+        ctx = jbp.Context(iters=1, early_stop=False, channel_node=node)
+        dec = jbp.Decoder(ctx, code, K, fr["sigma2"], fr["perm"])
+        msg = msg0.clone()
+        for _ in range(2):
+            dec.step_channel(y, msg, ch2v, stream=st)
+        st.synchronize()
+        f0 = dec.log_fallbacks()
+        sec = _timed(torch, st, lambda: dec.step_channel(y, msg, ch2v, stream=st), 3)
+        f1 = dec.log_fallbacks()
+        out[name] = {"ms": sec * 1e3, "ns_per_channel_use": sec / uses * 1e9,
+                     "gbs": algo_bytes / sec / 1e9, "rows_to_trellis_per_step": (f1 - f0) / 3,
+                     "tc_timeouts": dec.tc_timeouts()}
+        if node == jbp.CHAN_DFT:
+            rng = np.random.default_rng(5)
+            c2v_lin = np.exp(I.random_log_messages(rng, (2, K, E), q, spread=3.0)).astype(np.float32)
+            m = torch.from_numpy(c2v_lin).to(dev)
+            chs = torch.empty((2, K, n, q), dtype=torch.float32, device=dev)
+            dec.step_channel(y[:2], m, chs, stream=st)
+            st.synchronize()
+            ch_o = np.exp(O.step_channel(code, K, fr["sigma2"], fr["perm"], fr["y"][:2],
+                                         np.log(c2v_lin.astype(np.float64))))
+            out[name]["max_linear_err_vs_oracle_2_frames"] = float(np.abs(chs.cpu().numpy() - ch_o).max())
+        dec.close()
+        ctx.close()
+    out["speedup_dft_vs_trellis"] = out["trellis"]["ms"] / out["dft"]["ms"]
+    return out
 
 
 def _uneven_classes(F, seed):

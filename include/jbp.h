@@ -66,6 +66,19 @@ typedef enum {
  * (hi/lo), BF16 uses one. */
 typedef enum { JBP_PREC_FP32 = 0, JBP_PREC_BF16X2 = 1, JBP_PREC_BF16 = 2, JBP_PREC_BF16X3 = 3 } jbp_precision;
 
+/* Channel-node algorithm (kernel (a)).  TRELLIS: the exact FP32 sum-product
+ * over the integer symbol sums (prefix convolutions and scored suffixes; the
+ * reference numerics).  DFT: the same extrinsic messages as a correlation in
+ * the frequency domain of the sum alphabet (DFT length L >= K(q-1)+1), with the
+ * forward and inverse transforms issued as matrix products on the tensor cores
+ * (FP16 hi/lo operand terms, FP32 accumulation).  Its error is absolute, a
+ * small fraction of each message's maximum (about 1e-5; the tests bound it),
+ * rather than relative per entry, so entries far below the maximum are not
+ * resolved.  It runs in the step form where K >= 2, q >= 16 and K q <= 256;
+ * other handles of the context keep the trellis (jbp_query_channel tells
+ * which). */
+typedef enum { JBP_CHAN_TRELLIS = 0, JBP_CHAN_DFT = 1 } jbp_channel_node;
+
 /* Launch form of jbp_decode.  AUTO picks FUSED when one frame's message state
  * fits in one SM's shared memory, else STEP.  FUSED: one persistent kernel runs
  * every iteration of a group of frames with all messages in shared memory.
@@ -103,7 +116,8 @@ typedef struct {
  * variants run in the step form; AUTO then picks STEP).  mem_budget_bytes:
  * cap on the device memory the context allocates (0 = 90% of free memory at
  * creation).  device: CUDA device ordinal.  block_iters: iterations per
- * serving block (0 = 5). */
+ * serving block (0 = 5).  channel_node: jbp_channel_node (DFT runs in the step
+ * form; AUTO then picks STEP for the handles that use it).  reserved: zero. */
 typedef struct {
     int32_t iters;
     int32_t early_stop;
@@ -111,7 +125,8 @@ typedef struct {
     int32_t device;
     int64_t mem_budget_bytes;
     int32_t block_iters;
-    int32_t reserved[7];
+    int32_t channel_node;
+    int32_t reserved[6];
 } jbp_options;
 
 /* One decode call.  F >= 0 frames.  y [F*n] FP32 channel outputs.  Outputs:
@@ -262,6 +277,11 @@ int jbp_stats(jbp_h *h, uint64_t *log_fallbacks, int32_t *tc_timeouts);
 /* Shape information of a handle (host pointers, any may be NULL): edges E,
  * per-frame device state bytes, and whether one frame fits the fused form. */
 int jbp_query(jbp_h *h, int32_t *E, int64_t *state_bytes_per_frame, int32_t *fused_ok);
+
+/* The channel node this handle runs (jbp_channel_node): DFT where the context
+ * asked for it and the handle's (K, q) supports it, else TRELLIS.  No paper
+ * counterpart: an implementation query. */
+int jbp_query_channel(jbp_h *h, int32_t *channel_node);
 
 /* ---- the paper's own classical path on the evidence interface S ----
  *

@@ -211,6 +211,8 @@ struct jbp_h {
     int* d_tc_error = nullptr;
     uint16_t* d_slot = nullptr;
     uint16_t* d_chk_order = nullptr;
+    unsigned char* d_dft_tab = nullptr;   // tables of the tensor-core channel node (null: trellis)
+    size_t dft_bytes = 0;
     int64_t table_bytes = 0;
     Workspace ws;
     std::mutex ws_mu;
@@ -233,6 +235,7 @@ struct jbp_h {
         g.tc_error = d_tc_error;
         g.sigma2_f = nullptr;
         g.chk_order = d_chk_order;
+        g.dft_tab = d_dft_tab;
         return g;
     }
 };
@@ -367,10 +370,13 @@ static int decode_device(jbp_h* h, Workspace& w, int form, int F, const float* y
     g.sigma2_f = sigma2_f;
     // the fused kernel runs the FP32 butterfly check node; the tensor-core
     // precision variants run in the step form
-    if (form == JBP_FORM_AUTO) form = (h->fused_ok && ctx->opt.precision == JBP_PREC_FP32) ? JBP_FORM_FUSED : JBP_FORM_STEP;
+    if (form == JBP_FORM_AUTO)
+        form = (h->fused_ok && ctx->opt.precision == JBP_PREC_FP32 && !h->d_dft_tab) ? JBP_FORM_FUSED : JBP_FORM_STEP;
     if (form == JBP_FORM_FUSED && ctx->opt.precision != JBP_PREC_FP32)
         return fail(JBP_EINVAL, "the fused form runs the FP32 check node; use the step form for precision %d",
                     ctx->opt.precision);
+    if (form == JBP_FORM_FUSED && h->d_dft_tab)
+        return fail(JBP_EINVAL, "the fused form runs the trellis channel node; use the step form for the DFT node");
     if (form == JBP_FORM_FUSED) {
         if (!h->fused_ok) return fail(JBP_EINVAL, "one frame does not fit the fused form (shared memory)");
         FusedPlan plan;
@@ -411,6 +417,8 @@ extern "C" int jbp_context_create(const jbp_options* opt, jbp_ctx** out)
     if (!opt || !out) return fail(JBP_EINVAL, "jbp_context_create: NULL argument");
     if (opt->iters < 1) return fail(JBP_EINVAL, "iters must be >= 1 (got %d)", opt->iters);
     if (opt->precision < 0 || opt->precision > 3) return fail(JBP_EINVAL, "bad precision %d", opt->precision);
+    if (opt->channel_node != JBP_CHAN_TRELLIS && opt->channel_node != JBP_CHAN_DFT)
+        return fail(JBP_EINVAL, "bad channel_node %d", opt->channel_node);
     if (opt->mem_budget_bytes < 0) return fail(JBP_EINVAL, "negative memory budget");
     int ndev = 0;
     JBP_CU(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
@@ -601,6 +609,14 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
                             4ll * K * (E + n) * q <= (int64_t)ctx->di.smem_optin;
     std::vector<uint16_t> chk_order;
     if (want_order) chk_order = check_order(K, P, E, slot);
+    const DftShape dsh = dft_shape(K, q);
+    const bool want_dft = ctx->opt.channel_node == JBP_CHAN_DFT && dv == 2 && dc == kDC && dsh.ok &&
+                          dsh.smem <= ctx->di.smem_optin;
+    std::vector<unsigned char> dft_tab;
+    if (want_dft) {
+        dft_tab.resize(dft_table_bytes(K, q));
+        dft_build_table(K, q, dft_tab.data());
+    }
     std::vector<uint8_t> gmul((size_t)q * q), gdiv((size_t)q * q);
     std::vector<int> inv(q, 0);
     for (int a = 1; a < q; ++a)
@@ -632,10 +648,12 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
         (rc = dev_alloc(ctx, &h->d_pos_of, (size_t)K * n, &h->table_bytes)) ||
         (rc = dev_alloc(ctx, &h->d_tc_error, (size_t)1, &h->table_bytes)) ||
         (want_slot && (rc = dev_alloc(ctx, &h->d_slot, (size_t)K * E, &h->table_bytes))) ||
-        (want_order && (rc = dev_alloc(ctx, &h->d_chk_order, (size_t)K * P, &h->table_bytes)))) {
+        (want_order && (rc = dev_alloc(ctx, &h->d_chk_order, (size_t)K * P, &h->table_bytes))) ||
+        (want_dft && (rc = dev_alloc(ctx, &h->d_dft_tab, dft_table_bytes(K, q), &h->table_bytes)))) {
         jbp_destroy(h);
         return rc;
     }
+    if (want_dft) h->dft_bytes = dft_table_bytes(K, q);
     cudaError_t e;
     if ((e = cudaMemcpy(h->d_chk_var, code->chk_var, sizeof(int32_t) * E, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(h->d_chk_coef, code->chk_coef, (size_t)E, cudaMemcpyHostToDevice)) ||
@@ -649,7 +667,8 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
         (want_slot &&
          (e = cudaMemcpy(h->d_slot, slot.data(), sizeof(uint16_t) * slot.size(), cudaMemcpyHostToDevice))) ||
         (want_order && (e = cudaMemcpy(h->d_chk_order, chk_order.data(), sizeof(uint16_t) * chk_order.size(),
-                                       cudaMemcpyHostToDevice)))) {
+                                       cudaMemcpyHostToDevice))) ||
+        (want_dft && (e = cudaMemcpy(h->d_dft_tab, dft_tab.data(), dft_tab.size(), cudaMemcpyHostToDevice)))) {
         jbp_destroy(h);
         return cuda_fail(e, "jbp_create: copy tables");
     }
@@ -713,6 +732,7 @@ extern "C" int jbp_destroy(jbp_h* h)
     dev_free(ctx, h->d_gf_div, (size_t)h->Q * h->Q);
     dev_free(ctx, h->d_fallbacks, sizeof(unsigned long long));
     dev_free(ctx, h->d_pos_of, sizeof(int32_t) * (size_t)h->K * h->n);
+    dev_free(ctx, h->d_dft_tab, h->dft_bytes);
     dev_free(ctx, h->d_tc_error, sizeof(int));
     if (h->d_slot) dev_free(ctx, h->d_slot, sizeof(uint16_t) * (size_t)h->K * h->E);
     if (h->d_chk_order) dev_free(ctx, h->d_chk_order, sizeof(uint16_t) * (size_t)h->K * h->P);
@@ -726,6 +746,13 @@ extern "C" int jbp_query(jbp_h* h, int32_t* E, int64_t* state_bytes_per_frame, i
     if (E) *E = h->E;
     if (state_bytes_per_frame) *state_bytes_per_frame = state_bytes(h->graph());
     if (fused) *fused = h->fused_ok ? 1 : 0;
+    return JBP_OK;
+}
+
+extern "C" int jbp_query_channel(jbp_h* h, int32_t* node)
+{
+    if (!h || !node) return fail(JBP_EINVAL, "jbp_query_channel: NULL argument");
+    *node = h->d_dft_tab ? JBP_CHAN_DFT : JBP_CHAN_TRELLIS;
     return JBP_OK;
 }
 
@@ -936,7 +963,7 @@ extern "C" int jbp_decode_many(jbp_ctx* ctx, int32_t nparts, jbp_h* const* handl
         for (int i = 0; i < nparts; ++i) {
             jbp_h* h = handles[i];
             const jbp_batch& b = batches[i];
-            if (!h->tuned && h->fused_ok && ctx->opt.precision == JBP_PREC_FP32 &&
+            if (!h->tuned && h->fused_ok && ctx->opt.precision == JBP_PREC_FP32 && !h->d_dft_tab &&
                 (b.form == JBP_FORM_AUTO || b.form == JBP_FORM_FUSED)) {
                 int rc = autotune(h, b.F, b.y, b.hat, b.iters, b.ok, b.sigma2, main);
                 if (rc) return rc;

@@ -1,0 +1,613 @@
+// jbp_channel_dft.cu -- channel node (kernel (a)) as discrete Fourier transforms
+// over the integer symbol-sum alphabet, with the transforms issued as matrix
+// products on the 5th-generation tensor cores (tcgen05).
+//
+// For one channel use with user messages mu_0..mu_{K-1} (length q) and the
+// Gaussian score G(u) of the sum value u = 0..K(q-1), the extrinsic message to
+// user k is the correlation
+//     ch2v_k(a) ~ sum_s E_k(s) G(s + a),   E_k = the integer convolution of mu_j, j != k.
+// With a DFT length L >= K(q-1)+1 the circular correlation equals the linear one
+// for a = 0..q-1, and with hats for DFTs (e^{-2 pi i f x / L}):
+//     X_k(f) = G^(f) conj(prod_{j != k} mu^_j(f)),   ch2v_k(a) ~ sum_f X_k(f) e^{+2 pi i f a / L}.
+// Real inputs make the spectra Hermitian, so frequencies 0..L/2 carry everything:
+// L real spectral columns, pairs (Re, Im) of f = 1..L/2-1 and the pair (DC, Nyquist).
+//
+// A CTA of 256 threads takes tiles of 128 channel uses (rows; thread t and
+// t + 128 share row t % 128 and split its work).  Per tile:
+//   1. each row's mu_j = c2v_e0 * c2v_e1 (its variable's two edges) and a window of
+//      W values of G around the most likely sum are staged in shared memory as FP16
+//      operands (one term each; lane groups move the message vectors);
+//   2. per chunk of Nc spectral columns: one thread issues the forward DFT products
+//      (every mu_j, and the G window, against the shared forward matrix) into tensor
+//      memory; every thread reads its row's spectra, scales each by its DC term,
+//      rotates the window spectrum to its offset, forms the K leave-one-out
+//      products X_k by prefix and suffix products (no division) and stages them
+//      (hi + lo) as the operand of the inverse DFT, which accumulates over the
+//      chunks in tensor memory (K q columns);
+//   3. every thread reads the accumulated messages of its users, normalises them
+//      to max 1 with the floor, and writes ch2v and the two v2c messages of each
+//      variable (the same outputs as the trellis kernels).  A channel use whose
+//      peak is too small for the transform to resolve (the other users' beliefs
+//      make the observed sum nearly impossible) is left to the FP32 trellis,
+//      which a second launch runs on just those channel uses.
+// Numerics: products of FP16 terms are exact and accumulate in FP32.  mu and the
+// G window are single FP16 terms: a relative rounding of at most 2^-12 per value,
+// which perturbs each output by at most (K - 1 + 1) 2^-12 relative.  The DFT
+// matrices and the X_k are hi + lo terms (about 2^-22): the inverse transform
+// subtracts terms of the size of the whole spectrum, so that part of the error is
+// absolute, a fraction of each message's maximum, instead of relative per entry
+// as in the FP32 trellis.
+// Every mbarrier wait is bounded; on expiry the kernel records an error in
+// g.tc_error, frees its tensor memory and returns.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include <cuda_fp16.h>
+
+#include "jbp_internal.h"
+#include "jbp_tc.cuh"
+
+namespace jbp {
+namespace {
+
+__device__ __forceinline__ uint32_t pack_h2(__half a, __half b)
+{
+    return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+
+// 8 values as one 16-byte core-matrix row of FP16 hi terms and one of lo terms
+__device__ __forceinline__ void split8(const float (&v)[8], uint4& hi, uint4& lo)
+{
+    __half h[8], l[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        h[i] = __float2half_rn(v[i]);
+        l[i] = __float2half_rn(v[i] - __half2float(h[i]));
+    }
+    hi = make_uint4(pack_h2(h[0], h[1]), pack_h2(h[2], h[3]), pack_h2(h[4], h[5]), pack_h2(h[6], h[7]));
+    lo = make_uint4(pack_h2(l[0], l[1]), pack_h2(l[2], l[3]), pack_h2(l[4], l[5]), pack_h2(l[6], l[7]));
+}
+
+__device__ __forceinline__ uint4 pack8(const float (&v)[8])
+{
+    return make_uint4(pack_h2(__float2half_rn(v[0]), __float2half_rn(v[1])),
+                      pack_h2(__float2half_rn(v[2]), __float2half_rn(v[3])),
+                      pack_h2(__float2half_rn(v[4]), __float2half_rn(v[5])),
+                      pack_h2(__float2half_rn(v[6]), __float2half_rn(v[7])));
+}
+
+struct Cx {
+    float r, i;
+};
+__device__ __forceinline__ Cx cmul(Cx a, Cx b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+// a * conj(b)
+__device__ __forceinline__ Cx cmulc(Cx a, Cx b) { return {a.r * b.r + a.i * b.i, a.i * b.r - a.r * b.i}; }
+
+// X_k = g conj(prod_{j != k} m_j) for every k, by prefix and suffix products
+template <int K>
+__device__ __forceinline__ void leave_one_out(const Cx (&m)[K], Cx g, Cx (&X)[K])
+{
+    Cx pre[K];
+    pre[0] = {1.0f, 0.0f};
+#pragma unroll
+    for (int k = 1; k < K; ++k) pre[k] = k == 1 ? m[0] : cmul(pre[k - 1], m[k - 1]);
+    Cx suf = {1.0f, 0.0f};
+#pragma unroll
+    for (int k = K - 1; k >= 0; --k) {
+        const Cx e = k == K - 1 ? pre[k] : k == 0 ? suf : cmul(pre[k], suf);
+        X[k] = cmulc(g, e);
+        if (k > 0) suf = k == K - 1 ? m[k] : cmul(suf, m[k]);
+    }
+}
+
+// Smallest peak mass (fraction of the normalised spectra's total) that the
+// transform resolves: its absolute error, of order 2^-22 per spectral term,
+// stays below about 1e-3 of such a peak.
+constexpr float kMinPeak = 1.0f / 4096.0f;
+
+template <int Q, int K>
+struct ShapeOf {
+    static constexpr DftShape v = dft_shape(K, Q);
+};
+
+// Forward products of one chunk (one thread): spectrum of mu_j into columns
+// SP + j Nc, of the G window into SP + K Nc.  Terms A*B_hi + A*B_lo.
+template <int Q, int K, class Sh>
+__device__ __forceinline__ void issue_forward(uint32_t tmem, uint32_t sA1, uint32_t sAG, uint32_t sB1)
+{
+    constexpr DftShape S = Sh::v;
+    constexpr int NC = S.Nc, KB = S.KB, W = S.W, SP = K * Q;
+    constexpr uint32_t kA1 = kDftRows * Q * 2, kB1 = NC * KB * 2;
+    constexpr uint32_t id = tc::idesc_f16(kDftRows, NC, false);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const uint32_t d = tmem + SP + j * NC;
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int ks = 0; ks < Q / 16; ++ks)
+                tc::mma_f16(d, tc::step_desc(sA1 + j * kA1, ks, Q), tc::step_desc(sB1 + p * kB1, ks, KB), id,
+                            p | ks);
+    }
+    const uint32_t d = tmem + SP + K * NC;
+    int acc = 0;
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int ks = 0; ks < W / 16; ++ks) {
+            tc::mma_f16(d, tc::step_desc(sAG, ks, W), tc::step_desc(sB1 + p * kB1, ks, KB), id, acc);
+            acc = 1;
+        }
+}
+
+// Inverse products of chunk c (one thread): X_k against the inverse rows,
+// accumulated into columns k q.
+template <int Q, int K, class Sh>
+__device__ __forceinline__ void issue_inverse(uint32_t tmem, uint32_t sA3, uint32_t sB3, int c)
+{
+    constexpr int NC = Sh::v.Nc;
+    constexpr uint32_t kA3 = kDftRows * NC * 2, kB3 = Q * NC * 2;
+    constexpr uint32_t id = tc::idesc_f16(kDftRows, Q, false);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        int acc = c > 0;
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            const uint32_t a = sA3 + (2 * k + (p == 1)) * kA3, b = sB3 + (p == 2) * kB3;
+#pragma unroll
+            for (int ks = 0; ks < NC / 16; ++ks) {
+                tc::mma_f16(tmem + k * Q, tc::step_desc(a, ks, NC), tc::step_desc(b, ks, NC), id, acc);
+                acc = 1;
+            }
+        }
+    }
+}
+
+// lanes of one group that moves one (row, user) message vector: a float4 each
+template <int Q>
+struct Group {
+    static constexpr int GL = Q / 4;          // lanes per vector
+    static constexpr int PPW = 32 / GL;       // vectors per warp instruction
+};
+
+template <int GL>
+__device__ __forceinline__ float group_max(float x)
+{
+#pragma unroll
+    for (int o = GL / 2; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+__device__ __forceinline__ float max4(float4 v) { return fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)); }
+__device__ __forceinline__ float4 mul4(float4 a, float4 b) { return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w); }
+__device__ __forceinline__ float4 scale4(float4 a, float s) { return make_float4(a.x * s, a.y * s, a.z * s, a.w * s); }
+
+template <int Q, int K>
+__global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, const float* __restrict__ y,
+                                                               float* msg, float* ch2v,
+                                                               const uint8_t* __restrict__ active)
+{
+    using Sh = ShapeOf<Q, K>;
+    constexpr DftShape S = Sh::v;
+    static_assert(S.ok, "no tensor-core channel shape for this (K, q)");
+    constexpr int L = S.L, W = S.W, NC = S.Nc, CH = S.chunks, U = S.U, R = kDftRows, SP = K * Q;
+    constexpr int NW = kDftThreads / 32, GL = Group<Q>::GL, PPW = Group<Q>::PPW;
+    constexpr uint32_t kA1 = R * Q * 2, kAG = R * W * 2, kB1 = NC * S.KB * 2, kB3 = Q * NC * 2, kA3 = R * NC * 2;
+    constexpr uint32_t kChunk = 2 * kB1 + 2 * kB3;
+    constexpr int SS = K * Q + 4;   // row stride (floats) of the output stage: rows fall on shifted banks
+    static_assert(R * SS * 4 <= K * kA1 + kAG + 2 * K * kA3, "output stage exceeds the operand tiles it reuses");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* A1 = smem;                 // [K][R x q]           mu_j
+    unsigned char* AG = A1 + K * kA1;         // [R x W]              G window
+    unsigned char* A3 = AG + kAG;             // [K][hi, lo][R x Nc]  X_k
+    unsigned char* BC = A3 + 2 * K * kA3;     // forward rows (hi, lo), inverse rows (hi, lo) of a chunk
+    float2* TW = reinterpret_cast<float2*>(BC + kChunk);         // [L] (cos, sin)(2 pi m / L)
+    int* s_off = reinterpret_cast<int*>(TW + L);                 // [R][K][3] offsets of e0, e1 (msg), ch2v
+    float* stage = reinterpret_cast<float*>(smem);               // [R][SS] messages (reuses A1, AG, A3)
+    __shared__ __align__(8) uint64_t mbar_store;
+    __shared__ uint32_t tmem_holder;
+    __shared__ int s_rowf[R];          // frame of each row, -1 if the row is not decoded
+    __shared__ uint8_t s_weak[2][R];   // per half and row: a user's peak is below kMinPeak
+
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int m = quarter * 32 + lane;   // this thread's row (= its tensor-memory lane)
+    const int gsub = lane / GL, gl = lane % GL;
+    const unsigned char* tab = g.dft_tab;
+    for (int i = t; i < L; i += blockDim.x) TW[i] = reinterpret_cast<const float2*>(tab + (size_t)CH * kChunk)[i];
+    // forward rows of the next forward product (r1) and inverse rows of the next inverse product (r3)
+    constexpr int P1 = CH > 1 ? (int)((2 * kB1 / 16 + kDftThreads - 1) / kDftThreads) : 1;
+    constexpr int P3 = CH > 1 ? (int)((2 * kB3 / 16 + kDftThreads - 1) / kDftThreads) : 1;
+    uint4 r1[P1], r3[P3];
+    auto fetch = [&](int c) {   // r1 <- forward rows of chunk c
+        const uint4* src = reinterpret_cast<const uint4*>(tab + (size_t)c * kChunk);
+#pragma unroll
+        for (int i = 0; i < P1; ++i) {
+            const int j = t + i * kDftThreads;
+            if (j < (int)(2 * kB1 / 16)) r1[i] = src[j];
+        }
+    };
+    auto fetch3 = [&](int c) {   // r3 <- inverse rows of chunk c
+        const uint4* src = reinterpret_cast<const uint4*>(tab + (size_t)c * kChunk + 2 * kB1);
+#pragma unroll
+        for (int i = 0; i < P3; ++i) {
+            const int j = t + i * kDftThreads;
+            if (j < (int)(2 * kB3 / 16)) r3[i] = src[j];
+        }
+    };
+    auto put1 = [&]() {
+        uint4* dst = reinterpret_cast<uint4*>(BC);
+#pragma unroll
+        for (int i = 0; i < P1; ++i) {
+            const int j = t + i * kDftThreads;
+            if (j < (int)(2 * kB1 / 16)) dst[j] = r1[i];
+        }
+    };
+    auto put3 = [&]() {
+        uint4* dst = reinterpret_cast<uint4*>(BC + 2 * kB1);
+#pragma unroll
+        for (int i = 0; i < P3; ++i) {
+            const int j = t + i * kDftThreads;
+            if (j < (int)(2 * kB3 / 16)) dst[j] = r3[i];
+        }
+    };
+    if constexpr (CH == 1) {   // one chunk: the DFT rows stay resident
+        const uint4* src = reinterpret_cast<const uint4*>(tab);
+        uint4* dst = reinterpret_cast<uint4*>(BC);
+        for (int i = t; i < (int)(kChunk / 16); i += blockDim.x) dst[i] = src[i];
+    } else {
+        fetch(0);
+        fetch3(0);
+    }
+    const uint32_t mbar = tc::smem_addr(&mbar_store);
+    if (t == 0) tc::mbar_init(mbar);
+    if (warp == 0) tc::tmem_alloc(&tmem_holder, S.tmem_cols);
+    tc::proxy_fence();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = tmem_holder;
+    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
+    const uint32_t sA1 = tc::smem_addr(A1), sAG = tc::smem_addr(AG), sB1 = tc::smem_addr(BC), sB3 = sB1 + 2 * kB1,
+                   sA3 = tc::smem_addr(A3);
+    uint32_t phase = 0;
+    bool ok = true;
+    const long total = (long)F * g.n;
+    const long tiles = (total + R - 1) / R;
+    const size_t us = (size_t)g.E * Q, fs = (size_t)K * us, vs = (size_t)K * g.n * Q;
+
+    for (long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const long r = tile * R + m;
+        const long f = r < total ? r / g.n : 0;
+        const int u = r < total ? (int)(r % g.n) : 0;
+        const bool live = r < total && (!active || active[f]);
+        GaussTerm gt{};
+        int u_lo = 0;
+        if (live) {
+            gt = gauss_term(y[r], K, Q, frame_inv_s2(g, f));
+            u_lo = min(max(gt.ss - W / 2, 0), max(U - W, 0));
+        }
+        // 1. the row's message offsets (this half's users), then mu by lane groups
+        if (half == 0) s_rowf[m] = live ? (int)f : -1;
+        if (live) {
+            for (int k = half; k < K; k += 2) {
+                const int var = g.use_pos[k * g.n + u];
+                const int e0 = g.var_edge[2 * var], e1 = g.var_edge[2 * var + 1];
+                int* o = s_off + (m * K + k) * 3;
+                o[0] = (int)(k * us) + (e0 >> 2) * 4 * Q + (e0 & 3) * Q;
+                o[1] = (int)(k * us) + (e1 >> 2) * 4 * Q + (e1 & 3) * Q;
+                o[2] = (k * g.n + var) * Q;
+            }
+        }
+        if constexpr (CH > 1) put1();   // forward rows of chunk 0 (the last tile's products are done)
+#pragma unroll
+        for (int kq = 0; kq < W / 16; ++kq) {   // this half of the G window
+            const int kg = half * (W / 16) + kq;
+            float e[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int ii = kg * 8 + i, uu = u_lo + ii;
+                e[i] = live ? (uu < U ? __expf(gt.expo(uu)) : 0.0f) : (ii == 0 ? 1.0f : 0.0f);
+            }
+            *reinterpret_cast<uint4*>(AG + tc::tile_off(m, kg, W)) = pack8(e);
+        }
+        __syncthreads();
+        if constexpr (CH > 1) fetch(CH > 1 ? 1 : 0);
+#pragma unroll 2
+        for (int p = warp * PPW + gsub; p < R * K; p += NW * PPW) {
+            const int mr = p / K, k = p - mr * K;
+            const int fr = s_rowf[mr];
+            float4 v = make_float4(gl == 0 ? 1.0f : 0.0f, 0.0f, 0.0f, 0.0f);
+            if (fr >= 0) {
+                const float* mf = msg + (size_t)fr * fs;
+                const int* o = s_off + (mr * K + k) * 3;
+                v = mul4(reinterpret_cast<const float4*>(mf + o[0])[gl], reinterpret_cast<const float4*>(mf + o[1])[gl]);
+            }
+            const float inv = 1.0f / group_max<GL>(max4(v));
+            const float4 w = scale4(v, inv);
+            *reinterpret_cast<uint2*>(A1 + k * kA1 + tc::tile_off(mr, gl >> 1, Q) + (gl & 1) * 8) =
+                make_uint2(pack_h2(__float2half_rn(w.x), __float2half_rn(w.y)),
+                           pack_h2(__float2half_rn(w.z), __float2half_rn(w.w)));
+        }
+
+        // 2. chunks of the spectrum
+        tc::proxy_fence();
+        tc::fence_before();
+        __syncthreads();
+        if (t == 0) {
+            tc::fence_after();
+            issue_forward<Q, K, Sh>(tmem, sA1, sAG, sB1);
+            tc::mma_commit(mbar);
+        }
+        float inv_dc[K + 1];
+#pragma unroll 1
+        for (int c = 0; c < CH; ++c) {
+            // forward products of chunk c (and the inverse products of chunk c-1) done
+            if (!tc::wait_bounded(mbar, phase, g.tc_error)) {
+                ok = false;
+                break;
+            }
+            phase ^= 1;
+            tc::fence_after();
+            if constexpr (CH > 1) {
+                put3();                          // inverse rows of chunk c
+                fetch3((c + 1) % CH);
+                if (c + 1 < CH) {
+                    put1();                      // forward rows of chunk c + 1
+                    fetch((c + 2) % CH);
+                }
+            }
+            if (c == 0) {   // DC terms (real, >= 1): every spectrum is scaled to DC 1
+                uint32_t raw[K + 1][8];
+#pragma unroll
+                for (int j = 0; j <= K; ++j) tc::tmem_ld8_nowait(trow + SP + j * NC, raw[j]);
+                tc::ld_wait();
+#pragma unroll
+                for (int j = 0; j <= K; ++j) inv_dc[j] = 1.0f / __uint_as_float(raw[j][0]);
+            }
+#pragma unroll 1
+            for (int cq = 0; cq < NC / 16; ++cq) {
+                const int cg = half * (NC / 16) + cq;   // group of 8 columns = 4 frequency pairs
+                uint32_t raw[K + 1][8];
+#pragma unroll
+                for (int j = 0; j <= K; ++j) tc::tmem_ld8_nowait(trow + SP + j * NC + cg * 8, raw[j]);
+                tc::ld_wait();
+                float xs[K][8];
+#pragma unroll
+                for (int pp = 0; pp < 4; ++pp) {
+                    const int pg = c * (NC / 2) + cg * 4 + pp;
+                    Cx mh[K], X[K], gh;
+                    if (pg == 0) {   // (DC, Nyquist), both real
+#pragma unroll
+                        for (int j = 0; j < K; ++j) mh[j] = {__uint_as_float(raw[j][1]) * inv_dc[j], 0.0f};
+                        gh = {__uint_as_float(raw[K][1]) * inv_dc[K] * ((u_lo & 1) ? -1.0f : 1.0f), 0.0f};
+                        leave_one_out<K>(mh, gh, X);
+#pragma unroll
+                        for (int k = 0; k < K; ++k) {
+                            xs[k][0] = 1.0f;
+                            xs[k][1] = X[k].r;
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < K; ++j)
+                            mh[j] = {__uint_as_float(raw[j][2 * pp]) * inv_dc[j],
+                                     __uint_as_float(raw[j][2 * pp + 1]) * inv_dc[j]};
+                        const Cx gw = {__uint_as_float(raw[K][2 * pp]) * inv_dc[K],
+                                       __uint_as_float(raw[K][2 * pp + 1]) * inv_dc[K]};
+                        const float2 w = TW[(pg * u_lo) % L];   // window offset: G^ = Gw^ e^{-2 pi i f u_lo / L}
+                        gh = {gw.r * w.x + gw.i * w.y, gw.i * w.x - gw.r * w.y};
+                        leave_one_out<K>(mh, gh, X);
+#pragma unroll
+                        for (int k = 0; k < K; ++k) {
+                            xs[k][2 * pp] = X[k].r;
+                            xs[k][2 * pp + 1] = X[k].i;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    uint4 hi, lo;
+                    split8(xs[k], hi, lo);
+                    *reinterpret_cast<uint4*>(A3 + (2 * k) * kA3 + tc::tile_off(m, cg, NC)) = hi;
+                    *reinterpret_cast<uint4*>(A3 + (2 * k + 1) * kA3 + tc::tile_off(m, cg, NC)) = lo;
+                }
+            }
+            tc::fence_before();
+            tc::proxy_fence();
+            __syncthreads();
+            if (t == 0) {
+                tc::fence_after();
+                issue_inverse<Q, K, Sh>(tmem, sA3, sB3, c);
+                if (c + 1 < CH) issue_forward<Q, K, Sh>(tmem, sA1, sAG, sB1);
+                tc::mma_commit(mbar);
+            }
+        }
+        if (!ok) break;
+        if (!tc::wait_bounded(mbar, phase, g.tc_error)) {
+            ok = false;
+            break;
+        }
+        phase ^= 1;
+        tc::fence_after();
+
+        // 3. messages.  With every spectrum scaled to DC 1 the accumulated value is
+        // L times the probability mass sum_s E(s) G(s + a) of normalised sequences,
+        // computed with an absolute error of order L 2^-22.  A row where some
+        // user's peak mass is below kMinPeak is left to the FP32 trellis: nothing
+        // is written but a NaN in the first entry of user 0's channel message,
+        // which the trellis pass looks for.  Each thread normalises its row's
+        // messages into the stage; lane groups then write them out.
+        bool weak = false;
+#pragma unroll 1
+        for (int k = half; k < K; k += 2) {
+            float mx = -INFINITY;
+#pragma unroll
+            for (int c16 = 0; c16 < Q / 16; ++c16) {
+                float o[16];
+                tc::tmem_ld16(trow + k * Q + c16 * 16, o);
+                mx = fmaxf(mx, vmax(o));
+            }
+            weak |= !(mx >= kMinPeak * (float)L);
+            const float inv = 1.0f / mx;
+            float* srow = stage + m * SS + k * Q;
+#pragma unroll
+            for (int c16 = 0; c16 < Q / 16; ++c16) {
+                float o[16];
+                tc::tmem_ld16(trow + k * Q + c16 * 16, o);
+#pragma unroll
+                for (int a = 0; a < 16; a += 4)
+                    *reinterpret_cast<float4*>(srow + c16 * 16 + a) =
+                        make_float4(fmaxf(o[a] * inv, kRelFloor), fmaxf(o[a + 1] * inv, kRelFloor),
+                                    fmaxf(o[a + 2] * inv, kRelFloor), fmaxf(o[a + 3] * inv, kRelFloor));
+            }
+        }
+        s_weak[half][m] = weak ? 1 : 0;
+        tc::fence_before();
+        __syncthreads();
+#pragma unroll 2
+        for (int p = warp * PPW + gsub; p < R * K; p += NW * PPW) {
+            const int mr = p / K, k = p - mr * K;
+            const int fr = s_rowf[mr];
+            const bool emit = fr >= 0 && !(s_weak[0][mr] | s_weak[1][mr]);
+            const int* o = s_off + (mr * K + k) * 3;
+            float* mf = msg + (size_t)(fr >= 0 ? fr : 0) * fs;
+            const float4 ov = reinterpret_cast<const float4*>(stage + mr * SS + k * Q)[gl];
+            float4 c0 = make_float4(1.0f, 1.0f, 1.0f, 1.0f), c1 = c0;
+            if (emit) {
+                c0 = reinterpret_cast<const float4*>(mf + o[0])[gl];
+                c1 = reinterpret_cast<const float4*>(mf + o[1])[gl];
+            }
+            // v2c of each edge = ch2v * c2v of the other edge, rescaled to max 1
+            const float4 v0 = mul4(ov, c1), v1 = mul4(ov, c0);
+            const float i0 = 1.0f / group_max<GL>(max4(v0)), i1 = 1.0f / group_max<GL>(max4(v1));
+            if (emit) {
+                reinterpret_cast<float4*>(ch2v + (size_t)fr * vs + o[2])[gl] = ov;
+                reinterpret_cast<float4*>(mf + o[0])[gl] = scale4(v0, i0);
+                reinterpret_cast<float4*>(mf + o[1])[gl] = scale4(v1, i1);
+            } else if (fr >= 0 && k == 0 && gl == 0) {
+                ch2v[(size_t)fr * vs + o[2]] = __int_as_float(0x7fc00000);
+                if (g.log_fallbacks) atomicAdd(g.log_fallbacks, 1ull);
+            }
+        }
+        __syncthreads();   // the stage and the offsets are read before the next tile overwrites them
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::tmem_free(tmem, S.tmem_cols);
+    }
+}
+template <int Q, int K>
+cudaError_t channel_dft_qk(const Graph& g, const DeviceInfo& di, int F, const float* y, float* msg, float* ch2v,
+                           const uint8_t* active, cudaStream_t s)
+{
+    constexpr DftShape S = dft_shape(K, Q);
+    if constexpr (!S.ok) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (S.smem > di.smem_optin) return cudaErrorInvalidValue;
+        cudaError_t e =
+            cudaFuncSetAttribute(k_channel_dft<Q, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, S.smem);
+        if (e != cudaSuccess) return e;
+        const long tiles = ((long)F * g.n + kDftRows - 1) / kDftRows;
+        const int grid = (int)std::max(1L, std::min(tiles, (long)di.sm_count));   // one CTA per SM (tensor memory)
+        k_channel_dft<Q, K><<<grid, kDftThreads, S.smem, s>>>(g, F, y, msg, ch2v, active);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        return launch_channel_fix(g, di, F, y, msg, ch2v, active, s);
+    }
+}
+
+template <int Q>
+cudaError_t channel_dft_q(const Graph& g, const DeviceInfo& di, int F, const float* y, float* msg, float* ch2v,
+                          const uint8_t* active, cudaStream_t s)
+{
+    switch (g.K) {
+        case 2: return channel_dft_qk<Q, 2>(g, di, F, y, msg, ch2v, active, s);
+        case 3: return channel_dft_qk<Q, 3>(g, di, F, y, msg, ch2v, active, s);
+        case 4: return channel_dft_qk<Q, 4>(g, di, F, y, msg, ch2v, active, s);
+        case 5: return channel_dft_qk<Q, 5>(g, di, F, y, msg, ch2v, active, s);
+        case 6: return channel_dft_qk<Q, 6>(g, di, F, y, msg, ch2v, active, s);
+        case 7: return channel_dft_qk<Q, 7>(g, di, F, y, msg, ch2v, active, s);
+        case 8: return channel_dft_qk<Q, 8>(g, di, F, y, msg, ch2v, active, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_channel_dft(const Graph& g, const DeviceInfo& di, int F, const float* y, float* msg, float* ch2v,
+                               const uint8_t* active, cudaStream_t s)
+{
+    if (F <= 0) return cudaSuccess;
+    if (!g.dft_tab || g.dv != 2 || g.dc != kDC || !dft_shape(g.K, g.Q).ok) return cudaErrorInvalidValue;
+    switch (g.Q) {
+        case 16: return channel_dft_q<16>(g, di, F, y, msg, ch2v, active, s);
+        case 32: return channel_dft_q<32>(g, di, F, y, msg, ch2v, active, s);
+        case 64: return channel_dft_q<64>(g, di, F, y, msg, ch2v, active, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t dft_table_bytes(int K, int Q)
+{
+    const DftShape S = dft_shape(K, Q);
+    if (!S.ok) return 0;
+    return (size_t)S.chunks * (4ull * S.Nc * S.KB + 4ull * Q * S.Nc) + 8ull * S.L;
+}
+
+// Forward row n of the spectrum (pair p = n/2; n even: real part, odd: imaginary
+// part of the e^{-2 pi i p x / L} transform; pair 0 = DC and Nyquist), inner index x.
+static double forward_entry(int n, int x, int L)
+{
+    const int p = n / 2;
+    if (p == 0) return (n & 1) ? ((x & 1) ? -1.0 : 1.0) : 1.0;
+    const double th = 2.0 * M_PI * (double)(((long long)p * x) % L) / L;
+    return (n & 1) ? -std::sin(th) : std::cos(th);
+}
+
+// Inverse weight of spectral column n for output a: sum over the Hermitian
+// spectrum folded onto f = 0..L/2 (factor 2 on the pairs f = 1..L/2-1).
+static double inverse_entry(int n, int a, int L)
+{
+    const int p = n / 2;
+    if (p == 0) return (n & 1) ? ((a & 1) ? -1.0 : 1.0) : 1.0;
+    const double th = 2.0 * M_PI * (double)(((long long)p * a) % L) / L;
+    return (n & 1) ? -2.0 * std::sin(th) : 2.0 * std::cos(th);
+}
+
+// FP16 hi and lo terms of x at (row, col) of a (rows x KD) tile; lo tile at +tile_bytes.
+static void put_split(unsigned char* tile, size_t tile_bytes, int row, int col, int KD, double x)
+{
+    const __half hi = __float2half_rn((float)x);
+    const __half lo = __float2half_rn((float)(x - (double)__half2float(hi)));
+    const size_t off = tc::tile_off(row, col / 8, KD) + (col % 8) * 2;
+    std::memcpy(tile + off, &hi, 2);
+    std::memcpy(tile + tile_bytes + off, &lo, 2);
+}
+
+void dft_build_table(int K, int Q, unsigned char* out)
+{
+    const DftShape S = dft_shape(K, Q);
+    if (!S.ok) return;
+    const int L = S.L, NC = S.Nc, KB = S.KB;
+    const size_t kB1 = (size_t)NC * KB * 2, kB3 = (size_t)Q * NC * 2, kChunk = 2 * kB1 + 2 * kB3;
+    std::memset(out, 0, dft_table_bytes(K, Q));
+    for (int c = 0; c < S.chunks; ++c) {
+        unsigned char* B1 = out + c * kChunk;
+        unsigned char* B3 = B1 + 2 * kB1;
+        for (int nl = 0; nl < NC; ++nl)
+            for (int x = 0; x < KB; ++x) put_split(B1, kB1, nl, x, KB, forward_entry(c * NC + nl, x, L));
+        for (int a = 0; a < Q; ++a)
+            for (int nl = 0; nl < NC; ++nl) put_split(B3, kB3, a, nl, NC, inverse_entry(c * NC + nl, a, L));
+    }
+    float* tw = reinterpret_cast<float*>(out + S.chunks * kChunk);
+    for (int i = 0; i < L; ++i) {
+        const double th = 2.0 * M_PI * i / L;
+        tw[2 * i] = (float)std::cos(th);
+        tw[2 * i + 1] = (float)std::sin(th);
+    }
+}
+
+}  // namespace jbp

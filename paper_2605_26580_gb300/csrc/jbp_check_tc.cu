@@ -21,83 +21,23 @@
 #include <cuda_bf16.h>
 
 #include "jbp_internal.h"
+#include "jbp_tc.cuh"
 
 namespace jbp {
 namespace {
 
 constexpr int kTcThreads = 128;
 constexpr int kTileRows = 128;
-constexpr long long kSpinLimit = 1ll << 24;
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+using tc::fence_after;
+using tc::fence_before;
+using tc::proxy_fence;
+using tc::smem_addr;
 
-// tcgen05 shared-memory matrix descriptor: K-major, no swizzle.  lbo = byte
-// distance between 8x16-byte core matrices along K, sbo = along M (or N).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;   // descriptor version
-    return d;                 // base offset 0, absolute LBO mode, no swizzle
-}
-
-// instruction descriptor, kind::f16: BF16 x BF16 -> F32, both K-major
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, int accumulate)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t phase)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(mbar), "r"(phase)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// 16 consecutive TMEM columns of this thread's lane
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Operand tile layout: element (row m, column k) of a (rows x Q) BF16 matrix at
-// byte (m/8)*SBO + (k/8)*128 + (m%8)*16 + (k%8)*2, SBO = (Q/8)*128.
 template <int Q>
 __device__ __forceinline__ uint32_t tile_off(int m, int kg)
 {
-    return (uint32_t)((m >> 3) * (Q / 8) * 128 + kg * 128 + (m & 7) * 16);
+    return tc::tile_off(m, kg, Q);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi)
@@ -147,18 +87,18 @@ template <int Q, int NSPLIT>
 __device__ __forceinline__ void issue_transform(uint32_t a_base, uint32_t b_base, uint32_t tmem, uint32_t mbar)
 {
     constexpr uint32_t kTile = kTileRows * Q * 2, sbo = (Q / 8) * 128;
-    constexpr uint32_t idesc = idesc_bf16(kTileRows, Q);
+    constexpr uint32_t idesc = tc::idesc_f16(kTileRows, Q, true);
     int acc = 0;
 #pragma unroll
     for (int s = 0; s < NSPLIT; ++s)
 #pragma unroll
         for (int ks = 0; ks < Q / 16; ++ks) {
-            const uint64_t ad = smem_desc(a_base + s * kTile + ks * 256, 128, sbo);
-            const uint64_t bd = smem_desc(b_base + ks * 256, 128, sbo);
-            mma_bf16(tmem, ad, bd, idesc, acc);
+            const uint64_t ad = tc::smem_desc(a_base + s * kTile + ks * 256, 128, sbo);
+            const uint64_t bd = tc::smem_desc(b_base + ks * 256, 128, sbo);
+            tc::mma_f16(tmem, ad, bd, idesc, acc);
             acc = 1;
         }
-    mma_commit(mbar);
+    tc::mma_commit(mbar);
 }
 
 template <int Q>
@@ -167,25 +107,10 @@ __device__ __forceinline__ void read_row(uint32_t tmem_row, float (&v)[Q])
 #pragma unroll
     for (int c = 0; c < Q / 16; ++c) {
         float t[16];
-        tmem_ld16(tmem_row + c * 16, t);
+        tc::tmem_ld16(tmem_row + c * 16, t);
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[c * 16 + i] = t[i];
     }
-}
-
-// Bounded wait on the MMA completion; returns false (all threads agree) on expiry.
-__device__ __forceinline__ bool wait_mma(uint32_t mbar, uint32_t phase, int* err)
-{
-    long long spins = 0;
-    bool done = false;
-    while (!(done = mbar_try_wait(mbar, phase)) && ++spins < kSpinLimit) {
-    }
-    const int timed_out = __syncthreads_or(done ? 0 : 1);
-    if (timed_out) {
-        if (threadIdx.x == 0) atomicExch(err, 1);
-        return false;
-    }
-    return true;
 }
 
 template <int Q, int NSPLIT>
@@ -212,20 +137,12 @@ __global__ void __launch_bounds__(kTcThreads) k_check_tc(Graph g, long R, float*
             make_uint4(pack_bf16(e[0], e[1]), pack_bf16(e[2], e[3]), pack_bf16(e[4], e[5]), pack_bf16(e[6], e[7]));
     }
     const uint32_t mbar = smem_addr(&mbar_store);
-    if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_holder)),
-                     "r"(kCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
+    if (t == 0) tc::mbar_init(mbar);
+    if (warp == 0) tc::tmem_alloc(&tmem_holder, kCols);
     proxy_fence();
-    tc_fence_before();
+    fence_before();
     __syncthreads();
-    tc_fence_after();
+    fence_after();
     const uint32_t tmem = tmem_holder;
     const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
     const uint32_t a_base = smem_addr(A), b_base = smem_addr(B);
@@ -252,12 +169,12 @@ __global__ void __launch_bounds__(kTcThreads) k_check_tc(Graph g, long R, float*
         proxy_fence();
         __syncthreads();
         if (t == 0) {
-            tc_fence_after();
+            fence_after();
             issue_transform<Q, NSPLIT>(a_base, b_base, tmem, mbar);
         }
-        if (!wait_mma(mbar, phase, err)) break;
+        if (!tc::wait_bounded(mbar, phase, err)) break;
         phase ^= 1;
-        tc_fence_after();
+        fence_after();
         read_row<Q>(tmem_row, v);
         // leave-one-out product over the check's four rows (lanes t^1, t^2, t^3)
 #pragma unroll
@@ -269,16 +186,16 @@ __global__ void __launch_bounds__(kTcThreads) k_check_tc(Graph g, long R, float*
         }
         // inverse transform (the 1/q factor cancels in the normalisation)
         stage_row<Q, NSPLIT>(A, t, v);
-        tc_fence_before();
+        fence_before();
         proxy_fence();
         __syncthreads();
         if (t == 0) {
-            tc_fence_after();
+            fence_after();
             issue_transform<Q, NSPLIT>(a_base, b_base, tmem, mbar);
         }
-        if (!wait_mma(mbar, phase, err)) break;
+        if (!tc::wait_bounded(mbar, phase, err)) break;
         phase ^= 1;
-        tc_fence_after();
+        fence_after();
         read_row<Q>(tmem_row, v);
         if (live) {
             float mx = v[0];
@@ -288,14 +205,14 @@ __global__ void __launch_bounds__(kTcThreads) k_check_tc(Graph g, long R, float*
 #pragma unroll
             for (int x = 0; x < Q; ++x) row[sdiv[h * Q + x]] = fmaxf(v[x], fl) * inv;
         }
-        tc_fence_before();
+        fence_before();
         __syncthreads();
     }
-    tc_fence_before();
+    fence_before();
     __syncthreads();
     if (warp == 0) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+        fence_after();
+        tc::tmem_free(tmem, kCols);
     }
 }
 

@@ -50,6 +50,7 @@ struct Graph {
     int* tc_error;            // set to 1 if a tensor-core wait expired (may be null: FP32 only)
     const float* sigma2_f;    // [F]     per-frame noise variance of this batch (may be null)
     const uint16_t* chk_order;  // [K*P] order of the check units in the fused check phase (may be null)
+    const unsigned char* dft_tab = nullptr;   // DFT tables of the tensor-core channel node (null: trellis)
 };
 
 // 1 / sigma2 of frame f
@@ -372,12 +373,42 @@ __device__ __forceinline__ void chan_reg(const float (&mu)[K][Q], const GaussTer
     }
 }
 
+// Outputs of the channel node for user k's variable i (variable degree 2): its
+// channel message o (max 1, floored) into ch2v_f, and each of its two c2v
+// messages in the user's message blocks blk replaced by the v2c message of the
+// same edge (eq. app_ldpc_v2c with the channel message as the local belief:
+// v2c_0 = ch2v * c2v_1, v2c_1 = ch2v * c2v_0, each rescaled to max 1).
+template <int Q>
+__device__ __forceinline__ void chan_store_user(const Graph& g, float* blk, int cbs, float* ch2v_f, int k, int i,
+                                                const float (&o)[Q])
+{
+    vstore<Q>(ch2v_f + ((size_t)k * g.n + i) * Q, o);
+    float* p0 = edge_ptr(blk, g.var_edge[2 * i], cbs, Q);
+    float* p1 = edge_ptr(blk, g.var_edge[2 * i + 1], cbs, Q);
+    float c0[Q], c1[Q];
+    vload<Q>(p0, c0);
+    vload<Q>(p1, c1);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const float t = c0[a];
+        c0[a] = o[a] * c1[a];
+        c1[a] = o[a] * t;
+    }
+    const float i0 = 1.0f / vmax(c0), i1 = 1.0f / vmax(c1);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        c0[a] *= i0;
+        c1[a] *= i1;
+    }
+    vstore<Q>(p0, c0);
+    vstore<Q>(p1, c1);
+}
+
 // One channel use u of one frame, thread shape (variable degree 2).  msg_f:
 // the frame's message blocks (user k at msg_f + k*ustride); ch2v_f: the frame's
 // channel messages.  Reads the c2v of the K variables on this use, writes their
 // channel messages and replaces each of their two c2v by the v2c message of the
-// same edge (eq. app_ldpc_v2c with the channel message as the local belief:
-// v2c_0 = ch2v * c2v_1, v2c_1 = ch2v * c2v_0, each rescaled to max 1).
+// same edge (chan_store_user).
 template <int K, int Q>
 __device__ __forceinline__ void chan_thread(const Graph& g, float* msg_f, size_t ustride, int cbs, float* ch2v_f,
                                             float y, float inv_s2, int u)
@@ -399,28 +430,7 @@ __device__ __forceinline__ void chan_thread(const Graph& g, float* msg_f, size_t
     }
     const GaussTerm gt = gauss_term(y, K, Q, inv_s2);
     chan_reg<K, Q>(mu, gt, g.log_fallbacks, [&](int k, const float (&o)[Q]) {
-        const int i = var[k];
-        float* blk = msg_f + k * ustride;
-        vstore<Q>(ch2v_f + ((size_t)k * g.n + i) * Q, o);
-        float* p0 = edge_ptr(blk, g.var_edge[2 * i], cbs, Q);
-        float* p1 = edge_ptr(blk, g.var_edge[2 * i + 1], cbs, Q);
-        float c0[Q], c1[Q];
-        vload<Q>(p0, c0);
-        vload<Q>(p1, c1);
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            const float t = c0[a];
-            c0[a] = o[a] * c1[a];
-            c1[a] = o[a] * t;
-        }
-        const float i0 = 1.0f / vmax(c0), i1 = 1.0f / vmax(c1);
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            c0[a] *= i0;
-            c1[a] *= i1;
-        }
-        vstore<Q>(p0, c0);
-        vstore<Q>(p1, c1);
+        chan_store_user<Q>(g, msg_f + k * ustride, cbs, ch2v_f, k, var[k], o);
     });
 }
 

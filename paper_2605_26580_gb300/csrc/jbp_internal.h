@@ -39,6 +39,62 @@ cudaError_t launch_fill(float* p, size_t count, float value, cudaStream_t s);
 // terms (JBP_PREC_BF16X2 / BF16 / BF16X3) and FP32 accumulation.
 cudaError_t launch_check_tc(const Graph& g, const DeviceInfo& di, int F, float* msg, const uint8_t* active,
                             int precision, cudaStream_t s);
+// Channel node as DFTs over the symbol-sum alphabet on the tensor cores
+// (jbp_channel_dft.cu).  Tile: 128 channel uses (rows).  U = K(q-1)+1 sum
+// values; L >= U the DFT length (a multiple of 16); W the width of the window of
+// the Gaussian score G that is transformed (the rest is below the message floor
+// for W = L, and below exp(-2 (W/2 - 1)^2 / sigma2) of the maximum otherwise);
+// KB = max(q, W) the inner dimension of the forward DFT matrix; Nc the real
+// spectral columns per chunk.  Built where K >= 2, q >= 16 and K q <= 256 (the
+// inverse-DFT accumulators, K q tensor-memory columns, stay resident).
+constexpr int kDftRows = 128;
+constexpr int kDftThreads = 256;
+constexpr int kDftSmemMax = 226 * 1024;   // dynamic part; the kernel's static part is under 1 KB
+struct DftShape {
+    int U, L, W, KB, Nc, chunks, tmem_cols, smem;
+    bool ok;
+};
+__host__ __device__ constexpr DftShape dft_shape(int K, int Q)
+{
+    DftShape s{};
+    s.U = K * (Q - 1) + 1;
+    s.L = (s.U + 15) / 16 * 16;
+    s.W = s.L < 128 ? s.L : 128;
+    s.KB = Q > s.W ? Q : s.W;
+    s.ok = false;
+    if (Q < 16 || Q > 64 || K < 2 || K * Q > 256) return s;
+    // mu tiles + G window (one FP16 term each) + twiddles + message offsets + alignment slack
+    const int fixed = K * kDftRows * Q * 2 + kDftRows * s.W * 2 + s.L * 8 + kDftRows * K * 12 + 1024;
+    for (int nc = 128; nc >= 16; nc /= 2) {
+        if (s.L % nc || K * Q + (K + 1) * nc > 512) continue;
+        // forward chunk (hi, lo) + inverse chunk (hi, lo) + X tiles (hi, lo)
+        const int sm = fixed + nc * s.KB * 4 + Q * nc * 4 + K * kDftRows * nc * 4;
+        if (sm > kDftSmemMax) continue;
+        s.Nc = nc;
+        s.smem = sm;
+        s.ok = true;
+        break;
+    }
+    if (!s.ok) return s;
+    s.chunks = s.L / s.Nc;
+    const int need = K * Q + (K + 1) * s.Nc;
+    s.tmem_cols = need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
+    return s;
+}
+// Bytes of the device tables of one (K, q) and their contents (host memory):
+// per chunk the forward DFT rows (FP16 hi, lo) and the inverse DFT rows (hi,
+// lo) in tensor-core tile order, then L twiddles (cos, sin)(2 pi m / L).
+size_t dft_table_bytes(int K, int Q);
+void dft_build_table(int K, int Q, unsigned char* out);
+// Launches the tensor-core kernel, then the FP32 trellis on the channel uses it
+// could not resolve (launch_channel_fix).
+cudaError_t launch_channel_dft(const Graph& g, const DeviceInfo& di, int F, const float* y, float* msg, float* ch2v,
+                               const uint8_t* active, cudaStream_t s);
+// Team-shape trellis on the channel uses whose user-0 channel message starts
+// with a NaN (left by the tensor-core channel node); q = 16, 32, 64 (jbp_step.cu).
+cudaError_t launch_channel_fix(const Graph& g, const DeviceInfo& di, int F, const float* y, float* msg, float* ch2v,
+                               const uint8_t* active, cudaStream_t s);
+
 cudaError_t launch_ok_from_unsat(int F, int K, const uint8_t* unsat, uint8_t* ok, cudaStream_t s);
 
 // Resident pool of the serving loop: the step-form state of up to F frame

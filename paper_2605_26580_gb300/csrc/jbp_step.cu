@@ -52,7 +52,9 @@ __global__ void __launch_bounds__(kStepThreads) k_channel_thread(Graph g, int F,
 }
 
 // (a) team shape: T lanes per (frame, channel use), trellis in shared scratch.
-template <int Q>
+// FIX: only the channel uses that the tensor-core channel node left to the
+// trellis (a NaN in the first entry of user 0's channel message).
+template <int Q, bool FIX = false>
 __global__ void __launch_bounds__(kStepThreads) k_channel_team(Graph g, int F, const float* __restrict__ y,
                                                                float* msg, float* ch2v,
                                                                const uint8_t* __restrict__ active, int sc_floats)
@@ -69,6 +71,9 @@ __global__ void __launch_bounds__(kStepThreads) k_channel_team(Graph g, int F, c
     for (long unit = (long)blockIdx.x * teams + team; unit < total; unit += (long)gridDim.x * teams) {
         const int f = (int)(unit / g.n), u = (int)(unit % g.n);
         if (active && !active[f]) continue;
+        if constexpr (FIX) {
+            if (!isnan(ch2v[f * vs + (size_t)g.use_pos[u] * Q])) continue;
+        }
         float* msg_f = msg + f * fs;
         const float yv = y[(size_t)f * g.n + u], is2 = frame_inv_s2(g, f);
         if (chan_blocked<Q>(g, msg_f, us, 4 * Q, yv, is2, u, sc, res, L)) {
@@ -479,7 +484,7 @@ cudaError_t channel_thread_q(const Graph& g, const DeviceInfo& di, int F, const 
     return cudaGetLastError();
 }
 
-template <int Q>
+template <int Q, bool FIX = false>
 cudaError_t channel_team_q(const Graph& g, const DeviceInfo& di, int F, const float* y, float* msg, float* ch2v,
                            const uint8_t* active, cudaStream_t s)
 {
@@ -490,11 +495,12 @@ cudaError_t channel_team_q(const Graph& g, const DeviceInfo& di, int F, const fl
     while (threads > 32 && (size_t)(threads / T) * per_team > (size_t)di.smem_optin) threads -= 32;
     const size_t smem = (size_t)(threads / T) * per_team;
     if (smem > (size_t)di.smem_optin) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(k_channel_team<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_channel_team<Q, FIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long units = (long)F * g.n;
-    const int grid = persistent_grid(k_channel_team<Q>, threads, smem, di, threads / T, units);
-    k_channel_team<Q><<<grid, threads, smem, s>>>(g, F, y, msg, ch2v, active, scf);
+    const int grid = persistent_grid(k_channel_team<Q, FIX>, threads, smem, di, threads / T, units);
+    k_channel_team<Q, FIX><<<grid, threads, smem, s>>>(g, F, y, msg, ch2v, active, scf);
     return cudaGetLastError();
 }
 
@@ -578,7 +584,20 @@ cudaError_t launch_channel(const Graph& g, const DeviceInfo& di, int F, const fl
                            const uint8_t* active, cudaStream_t s)
 {
     if (F <= 0) return cudaSuccess;
+    if (g.dft_tab) return launch_channel_dft(g, di, F, y, msg, ch2v, active, s);
     JBP_DISPATCH_Q(g.Q, (channel_q<Qc>(g, di, F, y, msg, ch2v, active, s)));
+}
+
+cudaError_t launch_channel_fix(const Graph& g, const DeviceInfo& di, int F, const float* y, float* msg, float* ch2v,
+                               const uint8_t* active, cudaStream_t s)
+{
+    if (F <= 0) return cudaSuccess;
+    switch (g.Q) {
+        case 16: return channel_team_q<16, true>(g, di, F, y, msg, ch2v, active, s);
+        case 32: return channel_team_q<32, true>(g, di, F, y, msg, ch2v, active, s);
+        case 64: return channel_team_q<64, true>(g, di, F, y, msg, ch2v, active, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_check(const Graph& g, const DeviceInfo& di, int F, float* msg, const uint8_t* active, int precision,

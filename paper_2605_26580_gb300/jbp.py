@@ -19,11 +19,12 @@ LIB_PATH = os.path.join(HERE, "libjbp.so")
 OK, EINVAL, ENOMEM, ECUDA, EAGAIN, ETIMEOUT, ECLOSED = range(7)
 PREC_FP32, PREC_BF16X2, PREC_BF16, PREC_BF16X3 = 0, 1, 2, 3
 FORM_AUTO, FORM_FUSED, FORM_STEP, FORM_PLAIN = 0, 1, 2, 3
+CHAN_TRELLIS, CHAN_DFT = 0, 1
 
 EXPORTS = [
     "jbp_context_create", "jbp_context_destroy", "jbp_create", "jbp_destroy", "jbp_decode",
     "jbp_submit", "jbp_poll", "jbp_serving_stats", "jbp_last_error", "jbp_step_channel",
-    "jbp_step_check", "jbp_step_var", "jbp_step_syndrome", "jbp_query", "jbp_decode_noalloc", "jbp_stats", "jbp_decode_many", "jbp_tune",
+    "jbp_step_check", "jbp_step_var", "jbp_step_syndrome", "jbp_query", "jbp_query_channel", "jbp_decode_noalloc", "jbp_stats", "jbp_decode_many", "jbp_tune",
     "jbp_ura_create", "jbp_ura_destroy", "jbp_amp_evidence", "jbp_sic_decode", "jbp_ura_decode", "jbp_match_rows",
 ]
 
@@ -45,7 +46,8 @@ class Channel(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("iters", C.c_int32), ("early_stop", C.c_int32), ("precision", C.c_int32), ("device", C.c_int32),
-                ("mem_budget_bytes", C.c_int64), ("block_iters", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("mem_budget_bytes", C.c_int64), ("block_iters", C.c_int32), ("channel_node", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 class UraParams(C.Structure):
@@ -88,6 +90,7 @@ def lib():
             L.jbp_step_var.argtypes = [vp, i32, vp, vp, vp, vp, vp]
             L.jbp_step_syndrome.argtypes = [vp, i32, vp, vp, vp]
             L.jbp_query.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]
+            L.jbp_query_channel.argtypes = [vp, C.POINTER(i32)]
             L.jbp_decode_many.argtypes = [vp, i32, C.POINTER(vp), C.POINTER(Batch), vp]
             L.jbp_tune.argtypes = [vp, C.POINTER(Batch), C.POINTER(i32), C.POINTER(i32)]
             L.jbp_stats.argtypes = [vp, C.POINTER(u64), C.POINTER(i32)]
@@ -131,9 +134,9 @@ def _stream_ptr(stream):
 
 class Context:
     def __init__(self, iters: int = 50, early_stop: bool = True, precision: int = PREC_FP32, device: int = 0,
-                 mem_budget_bytes: int = 0, block_iters: int = 0):
+                 mem_budget_bytes: int = 0, block_iters: int = 0, channel_node: int = CHAN_TRELLIS):
         self.opt = Options(int(iters), int(bool(early_stop)), int(precision), int(device), int(mem_budget_bytes),
-                           int(block_iters))
+                           int(block_iters), int(channel_node))
         h = C.c_void_p()
         check(lib().jbp_context_create(C.byref(self.opt), C.byref(h)))
         self.ptr = h
@@ -210,6 +213,9 @@ class Decoder:
         fz = C.c_int32()
         check(lib().jbp_query(h, C.byref(E), C.byref(sb), C.byref(fz)))
         self.E, self.state_bytes, self.fused_ok = E.value, sb.value, bool(fz.value)
+        cn = C.c_int32()
+        check(lib().jbp_query_channel(h, C.byref(cn)))
+        self.channel_node = cn.value
 
     def close(self):
         if self.ptr:

@@ -1,0 +1,189 @@
+"""Tensor-core channel node (DFT over the symbol-sum alphabet) against the FP64
+oracle's trellis.
+
+The transform computes the same extrinsic messages as the trellis (kernel (a))
+with two kinds of error.  The user messages mu_j and the window of the Gaussian
+score G enter as one FP16 term each: a relative rounding of at most 2^-12 per
+value, so each output moves by at most K 2^-12 relative.  The DFT matrices and
+the frequency-domain products are hi + lo FP16 terms (about 2^-22) accumulated in
+FP32, but the inverse transform cancels terms of the size of the spectrum: with
+spectra scaled to DC 1 the accumulated value is L times a probability mass, so
+that error is absolute, at most (K + 2) 2^-22 per term over L terms, and rows
+whose peak mass is below 2^-12 are handed to the FP32 trellis.  Against the
+oracle, max-normalised linear messages therefore differ by at most
+(K + 2) 2^-9 + K 2^-12; the tests print the measured value (a few 1e-4).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2605_26580_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+LN_1E4 = math.log(1e-4)
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def env(jbp_lib, oracle):
+    return jbp_lib, oracle, _torch()
+
+
+def _decoder(jbp, code, K, sigma2, perm, iters=20, early_stop=True, channel_node=1):
+    ctx = jbp.Context(iters=iters, early_stop=early_stop, channel_node=channel_node)
+    return ctx, jbp.Decoder(ctx, code, K, sigma2, perm)
+
+
+def dft_bound(K):
+    return (K + 2) * 2.0 ** -9 + K * 2.0 ** -12
+
+
+def masked_log_err(gpu, ref, thresh=LN_1E4):
+    mask = ref >= thresh
+    return float(np.abs(gpu - ref)[mask].max()) if mask.any() else 0.0
+
+
+def _step_channel(jbp, torch, dec, fr, c2v_lin, K, n, q):
+    F = c2v_lin.shape[0]
+    y_d = torch.from_numpy(fr["y"]).cuda()
+    msg_d = torch.from_numpy(c2v_lin).cuda()
+    ch_d = torch.empty((F, K, n, q), dtype=torch.float32, device="cuda")
+    dec.step_channel(y_d, msg_d, ch_d)
+    torch.cuda.synchronize()
+    return ch_d.cpu().numpy().astype(np.float64), msg_d.cpu().numpy().astype(np.float64)
+
+
+# (K, q, n, F): tiles of 128 channel uses with ragged tails, one and several DFT chunks
+DFT_CASES = [
+    (2, 16, 64, 7), (4, 16, 256, 5), (3, 32, 64, 9), (4, 64, 120, 3), (7, 32, 32, 11),
+    (8, 16, 64, 5), (5, 32, 40, 7), (2, 64, 24, 3), (3, 64, 64, 4),
+]
+
+
+@pytest.mark.parametrize("K,q,n,F", DFT_CASES)
+def test_dft_step_channel_matches_oracle(env, K, q, n, F):
+    jbp, O, torch = env
+    code = I.make_code(n, q)
+    fr = I.make_frames(code, K, 12.0, F, seed=K * 7919 + q * 31 + n)
+    rng = np.random.default_rng(n * 13 + q + K)
+    E = code["P"] * code["dc"]
+    c2v_lin = np.exp(I.random_log_messages(rng, (F, K, E), q, spread=3.0)).astype(np.float32)
+    c2v = np.log(c2v_lin.astype(np.float64))
+    ctx, dec = _decoder(jbp, code, K, fr["sigma2"], fr["perm"])
+    try:
+        assert dec.channel_node == jbp.CHAN_DFT
+        ch_g, v2c_g = _step_channel(jbp, torch, dec, fr, c2v_lin, K, n, q)
+        weak = dec.log_fallbacks()
+        assert dec.tc_timeouts() == 0
+    finally:
+        dec.close()
+        ctx.close()
+    ch_o = np.exp(O.step_channel(code, K, fr["sigma2"], fr["perm"], fr["y"], c2v))
+    lin = float(np.abs(ch_g - ch_o).max())
+    # v2c = ch2v * c2v of the other edge, rescaled: the GPU's own ch2v through the oracle's rule
+    v2c_o = O.step_v2c(code, K, np.log(ch_g), c2v)
+    e_v2c = masked_log_err(np.log(v2c_g), v2c_o)
+    print("DFT channel K=%d q=%d n=%d F=%d: linear err %.2e (bound %.2e), rows to trellis %d of %d, v2c err %.2e"
+          % (K, q, n, F, lin, dft_bound(K), weak, F * n, e_v2c))
+    assert np.isfinite(ch_g).all() and np.isfinite(v2c_g).all()
+    assert np.allclose(ch_g.max(-1), 1.0)
+    assert lin <= dft_bound(K)
+    assert e_v2c <= 1e-4
+
+
+def test_dft_unresolved_rows_go_to_the_trellis(env):
+    """Confident messages that make the observed sum (nearly) impossible: the
+    transform cannot resolve the peak, so every row is handed to the FP32
+    trellis and the messages equal the oracle's in the log domain."""
+    jbp, O, torch = env
+    K, q, n, F = 4, 64, 64, 3
+    code = I.make_code(n, q)
+    fr = I.make_frames(code, K, 14.0, F, seed=5)
+    E = code["P"] * code["dc"]
+    c2v_lin = np.full((F, K, E, q), 1e-12, dtype=np.float32)
+    c2v_lin[..., 0] = 1.0                                 # every user believes symbol 0 ...
+    fr = dict(fr)
+    fr["y"] = np.full((F, n), float(K * (q - 1)), dtype=np.float32)   # ... while y says all are q - 1
+    c2v = np.log(c2v_lin.astype(np.float64))
+    ctx, dec = _decoder(jbp, code, K, fr["sigma2"], fr["perm"])
+    try:
+        ch_g, v2c_g = _step_channel(jbp, torch, dec, fr, c2v_lin, K, n, q)
+        weak = dec.log_fallbacks()
+    finally:
+        dec.close()
+        ctx.close()
+    ch_o = O.step_channel(code, K, fr["sigma2"], fr["perm"], fr["y"], c2v)
+    e = masked_log_err(np.log(ch_g), ch_o)
+    print("unresolved rows: %d of %d to the trellis, log err %.2e" % (weak, F * n, e))
+    assert weak >= F * n
+    assert np.isfinite(ch_g).all()
+    assert e <= 1e-4
+
+
+# (K, q, n, F, SNR dB, T, margin): a converging operating point (2 users x 2 bits per
+# channel use need about 21 dB), and the past-capacity config-3 shape over few
+# iterations (non-converging BP amplifies any rounding by about 2..10 per iteration).
+@pytest.mark.parametrize("K,q,n,F,snr,T,margin", [(2, 16, 64, 60, 24.0, 15, 1e-3),
+                                                  (4, 64, 128, 24, 14.0, 3, 2e-2)])
+def test_dft_decode_agrees_with_oracle(env, K, q, n, F, snr, T, margin):
+    """Whole decodes (step form) with the tensor-core channel node: decisions
+    agree with the FP64 oracle wherever its margin exceeds `margin`, and the
+    symbol error rates agree within the binomial 95% interval."""
+    jbp, O, torch = env
+    code = I.make_code(n, q)
+    fr = I.make_frames(code, K, snr, F, seed=2026 + K + q)
+    ctx, dec = _decoder(jbp, code, K, fr["sigma2"], fr["perm"], iters=T, early_stop=True)
+    try:
+        got = dec.decode(fr["y"])
+        assert dec.tc_timeouts() == 0
+    finally:
+        dec.close()
+        ctx.close()
+    ref = O.decode(code, K, fr["sigma2"], fr["perm"], fr["y"], T, early_stop=True, want_margin=True)
+    diff = got["hat"] != ref["hat"]
+    N = diff.size
+    ser_g, ser_o = float((got["hat"] != fr["c"]).mean()), float((ref["hat"] != fr["c"]).mean())
+    ci = 1.96 * math.sqrt(max(ser_o * (1 - ser_o), 1.0 / N) / N)
+    print("DFT decode K=%d q=%d %.0f dB T=%d: SER gpu %.5f oracle %.5f (CI %.5f); differing %d, at margin > %g: %d; "
+          "iterations equal in %d of %d frames"
+          % (K, q, snr, T, ser_g, ser_o, ci, int(diff.sum()), margin, int((diff & (ref["margin"] > margin)).sum()),
+             int((got["iters"] == ref["iters"]).sum()), F))
+    assert abs(ser_g - ser_o) <= ci + 1e-12
+    assert not (diff & (ref["margin"] > margin)).any()
+
+
+def test_dft_channel_routing(env):
+    """Handles whose (K, q) has a tensor-core shape run it; the others keep the
+    trellis; the fused form refuses the DFT node; a bad option is refused."""
+    jbp, O, torch = env
+    ctx = jbp.Context(iters=4, channel_node=jbp.CHAN_DFT)
+    try:
+        for K, q, n, want in [(4, 64, 64, jbp.CHAN_DFT), (8, 64, 64, jbp.CHAN_TRELLIS),
+                              (2, 4, 32, jbp.CHAN_TRELLIS), (7, 32, 32, jbp.CHAN_DFT),
+                              (8, 32, 32, jbp.CHAN_DFT), (8, 16, 32, jbp.CHAN_DFT)]:
+            code = I.make_code(n, q)
+            fr = I.make_frames(code, K, 12.0, 2, seed=1)
+            dec = jbp.Decoder(ctx, code, K, fr["sigma2"], fr["perm"])
+            try:
+                assert dec.channel_node == want, (K, q)
+                if want == jbp.CHAN_DFT and dec.fused_ok:
+                    with pytest.raises(jbp.JBPError) as ei:
+                        dec.decode(fr["y"], form=jbp.FORM_FUSED)
+                    assert ei.value.code == jbp.EINVAL
+                out = dec.decode(fr["y"])            # AUTO runs the step form for the DFT node
+                assert out["hat"].shape == (2, K, n)
+            finally:
+                dec.close()
+    finally:
+        ctx.close()
+    with pytest.raises(jbp.JBPError) as ei:
+        jbp.Context(iters=4, channel_node=2)
+    assert ei.value.code == jbp.EINVAL
