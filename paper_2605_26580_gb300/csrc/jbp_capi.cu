@@ -612,10 +612,12 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
     const DftShape dsh = dft_shape(K, q);
     const bool want_dft = ctx->opt.channel_node == JBP_CHAN_DFT && dv == 2 && dc == kDC && dsh.ok &&
                           dsh.smem <= ctx->di.smem_optin;
-    std::vector<unsigned char> dft_tab;
+    std::vector<unsigned char> dft_tab;   // shape tables, then this handle's message offsets
     if (want_dft) {
-        dft_tab.resize(dft_table_bytes(K, q));
+        dft_tab.resize(dft_table_bytes(K, q) + dft_offsets_bytes(K, n));
         dft_build_table(K, q, dft_tab.data());
+        dft_build_offsets(K, q, n, E, use_pos.data(), var_edge.data(),
+                          reinterpret_cast<int32_t*>(dft_tab.data() + dft_table_bytes(K, q)));
     }
     std::vector<uint8_t> gmul((size_t)q * q), gdiv((size_t)q * q);
     std::vector<int> inv(q, 0);
@@ -649,11 +651,11 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
         (rc = dev_alloc(ctx, &h->d_tc_error, (size_t)1, &h->table_bytes)) ||
         (want_slot && (rc = dev_alloc(ctx, &h->d_slot, (size_t)K * E, &h->table_bytes))) ||
         (want_order && (rc = dev_alloc(ctx, &h->d_chk_order, (size_t)K * P, &h->table_bytes))) ||
-        (want_dft && (rc = dev_alloc(ctx, &h->d_dft_tab, dft_table_bytes(K, q), &h->table_bytes)))) {
+        (want_dft && (rc = dev_alloc(ctx, &h->d_dft_tab, dft_tab.size(), &h->table_bytes)))) {
         jbp_destroy(h);
         return rc;
     }
-    if (want_dft) h->dft_bytes = dft_table_bytes(K, q);
+    if (want_dft) h->dft_bytes = dft_tab.size();
     cudaError_t e;
     if ((e = cudaMemcpy(h->d_chk_var, code->chk_var, sizeof(int32_t) * E, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(h->d_chk_coef, code->chk_coef, (size_t)E, cudaMemcpyHostToDevice)) ||

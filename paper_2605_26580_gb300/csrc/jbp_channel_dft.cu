@@ -171,6 +171,14 @@ struct Group {
     static constexpr int PPW = 32 / GL;       // vectors per warp instruction
 };
 
+// largest divisor of n that is at most 8
+__host__ __device__ constexpr int batch_of(int n)
+{
+    int b = 8;
+    while (n % b) --b;
+    return b;
+}
+
 template <int GL>
 __device__ __forceinline__ float group_max(float x)
 {
@@ -193,6 +201,8 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
     static_assert(S.ok, "no tensor-core channel shape for this (K, q)");
     constexpr int L = S.L, W = S.W, NC = S.Nc, CH = S.chunks, U = S.U, R = kDftRows, SP = K * Q;
     constexpr int NW = kDftThreads / 32, GL = Group<Q>::GL, PPW = Group<Q>::PPW;
+    constexpr int IT = R * K / (NW * PPW);   // (row, user) vectors per lane group and tile
+    constexpr int BT = batch_of(IT);         // of which in flight at once
     constexpr uint32_t kA1 = R * Q * 2, kAG = R * W * 2, kB1 = NC * S.KB * 2, kB3 = Q * NC * 2, kA3 = R * NC * 2;
     constexpr uint32_t kChunk = 2 * kB1 + 2 * kB3;
     constexpr int SS = K * Q + 4;   // row stride (floats) of the output stage: rows fall on shifted banks
@@ -277,6 +287,8 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
     const long tiles = (total + R - 1) / R;
     const size_t us = (size_t)g.E * Q, fs = (size_t)K * us, vs = (size_t)K * g.n * Q;
 
+    const int* __restrict__ tab_off = reinterpret_cast<const int*>(tab + (size_t)CH * kChunk + (size_t)L * 8);
+
     for (long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const long r = tile * R + m;
         const long f = r < total ? r / g.n : 0;
@@ -284,21 +296,19 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
         const bool live = r < total && (!active || active[f]);
         GaussTerm gt{};
         int u_lo = 0;
-        if (live) {
-            gt = gauss_term(y[r], K, Q, frame_inv_s2(g, f));
-            u_lo = min(max(gt.ss - W / 2, 0), max(U - W, 0));
-        }
-        // 1. the row's message offsets (this half's users), then mu by lane groups
+        // 1. the row's message offsets (this half's users, from the handle's table),
+        // the G window, then mu by lane groups
         if (half == 0) s_rowf[m] = live ? (int)f : -1;
         if (live) {
             for (int k = half; k < K; k += 2) {
-                const int var = g.use_pos[k * g.n + u];
-                const int e0 = g.var_edge[2 * var], e1 = g.var_edge[2 * var + 1];
-                int* o = s_off + (m * K + k) * 3;
-                o[0] = (int)(k * us) + (e0 >> 2) * 4 * Q + (e0 & 3) * Q;
-                o[1] = (int)(k * us) + (e1 >> 2) * 4 * Q + (e1 & 3) * Q;
-                o[2] = (k * g.n + var) * Q;
+                const int* o = tab_off + ((size_t)u * K + k) * 3;
+                int* so = s_off + (m * K + k) * 3;
+                so[0] = o[0];
+                so[1] = o[1];
+                so[2] = o[2];
             }
+            gt = gauss_term(y[r], K, Q, frame_inv_s2(g, f));
+            u_lo = min(max(gt.ss - W / 2, 0), max(U - W, 0));
         }
         if constexpr (CH > 1) put1();   // forward rows of chunk 0 (the last tile's products are done)
 #pragma unroll
@@ -314,24 +324,39 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
         }
         __syncthreads();
         if constexpr (CH > 1) fetch(CH > 1 ? 1 : 0);
-#pragma unroll 2
-        for (int p = warp * PPW + gsub; p < R * K; p += NW * PPW) {
-            const int mr = p / K, k = p - mr * K;
-            const int fr = s_rowf[mr];
-            float4 v = make_float4(gl == 0 ? 1.0f : 0.0f, 0.0f, 0.0f, 0.0f);
-            if (fr >= 0) {
-                const float* mf = msg + (size_t)fr * fs;
-                const int* o = s_off + (mr * K + k) * 3;
-                v = mul4(reinterpret_cast<const float4*>(mf + o[0])[gl], reinterpret_cast<const float4*>(mf + o[1])[gl]);
+        // mu_j = c2v_e0 * c2v_e1, max 1: BT vectors per lane group in flight
+#pragma unroll 1
+        for (int b0 = 0; b0 < IT; b0 += BT) {
+            float4 va[BT], vb[BT];
+#pragma unroll
+            for (int i = 0; i < BT; ++i) {
+                const int p = (b0 + i) * NW * PPW + warp * PPW + gsub, mr = p / K, k = p - mr * K;
+                const int fr = s_rowf[mr];
+                va[i] = vb[i] = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+                if (fr >= 0) {
+                    const float* mf = msg + (size_t)fr * fs;
+                    const int* o = s_off + (mr * K + k) * 3;
+                    va[i] = reinterpret_cast<const float4*>(mf + o[0])[gl];
+                    vb[i] = reinterpret_cast<const float4*>(mf + o[1])[gl];
+                }
             }
-            const float inv = 1.0f / group_max<GL>(max4(v));
-            const float4 w = scale4(v, inv);
-            *reinterpret_cast<uint2*>(A1 + k * kA1 + tc::tile_off(mr, gl >> 1, Q) + (gl & 1) * 8) =
-                make_uint2(pack_h2(__float2half_rn(w.x), __float2half_rn(w.y)),
-                           pack_h2(__float2half_rn(w.z), __float2half_rn(w.w)));
+#pragma unroll
+            for (int i = 0; i < BT; ++i) {
+                const int p = (b0 + i) * NW * PPW + warp * PPW + gsub, mr = p / K, k = p - mr * K;
+                float4 v = mul4(va[i], vb[i]);
+                if (s_rowf[mr] < 0) v = make_float4(gl == 0 ? 1.0f : 0.0f, 0.0f, 0.0f, 0.0f);
+                const float inv = 1.0f / group_max<GL>(max4(v));
+                const float4 w = scale4(v, inv);
+                *reinterpret_cast<uint2*>(A1 + k * kA1 + tc::tile_off(mr, gl >> 1, Q) + (gl & 1) * 8) =
+                    make_uint2(pack_h2(__float2half_rn(w.x), __float2half_rn(w.y)),
+                               pack_h2(__float2half_rn(w.z), __float2half_rn(w.w)));
+            }
         }
 
-        // 2. chunks of the spectrum
+        // 2. chunks of the spectrum.  Per chunk c: wait for the forward products of c
+        // (and the inverse products of c-1); every thread takes its share of the
+        // chunk's spectra into registers; the forward products of c+1 are issued and
+        // run while the threads form the X_k of chunk c; then the inverse products of c.
         tc::proxy_fence();
         tc::fence_before();
         __syncthreads();
@@ -343,21 +368,18 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
         float inv_dc[K + 1];
 #pragma unroll 1
         for (int c = 0; c < CH; ++c) {
-            // forward products of chunk c (and the inverse products of chunk c-1) done
             if (!tc::wait_bounded(mbar, phase, g.tc_error)) {
                 ok = false;
                 break;
             }
             phase ^= 1;
             tc::fence_after();
-            if constexpr (CH > 1) {
-                put3();                          // inverse rows of chunk c
-                fetch3((c + 1) % CH);
-                if (c + 1 < CH) {
-                    put1();                      // forward rows of chunk c + 1
-                    fetch((c + 2) % CH);
-                }
-            }
+            uint32_t spec[K + 1][NC / 16][8];
+#pragma unroll
+            for (int j = 0; j <= K; ++j)
+#pragma unroll
+                for (int q8 = 0; q8 < NC / 16; ++q8)
+                    tc::tmem_ld8_nowait(trow + SP + j * NC + half * (NC / 2) + q8 * 8, spec[j][q8]);
             if (c == 0) {   // DC terms (real, >= 1): every spectrum is scaled to DC 1
                 uint32_t raw[K + 1][8];
 #pragma unroll
@@ -366,13 +388,25 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
 #pragma unroll
                 for (int j = 0; j <= K; ++j) inv_dc[j] = 1.0f / __uint_as_float(raw[j][0]);
             }
-#pragma unroll 1
+            tc::ld_wait();
+            if constexpr (CH > 1) {
+                put3();                          // inverse rows of chunk c
+                fetch3((c + 1) % CH);
+                if (c + 1 < CH) {
+                    put1();                      // forward rows of chunk c + 1
+                    fetch((c + 2) % CH);
+                }
+            }
+            tc::fence_before();
+            tc::proxy_fence();
+            __syncthreads();
+            if (t == 0 && c + 1 < CH) {
+                tc::fence_after();
+                issue_forward<Q, K, Sh>(tmem, sA1, sAG, sB1);
+            }
+#pragma unroll
             for (int cq = 0; cq < NC / 16; ++cq) {
                 const int cg = half * (NC / 16) + cq;   // group of 8 columns = 4 frequency pairs
-                uint32_t raw[K + 1][8];
-#pragma unroll
-                for (int j = 0; j <= K; ++j) tc::tmem_ld8_nowait(trow + SP + j * NC + cg * 8, raw[j]);
-                tc::ld_wait();
                 float xs[K][8];
 #pragma unroll
                 for (int pp = 0; pp < 4; ++pp) {
@@ -380,8 +414,8 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
                     Cx mh[K], X[K], gh;
                     if (pg == 0) {   // (DC, Nyquist), both real
 #pragma unroll
-                        for (int j = 0; j < K; ++j) mh[j] = {__uint_as_float(raw[j][1]) * inv_dc[j], 0.0f};
-                        gh = {__uint_as_float(raw[K][1]) * inv_dc[K] * ((u_lo & 1) ? -1.0f : 1.0f), 0.0f};
+                        for (int j = 0; j < K; ++j) mh[j] = {__uint_as_float(spec[j][cq][1]) * inv_dc[j], 0.0f};
+                        gh = {__uint_as_float(spec[K][cq][1]) * inv_dc[K] * ((u_lo & 1) ? -1.0f : 1.0f), 0.0f};
                         leave_one_out<K>(mh, gh, X);
 #pragma unroll
                         for (int k = 0; k < K; ++k) {
@@ -391,10 +425,10 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
                     } else {
 #pragma unroll
                         for (int j = 0; j < K; ++j)
-                            mh[j] = {__uint_as_float(raw[j][2 * pp]) * inv_dc[j],
-                                     __uint_as_float(raw[j][2 * pp + 1]) * inv_dc[j]};
-                        const Cx gw = {__uint_as_float(raw[K][2 * pp]) * inv_dc[K],
-                                       __uint_as_float(raw[K][2 * pp + 1]) * inv_dc[K]};
+                            mh[j] = {__uint_as_float(spec[j][cq][2 * pp]) * inv_dc[j],
+                                     __uint_as_float(spec[j][cq][2 * pp + 1]) * inv_dc[j]};
+                        const Cx gw = {__uint_as_float(spec[K][cq][2 * pp]) * inv_dc[K],
+                                       __uint_as_float(spec[K][cq][2 * pp + 1]) * inv_dc[K]};
                         const float2 w = TW[(pg * u_lo) % L];   // window offset: G^ = Gw^ e^{-2 pi i f u_lo / L}
                         gh = {gw.r * w.x + gw.i * w.y, gw.i * w.x - gw.r * w.y};
                         leave_one_out<K>(mh, gh, X);
@@ -419,7 +453,6 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
             if (t == 0) {
                 tc::fence_after();
                 issue_inverse<Q, K, Sh>(tmem, sA3, sB3, c);
-                if (c + 1 < CH) issue_forward<Q, K, Sh>(tmem, sA1, sAG, sB1);
                 tc::mma_commit(mbar);
             }
         }
@@ -465,29 +498,40 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
         s_weak[half][m] = weak ? 1 : 0;
         tc::fence_before();
         __syncthreads();
-#pragma unroll 2
-        for (int p = warp * PPW + gsub; p < R * K; p += NW * PPW) {
-            const int mr = p / K, k = p - mr * K;
-            const int fr = s_rowf[mr];
-            const bool emit = fr >= 0 && !(s_weak[0][mr] | s_weak[1][mr]);
-            const int* o = s_off + (mr * K + k) * 3;
-            float* mf = msg + (size_t)(fr >= 0 ? fr : 0) * fs;
-            const float4 ov = reinterpret_cast<const float4*>(stage + mr * SS + k * Q)[gl];
-            float4 c0 = make_float4(1.0f, 1.0f, 1.0f, 1.0f), c1 = c0;
-            if (emit) {
-                c0 = reinterpret_cast<const float4*>(mf + o[0])[gl];
-                c1 = reinterpret_cast<const float4*>(mf + o[1])[gl];
+#pragma unroll 1
+        for (int b0 = 0; b0 < IT; b0 += BT) {
+            float4 c0[BT], c1[BT];
+#pragma unroll
+            for (int i = 0; i < BT; ++i) {
+                const int p = (b0 + i) * NW * PPW + warp * PPW + gsub, mr = p / K, k = p - mr * K;
+                const int fr = s_rowf[mr];
+                c0[i] = c1[i] = make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+                if (fr >= 0 && !(s_weak[0][mr] | s_weak[1][mr])) {
+                    const float* mf = msg + (size_t)fr * fs;
+                    const int* o = s_off + (mr * K + k) * 3;
+                    c0[i] = reinterpret_cast<const float4*>(mf + o[0])[gl];
+                    c1[i] = reinterpret_cast<const float4*>(mf + o[1])[gl];
+                }
             }
-            // v2c of each edge = ch2v * c2v of the other edge, rescaled to max 1
-            const float4 v0 = mul4(ov, c1), v1 = mul4(ov, c0);
-            const float i0 = 1.0f / group_max<GL>(max4(v0)), i1 = 1.0f / group_max<GL>(max4(v1));
-            if (emit) {
-                reinterpret_cast<float4*>(ch2v + (size_t)fr * vs + o[2])[gl] = ov;
-                reinterpret_cast<float4*>(mf + o[0])[gl] = scale4(v0, i0);
-                reinterpret_cast<float4*>(mf + o[1])[gl] = scale4(v1, i1);
-            } else if (fr >= 0 && k == 0 && gl == 0) {
-                ch2v[(size_t)fr * vs + o[2]] = __int_as_float(0x7fc00000);
-                if (g.log_fallbacks) atomicAdd(g.log_fallbacks, 1ull);
+#pragma unroll
+            for (int i = 0; i < BT; ++i) {
+                const int p = (b0 + i) * NW * PPW + warp * PPW + gsub, mr = p / K, k = p - mr * K;
+                const int fr = s_rowf[mr];
+                const bool emit = fr >= 0 && !(s_weak[0][mr] | s_weak[1][mr]);
+                const int* o = s_off + (mr * K + k) * 3;
+                float* mf = msg + (size_t)(fr >= 0 ? fr : 0) * fs;
+                const float4 ov = reinterpret_cast<const float4*>(stage + mr * SS + k * Q)[gl];
+                // v2c of each edge = ch2v * c2v of the other edge, rescaled to max 1
+                const float4 v0 = mul4(ov, c1[i]), v1 = mul4(ov, c0[i]);
+                const float i0 = 1.0f / group_max<GL>(max4(v0)), i1 = 1.0f / group_max<GL>(max4(v1));
+                if (emit) {
+                    reinterpret_cast<float4*>(ch2v + (size_t)fr * vs + o[2])[gl] = ov;
+                    reinterpret_cast<float4*>(mf + o[0])[gl] = scale4(v0, i0);
+                    reinterpret_cast<float4*>(mf + o[1])[gl] = scale4(v1, i1);
+                } else if (fr >= 0 && k == 0 && gl == 0) {
+                    ch2v[(size_t)fr * vs + o[2]] = __int_as_float(0x7fc00000);
+                    if (g.log_fallbacks) atomicAdd(g.log_fallbacks, 1ull);
+                }
             }
         }
         __syncthreads();   // the stage and the offsets are read before the next tile overwrites them
@@ -555,6 +599,21 @@ size_t dft_table_bytes(int K, int Q)
     const DftShape S = dft_shape(K, Q);
     if (!S.ok) return 0;
     return (size_t)S.chunks * (4ull * S.Nc * S.KB + 4ull * Q * S.Nc) + 8ull * S.L;
+}
+
+size_t dft_offsets_bytes(int K, int n) { return 12ull * K * n; }
+
+void dft_build_offsets(int K, int Q, int n, int E, const int32_t* use_pos, const int32_t* var_edge, int32_t* out)
+{
+    for (int u = 0; u < n; ++u)
+        for (int k = 0; k < K; ++k) {
+            const int var = use_pos[k * n + u];
+            const int e0 = var_edge[2 * var], e1 = var_edge[2 * var + 1];
+            int32_t* o = out + ((size_t)u * K + k) * 3;
+            o[0] = k * E * Q + (e0 >> 2) * 4 * Q + (e0 & 3) * Q;
+            o[1] = k * E * Q + (e1 >> 2) * 4 * Q + (e1 & 3) * Q;
+            o[2] = (k * n + var) * Q;
+        }
 }
 
 // Forward row n of the spectrum (pair p = n/2; n even: real part, odd: imaginary

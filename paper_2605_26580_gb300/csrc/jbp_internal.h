@@ -66,7 +66,8 @@ __host__ __device__ constexpr DftShape dft_shape(int K, int Q)
     // mu tiles + G window (one FP16 term each) + twiddles + message offsets + alignment slack
     const int fixed = K * kDftRows * Q * 2 + kDftRows * s.W * 2 + s.L * 8 + kDftRows * K * 12 + 1024;
     for (int nc = 128; nc >= 16; nc /= 2) {
-        if (s.L % nc || K * Q + (K + 1) * nc > 512) continue;
+        // tensor-memory columns; a thread holds (K + 1) nc / 2 spectral values in registers
+        if (s.L % nc || K * Q + (K + 1) * nc > 512 || (K + 1) * nc > 192) continue;
         // forward chunk (hi, lo) + inverse chunk (hi, lo) + X tiles (hi, lo)
         const int sm = fixed + nc * s.KB * 4 + Q * nc * 4 + K * kDftRows * nc * 4;
         if (sm > kDftSmemMax) continue;
@@ -86,6 +87,11 @@ __host__ __device__ constexpr DftShape dft_shape(int K, int Q)
 // lo) in tensor-core tile order, then L twiddles (cos, sin)(2 pi m / L).
 size_t dft_table_bytes(int K, int Q);
 void dft_build_table(int K, int Q, unsigned char* out);
+// Per-handle part that follows those tables: for every channel use u and user k
+// (index u*K + k) three int32 offsets, in floats: the variable's two c2v messages
+// within a frame's msg block and its channel message within the frame's ch2v.
+size_t dft_offsets_bytes(int K, int n);
+void dft_build_offsets(int K, int Q, int n, int E, const int32_t* use_pos, const int32_t* var_edge, int32_t* out);
 // Launches the tensor-core kernel, then the FP32 trellis on the channel uses it
 // could not resolve (launch_channel_fix).
 cudaError_t launch_channel_dft(const Graph& g, const DeviceInfo& di, int F, const float* y, float* msg, float* ch2v,
