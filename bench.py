@@ -240,6 +240,8 @@ def main() -> None:
     ap.add_argument("--variants", default="0,d0,3,1,2",
                     help="precision workload: check-node variants to run (dP: with the DFT channel node)")
     ap.add_argument("--channel-legs", type=int, default=1, help="precision workload: time the channel node alone")
+    ap.add_argument("--channel-node", default="trellis", choices=["trellis", "dft"],
+                    help="uneven and serving workloads: channel node (dft: tensor-core variant where it applies)")
     ap.add_argument("--channel-frames", type=int, default=4096, help="precision workload: frames of that leg")
     ap.add_argument("--oracle-sample", type=int, default=16, help="precision workload: oracle frames")
     args = ap.parse_args()
@@ -672,6 +674,10 @@ def _waves(parts, budget):
     return waves
 
 
+def _channel_node(jbp, args):
+    return jbp.CHAN_DFT if args.channel_node == "dft" else jbp.CHAN_TRELLIS
+
+
 def wl_uneven(args):
     """100,000 frames with K ~ U{2..8}, n ~ U{128,...,2048}, q ~ U{16,64}, SNR ~ U[8,16] dB
     (per frame), 50 iterations with per-frame early stop.  Classes of equal
@@ -680,7 +686,7 @@ def wl_uneven(args):
     jbp, torch, dev = _ctx_dev()
     F = int(100000 * args.frac)
     classes, snr = _uneven_classes(F, 404)
-    ctx = jbp.Context(iters=50, early_stop=True)
+    ctx = jbp.Context(iters=50, early_stop=True, channel_node=_channel_node(jbp, args))
     t0 = time.perf_counter()
     parts = _uneven_inputs(jbp, torch, dev, ctx, classes, snr)
     t_gen = time.perf_counter() - t0
@@ -711,6 +717,7 @@ def wl_uneven(args):
            "config": {"workload": "uneven batch: %d frames, K~U{2..8}, n~U{128,256,512,1024,2048}, q~U{16,64}, "
                                   "SNR~U[8,16] dB per frame, 50 iterations with per-frame early stop" % F,
                       "classes": len(parts), "waves": len(waves), "wave_budget_gb": budget / 1e9,
+                      "channel_node": args.channel_node,
                       "graph": "one CUDA graph per wave (jbp_decode_many replay)"},
            "dtype": "f32", "s_per_batch": sec, "ser": ser_num / ser_den, "mean_iters": iters / F,
            "frames_fused_form": fused_frames, "frames_step_form": F - fused_frames,
@@ -735,7 +742,8 @@ def wl_serve(args):
     rates = [250, 500, 1000, 20000, 50000, 100000, 200000]
     results = []
     for lam in rates:
-        ctx = jbp.Context(iters=50, early_stop=True, mem_budget_bytes=int(64e9))
+        ctx = jbp.Context(iters=50, early_stop=True, mem_budget_bytes=int(64e9),
+                          channel_node=_channel_node(jbp, args))
         parts = _uneven_inputs(jbp, torch, dev, ctx, classes, snr)
         reqs = []
         for p in parts:

@@ -74,7 +74,7 @@ typedef enum { JBP_PREC_FP32 = 0, JBP_PREC_BF16X2 = 1, JBP_PREC_BF16 = 2, JBP_PR
  * (FP16 hi/lo operand terms, FP32 accumulation).  Its error is absolute, a
  * small fraction of each message's maximum (about 1e-5; the tests bound it),
  * rather than relative per entry, so entries far below the maximum are not
- * resolved.  It runs in the step form where K >= 2, q >= 16 and K q <= 256;
+ * resolved.  It runs in the step form for 2 <= K <= 8 and q = 16, 32, 64;
  * other handles of the context keep the trellis (jbp_query_channel tells
  * which). */
 typedef enum { JBP_CHAN_TRELLIS = 0, JBP_CHAN_DFT = 1 } jbp_channel_node;

@@ -117,7 +117,7 @@ template <int Q, int K, class Sh>
 __device__ __forceinline__ void issue_forward(uint32_t tmem, uint32_t sA1, uint32_t sAG, uint32_t sB1)
 {
     constexpr DftShape S = Sh::v;
-    constexpr int NC = S.Nc, KB = S.KB, W = S.W, SP = K * Q;
+    constexpr int NC = S.Nc, KB = S.KB, W = S.W, SP = S.KG * Q;
     constexpr uint32_t kA1 = kDftRows * Q * 2, kB1 = NC * KB * 2;
     constexpr uint32_t id = tc::idesc_f16(kDftRows, NC, false);
 #pragma unroll
@@ -141,16 +141,17 @@ __device__ __forceinline__ void issue_forward(uint32_t tmem, uint32_t sA1, uint3
         }
 }
 
-// Inverse products of chunk c (one thread): X_k against the inverse rows,
-// accumulated into columns k q.
+// Inverse products of chunk c (one thread): X of the pass's user slot k < kn
+// against the inverse rows, accumulated into columns k q.
 template <int Q, int K, class Sh>
-__device__ __forceinline__ void issue_inverse(uint32_t tmem, uint32_t sA3, uint32_t sB3, int c)
+__device__ __forceinline__ void issue_inverse(uint32_t tmem, uint32_t sA3, uint32_t sB3, int c, int kn)
 {
     constexpr int NC = Sh::v.Nc;
     constexpr uint32_t kA3 = kDftRows * NC * 2, kB3 = Q * NC * 2;
     constexpr uint32_t id = tc::idesc_f16(kDftRows, Q, false);
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
+    for (int k = 0; k < Sh::v.KG; ++k) {
+        if (k >= kn) break;
         int acc = c > 0;
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
@@ -199,19 +200,21 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
     using Sh = ShapeOf<Q, K>;
     constexpr DftShape S = Sh::v;
     static_assert(S.ok, "no tensor-core channel shape for this (K, q)");
-    constexpr int L = S.L, W = S.W, NC = S.Nc, CH = S.chunks, U = S.U, R = kDftRows, SP = K * Q;
+    constexpr int L = S.L, W = S.W, NC = S.Nc, CH = S.chunks, U = S.U, R = kDftRows;
+    constexpr int KG = S.KG, NP = S.NP, SP = KG * Q;   // users per pass, passes, first spectrum column
     constexpr int NW = kDftThreads / 32, GL = Group<Q>::GL, PPW = Group<Q>::PPW;
     constexpr int IT = R * K / (NW * PPW);   // (row, user) vectors per lane group and tile
     constexpr int BT = batch_of(IT);         // of which in flight at once
     constexpr uint32_t kA1 = R * Q * 2, kAG = R * W * 2, kB1 = NC * S.KB * 2, kB3 = Q * NC * 2, kA3 = R * NC * 2;
     constexpr uint32_t kChunk = 2 * kB1 + 2 * kB3;
     constexpr int SS = K * Q + 4;   // row stride (floats) of the output stage: rows fall on shifted banks
-    static_assert(R * SS * 4 <= K * kA1 + kAG + 2 * K * kA3, "output stage exceeds the operand tiles it reuses");
+    static_assert(NP > 1 || R * SS * 4 <= K * kA1 + kAG + 2 * K * kA3,
+                  "output stage exceeds the operand tiles it reuses");
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* A1 = smem;                 // [K][R x q]           mu_j
     unsigned char* AG = A1 + K * kA1;         // [R x W]              G window
-    unsigned char* A3 = AG + kAG;             // [K][hi, lo][R x Nc]  X_k
-    unsigned char* BC = A3 + 2 * K * kA3;     // forward rows (hi, lo), inverse rows (hi, lo) of a chunk
+    unsigned char* A3 = AG + kAG;             // [KG][hi, lo][R x Nc] X_k of the pass's users
+    unsigned char* BC = A3 + 2 * KG * kA3;    // forward rows (hi, lo), inverse rows (hi, lo) of a chunk
     float2* TW = reinterpret_cast<float2*>(BC + kChunk);         // [L] (cos, sin)(2 pi m / L)
     int* s_off = reinterpret_cast<int*>(TW + L);                 // [R][K][3] offsets of e0, e1 (msg), ch2v
     float* stage = reinterpret_cast<float*>(smem);               // [R][SS] messages (reuses A1, AG, A3)
@@ -357,6 +360,17 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
         // (and the inverse products of c-1); every thread takes its share of the
         // chunk's spectra into registers; the forward products of c+1 are issued and
         // run while the threads form the X_k of chunk c; then the inverse products of c.
+        float inv_dc[K + 1];
+        bool weak = false;   // some user's peak below kMinPeak (this thread's users, all passes)
+#pragma unroll
+        for (int pass = 0; pass < NP; ++pass) {
+        const int k0 = pass * KG, kn = min(KG, K - k0);
+        if (pass > 0) {
+            if constexpr (CH > 1) {   // forward rows of chunk 0 (the previous pass's products are done)
+                put1();
+                fetch(1);
+            }
+        }
         tc::proxy_fence();
         tc::fence_before();
         __syncthreads();
@@ -365,7 +379,6 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
             issue_forward<Q, K, Sh>(tmem, sA1, sAG, sB1);
             tc::mma_commit(mbar);
         }
-        float inv_dc[K + 1];
 #pragma unroll 1
         for (int c = 0; c < CH; ++c) {
             if (!tc::wait_bounded(mbar, phase, g.tc_error)) {
@@ -407,7 +420,7 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
 #pragma unroll
             for (int cq = 0; cq < NC / 16; ++cq) {
                 const int cg = half * (NC / 16) + cq;   // group of 8 columns = 4 frequency pairs
-                float xs[K][8];
+                float xs[KG][8];
 #pragma unroll
                 for (int pp = 0; pp < 4; ++pp) {
                     const int pg = c * (NC / 2) + cg * 4 + pp;
@@ -418,9 +431,9 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
                         gh = {__uint_as_float(spec[K][cq][1]) * inv_dc[K] * ((u_lo & 1) ? -1.0f : 1.0f), 0.0f};
                         leave_one_out<K>(mh, gh, X);
 #pragma unroll
-                        for (int k = 0; k < K; ++k) {
+                        for (int k = 0; k < KG; ++k) {
                             xs[k][0] = 1.0f;
-                            xs[k][1] = X[k].r;
+                            xs[k][1] = k0 + k < K ? X[k0 + k].r : 0.0f;
                         }
                     } else {
 #pragma unroll
@@ -433,14 +446,14 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
                         gh = {gw.r * w.x + gw.i * w.y, gw.i * w.x - gw.r * w.y};
                         leave_one_out<K>(mh, gh, X);
 #pragma unroll
-                        for (int k = 0; k < K; ++k) {
-                            xs[k][2 * pp] = X[k].r;
-                            xs[k][2 * pp + 1] = X[k].i;
+                        for (int k = 0; k < KG; ++k) {
+                            xs[k][2 * pp] = k0 + k < K ? X[k0 + k].r : 0.0f;
+                            xs[k][2 * pp + 1] = k0 + k < K ? X[k0 + k].i : 0.0f;
                         }
                     }
                 }
 #pragma unroll
-                for (int k = 0; k < K; ++k) {
+                for (int k = 0; k < KG; ++k) {
                     uint4 hi, lo;
                     split8(xs[k], hi, lo);
                     *reinterpret_cast<uint4*>(A3 + (2 * k) * kA3 + tc::tile_off(m, cg, NC)) = hi;
@@ -452,7 +465,7 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
             __syncthreads();
             if (t == 0) {
                 tc::fence_after();
-                issue_inverse<Q, K, Sh>(tmem, sA3, sB3, c);
+                issue_inverse<Q, K, Sh>(tmem, sA3, sB3, c, kn);
                 tc::mma_commit(mbar);
             }
         }
@@ -463,6 +476,38 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
         }
         phase ^= 1;
         tc::fence_after();
+        if constexpr (NP > 1) {
+            // this pass's messages straight to ch2v (row threads); the in-place v2c
+            // waits until every pass has passed the resolution test
+#pragma unroll 1
+            for (int k = k0 + half; k < k0 + kn; k += 2) {
+                float mx = -INFINITY;
+#pragma unroll
+                for (int c16 = 0; c16 < Q / 16; ++c16) {
+                    float o[16];
+                    tc::tmem_ld16(trow + (k - k0) * Q + c16 * 16, o);
+                    mx = fmaxf(mx, vmax(o));
+                }
+                weak |= !(mx >= kMinPeak * (float)L);
+                const float inv = 1.0f / mx;
+                float* dst = ch2v + f * vs + (live ? s_off[(m * K + k) * 3 + 2] : 0);
+#pragma unroll
+                for (int c16 = 0; c16 < Q / 16; ++c16) {
+                    float o[16];
+                    tc::tmem_ld16(trow + (k - k0) * Q + c16 * 16, o);
+                    if (live)
+#pragma unroll
+                        for (int a = 0; a < 16; a += 4)
+                            *reinterpret_cast<float4*>(dst + c16 * 16 + a) =
+                                make_float4(fmaxf(o[a] * inv, kRelFloor), fmaxf(o[a + 1] * inv, kRelFloor),
+                                            fmaxf(o[a + 2] * inv, kRelFloor), fmaxf(o[a + 3] * inv, kRelFloor));
+                }
+            }
+            tc::fence_before();
+            __syncthreads();   // accumulators read before the next pass overwrites them
+        }
+        }   // passes
+        if (!ok) break;
 
         // 3. messages.  With every spectrum scaled to DC 1 the accumulated value is
         // L times the probability mass sum_s E(s) G(s + a) of normalised sequences,
@@ -471,7 +516,7 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
         // is written but a NaN in the first entry of user 0's channel message,
         // which the trellis pass looks for.  Each thread normalises its row's
         // messages into the stage; lane groups then write them out.
-        bool weak = false;
+        if constexpr (NP == 1) {
 #pragma unroll 1
         for (int k = half; k < K; k += 2) {
             float mx = -INFINITY;
@@ -531,6 +576,44 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
                 } else if (fr >= 0 && k == 0 && gl == 0) {
                     ch2v[(size_t)fr * vs + o[2]] = __int_as_float(0x7fc00000);
                     if (g.log_fallbacks) atomicAdd(g.log_fallbacks, 1ull);
+                }
+            }
+        }
+        } else {
+            s_weak[half][m] = weak ? 1 : 0;
+            __syncthreads();
+#pragma unroll 1
+            for (int b0 = 0; b0 < IT; b0 += BT) {
+                float4 c0[BT], c1[BT], ov[BT];
+#pragma unroll
+                for (int i = 0; i < BT; ++i) {
+                    const int p = (b0 + i) * NW * PPW + warp * PPW + gsub, mr = p / K, k = p - mr * K;
+                    const int fr = s_rowf[mr];
+                    c0[i] = c1[i] = ov[i] = make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+                    if (fr >= 0 && !(s_weak[0][mr] | s_weak[1][mr])) {
+                        const float* mf = msg + (size_t)fr * fs;
+                        const int* o = s_off + (mr * K + k) * 3;
+                        c0[i] = reinterpret_cast<const float4*>(mf + o[0])[gl];
+                        c1[i] = reinterpret_cast<const float4*>(mf + o[1])[gl];
+                        ov[i] = reinterpret_cast<const float4*>(ch2v + (size_t)fr * vs + o[2])[gl];
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < BT; ++i) {
+                    const int p = (b0 + i) * NW * PPW + warp * PPW + gsub, mr = p / K, k = p - mr * K;
+                    const int fr = s_rowf[mr];
+                    const bool emit = fr >= 0 && !(s_weak[0][mr] | s_weak[1][mr]);
+                    const int* o = s_off + (mr * K + k) * 3;
+                    float* mf = msg + (size_t)(fr >= 0 ? fr : 0) * fs;
+                    const float4 v0 = mul4(ov[i], c1[i]), v1 = mul4(ov[i], c0[i]);
+                    const float i0 = 1.0f / group_max<GL>(max4(v0)), i1 = 1.0f / group_max<GL>(max4(v1));
+                    if (emit) {
+                        reinterpret_cast<float4*>(mf + o[0])[gl] = scale4(v0, i0);
+                        reinterpret_cast<float4*>(mf + o[1])[gl] = scale4(v1, i1);
+                    } else if (fr >= 0 && k == 0 && gl == 0) {
+                        ch2v[(size_t)fr * vs + o[2]] = __int_as_float(0x7fc00000);
+                        if (g.log_fallbacks) atomicAdd(g.log_fallbacks, 1ull);
+                    }
                 }
             }
         }

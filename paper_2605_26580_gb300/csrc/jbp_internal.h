@@ -45,13 +45,14 @@ cudaError_t launch_check_tc(const Graph& g, const DeviceInfo& di, int F, float* 
 // the Gaussian score G that is transformed (the rest is below the message floor
 // for W = L, and below exp(-2 (W/2 - 1)^2 / sigma2) of the maximum otherwise);
 // KB = max(q, W) the inner dimension of the forward DFT matrix; Nc the real
-// spectral columns per chunk.  Built where K >= 2, q >= 16 and K q <= 256 (the
-// inverse-DFT accumulators, K q tensor-memory columns, stay resident).
+// spectral columns per chunk.  The inverse-DFT accumulators of KG = min(K, 256/q)
+// users stay in tensor memory; with K > KG the users go in NP passes, each
+// recomputing the forward spectra.  Built for 2 <= K <= 8 and q = 16, 32, 64.
 constexpr int kDftRows = 128;
 constexpr int kDftThreads = 256;
 constexpr int kDftSmemMax = 226 * 1024;   // dynamic part; the kernel's static part is under 1 KB
 struct DftShape {
-    int U, L, W, KB, Nc, chunks, tmem_cols, smem;
+    int U, L, W, KB, Nc, chunks, tmem_cols, smem, KG, NP;
     bool ok;
 };
 __host__ __device__ constexpr DftShape dft_shape(int K, int Q)
@@ -62,14 +63,16 @@ __host__ __device__ constexpr DftShape dft_shape(int K, int Q)
     s.W = s.L < 128 ? s.L : 128;
     s.KB = Q > s.W ? Q : s.W;
     s.ok = false;
-    if (Q < 16 || Q > 64 || K < 2 || K * Q > 256) return s;
+    if (Q < 16 || Q > 64 || (Q & (Q - 1)) || K < 2 || K > 8) return s;
+    s.KG = K < 256 / Q ? K : 256 / Q;
+    s.NP = (K + s.KG - 1) / s.KG;
     // mu tiles + G window (one FP16 term each) + twiddles + message offsets + alignment slack
     const int fixed = K * kDftRows * Q * 2 + kDftRows * s.W * 2 + s.L * 8 + kDftRows * K * 12 + 1024;
     for (int nc = 128; nc >= 16; nc /= 2) {
         // tensor-memory columns; a thread holds (K + 1) nc / 2 spectral values in registers
-        if (s.L % nc || K * Q + (K + 1) * nc > 512 || (K + 1) * nc > 192) continue;
-        // forward chunk (hi, lo) + inverse chunk (hi, lo) + X tiles (hi, lo)
-        const int sm = fixed + nc * s.KB * 4 + Q * nc * 4 + K * kDftRows * nc * 4;
+        if (s.L % nc || s.KG * Q + (K + 1) * nc > 512 || (K + 1) * nc > 192) continue;
+        // forward chunk (hi, lo) + inverse chunk (hi, lo) + X tiles of one pass (hi, lo)
+        const int sm = fixed + nc * s.KB * 4 + Q * nc * 4 + s.KG * kDftRows * nc * 4;
         if (sm > kDftSmemMax) continue;
         s.Nc = nc;
         s.smem = sm;
@@ -78,7 +81,7 @@ __host__ __device__ constexpr DftShape dft_shape(int K, int Q)
     }
     if (!s.ok) return s;
     s.chunks = s.L / s.Nc;
-    const int need = K * Q + (K + 1) * s.Nc;
+    const int need = s.KG * Q + (K + 1) * s.Nc;
     s.tmem_cols = need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
     return s;
 }

@@ -65,6 +65,8 @@ def _step_channel(jbp, torch, dec, fr, c2v_lin, K, n, q):
 DFT_CASES = [
     (2, 16, 64, 7), (4, 16, 256, 5), (3, 32, 64, 9), (4, 64, 120, 3), (7, 32, 32, 11),
     (8, 16, 64, 5), (5, 32, 40, 7), (2, 64, 24, 3), (3, 64, 64, 4),
+    (8, 32, 32, 5),                      # K q = 256: the last shape with one pass
+    (5, 64, 40, 5), (8, 64, 48, 3),      # K q > 256: users in two passes
 ]
 
 
@@ -166,8 +168,9 @@ def test_dft_channel_routing(env):
     jbp, O, torch = env
     ctx = jbp.Context(iters=4, channel_node=jbp.CHAN_DFT)
     try:
-        for K, q, n, want in [(4, 64, 64, jbp.CHAN_DFT), (8, 64, 64, jbp.CHAN_TRELLIS),
-                              (2, 4, 32, jbp.CHAN_TRELLIS), (7, 32, 32, jbp.CHAN_DFT),
+        for K, q, n, want in [(4, 64, 64, jbp.CHAN_DFT), (8, 64, 64, jbp.CHAN_DFT),
+                              (2, 4, 32, jbp.CHAN_TRELLIS), (1, 64, 32, jbp.CHAN_TRELLIS),
+                              (9, 16, 32, jbp.CHAN_TRELLIS), (7, 32, 32, jbp.CHAN_DFT),
                               (8, 32, 32, jbp.CHAN_DFT), (8, 16, 32, jbp.CHAN_DFT)]:
             code = I.make_code(n, q)
             fr = I.make_frames(code, K, 12.0, 2, seed=1)
