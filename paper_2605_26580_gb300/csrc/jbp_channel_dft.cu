@@ -51,30 +51,28 @@
 namespace jbp {
 namespace {
 
-__device__ __forceinline__ uint32_t pack_h2(__half a, __half b)
-{
-    return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
-}
+// two values rounded to FP16 in one packed conversion (first in the low half)
+__device__ __forceinline__ uint32_t h2bits(__half2 h) { return *reinterpret_cast<const uint32_t*>(&h); }
 
 // 8 values as one 16-byte core-matrix row of FP16 hi terms and one of lo terms
 __device__ __forceinline__ void split8(const float (&v)[8], uint4& hi, uint4& lo)
 {
-    __half h[8], l[8];
+    uint32_t h[4], l[4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        h[i] = __float2half_rn(v[i]);
-        l[i] = __float2half_rn(v[i] - __half2float(h[i]));
+    for (int i = 0; i < 4; ++i) {
+        const __half2 hh = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+        const float2 back = __half22float2(hh);
+        h[i] = h2bits(hh);
+        l[i] = h2bits(__floats2half2_rn(v[2 * i] - back.x, v[2 * i + 1] - back.y));
     }
-    hi = make_uint4(pack_h2(h[0], h[1]), pack_h2(h[2], h[3]), pack_h2(h[4], h[5]), pack_h2(h[6], h[7]));
-    lo = make_uint4(pack_h2(l[0], l[1]), pack_h2(l[2], l[3]), pack_h2(l[4], l[5]), pack_h2(l[6], l[7]));
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 __device__ __forceinline__ uint4 pack8(const float (&v)[8])
 {
-    return make_uint4(pack_h2(__float2half_rn(v[0]), __float2half_rn(v[1])),
-                      pack_h2(__float2half_rn(v[2]), __float2half_rn(v[3])),
-                      pack_h2(__float2half_rn(v[4]), __float2half_rn(v[5])),
-                      pack_h2(__float2half_rn(v[6]), __float2half_rn(v[7])));
+    return make_uint4(h2bits(__floats2half2_rn(v[0], v[1])), h2bits(__floats2half2_rn(v[2], v[3])),
+                      h2bits(__floats2half2_rn(v[4], v[5])), h2bits(__floats2half2_rn(v[6], v[7])));
 }
 
 struct Cx {
@@ -351,8 +349,7 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
                 const float inv = 1.0f / group_max<GL>(max4(v));
                 const float4 w = scale4(v, inv);
                 *reinterpret_cast<uint2*>(A1 + k * kA1 + tc::tile_off(mr, gl >> 1, Q) + (gl & 1) * 8) =
-                    make_uint2(pack_h2(__float2half_rn(w.x), __float2half_rn(w.y)),
-                               pack_h2(__float2half_rn(w.z), __float2half_rn(w.w)));
+                    make_uint2(h2bits(__floats2half2_rn(w.x, w.y)), h2bits(__floats2half2_rn(w.z, w.w)));
             }
         }
 
@@ -381,10 +378,8 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
         }
 #pragma unroll 1
         for (int c = 0; c < CH; ++c) {
-            if (!tc::wait_bounded(mbar, phase, g.tc_error)) {
-                ok = false;
-                break;
-            }
+            // each thread waits on its own; the barrier below settles an expiry for all
+            const bool done = tc::spin_wait(mbar, phase);
             phase ^= 1;
             tc::fence_after();
             uint32_t spec[K + 1][NC / 16][8];
@@ -412,7 +407,11 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
             }
             tc::fence_before();
             tc::proxy_fence();
-            __syncthreads();
+            if (__syncthreads_or(done ? 0 : 1)) {
+                if (t == 0) atomicExch(g.tc_error, 1);
+                ok = false;
+                break;
+            }
             if (t == 0 && c + 1 < CH) {
                 tc::fence_after();
                 issue_forward<Q, K, Sh>(tmem, sA1, sAG, sB1);

@@ -127,14 +127,21 @@ __device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8]
 }
 __device__ __forceinline__ void ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Bounded wait of every thread of the CTA on an mbarrier phase; returns false
-// (all threads agree) on expiry, after recording it in *err.
-__device__ __forceinline__ bool wait_bounded(uint32_t mbar, uint32_t phase, int* err)
+// Bounded wait of this thread on an mbarrier phase; true if the phase completed.
+__device__ __forceinline__ bool spin_wait(uint32_t mbar, uint32_t phase)
 {
     long long spins = 0;
     bool done = false;
     while (!(done = mbar_try_wait(mbar, phase)) && ++spins < kSpinLimit) {
     }
+    return done;
+}
+
+// Bounded wait of every thread of the CTA on an mbarrier phase; returns false
+// (all threads agree) on expiry, after recording it in *err.
+__device__ __forceinline__ bool wait_bounded(uint32_t mbar, uint32_t phase, int* err)
+{
+    const bool done = spin_wait(mbar, phase);
     const int timed_out = __syncthreads_or(done ? 0 : 1);
     if (timed_out) {
         if (threadIdx.x == 0 && err) atomicExch(err, 1);
