@@ -68,12 +68,8 @@ __global__ void __launch_bounds__(kStepThreads) k_channel_team(Graph g, int F, c
     const long total = (long)F * g.n;
     const size_t us = (size_t)g.E * Q, fs = (size_t)g.K * us, vs = (size_t)g.K * g.n * Q;
     blk_clear<T>(sc, sc_floats, L);
-    for (long unit = (long)blockIdx.x * teams + team; unit < total; unit += (long)gridDim.x * teams) {
+    auto one_use = [&](long unit) {   // the channel node of one (frame, channel use), team-uniform
         const int f = (int)(unit / g.n), u = (int)(unit % g.n);
-        if (active && !active[f]) continue;
-        if constexpr (FIX) {
-            if (!isnan(ch2v[f * vs + (size_t)g.use_pos[u] * Q])) continue;
-        }
         float* msg_f = msg + f * fs;
         const float yv = y[(size_t)f * g.n + u], is2 = frame_inv_s2(g, f);
         if (chan_blocked<Q>(g, msg_f, us, 4 * Q, yv, is2, u, sc, res, L)) {
@@ -82,6 +78,29 @@ __global__ void __launch_bounds__(kStepThreads) k_channel_team(Graph g, int F, c
             blk_clear<T>(sc, sc_floats - g.K * Q, L);
         }
         chan_write_team<Q>(g, msg_f, us, 4 * Q, ch2v + f * vs, res, u, L);
+    };
+    if constexpr (FIX) {
+        // each lane tests one channel use; the team then runs the flagged ones
+        for (long base = ((long)blockIdx.x * teams + team) * T; base < total; base += (long)gridDim.x * teams * T) {
+            const long unit = base + L.tl;
+            bool flag = false;
+            if (unit < total) {
+                const int f = (int)(unit / g.n), u = (int)(unit % g.n);
+                flag = (!active || active[f]) && isnan(ch2v[f * vs + (size_t)g.use_pos[u] * Q]);
+            }
+            unsigned bits = __ballot_sync(L.mask, flag) >> ((threadIdx.x & 31) & ~(T - 1));
+            if constexpr (T < 32) bits &= (1u << T) - 1u;
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                one_use(base + b);
+            }
+        }
+    } else {
+        for (long unit = (long)blockIdx.x * teams + team; unit < total; unit += (long)gridDim.x * teams) {
+            if (active && !active[unit / g.n]) continue;
+            one_use(unit);
+        }
     }
 }
 
@@ -499,7 +518,8 @@ cudaError_t channel_team_q(const Graph& g, const DeviceInfo& di, int F, const fl
         cudaFuncSetAttribute(k_channel_team<Q, FIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long units = (long)F * g.n;
-    const int grid = persistent_grid(k_channel_team<Q, FIX>, threads, smem, di, threads / T, units);
+    // the hand-off pass gives each team T channel uses to test per step
+    const int grid = persistent_grid(k_channel_team<Q, FIX>, threads, smem, di, (threads / T) * (FIX ? T : 1), units);
     k_channel_team<Q, FIX><<<grid, threads, smem, s>>>(g, F, y, msg, ch2v, active, scf);
     return cudaGetLastError();
 }
