@@ -110,13 +110,14 @@ struct ShapeOf {
 };
 
 // Forward products of one chunk (one thread): spectrum of mu_j into columns
-// SP + j Nc, of the G window into SP + K Nc.  Terms A*B_hi + A*B_lo.
+// SP + j Nc, of the G window into SP + K Nc.  Terms A*B_hi + A*B_lo.  The
+// operand descriptors are the tiles' step-0 descriptors plus constant offsets.
 template <int Q, int K, class Sh>
-__device__ __forceinline__ void issue_forward(uint32_t tmem, uint32_t sA1, uint32_t sAG, uint32_t sB1)
+__device__ __forceinline__ void issue_forward(uint32_t tmem, uint64_t dA1, uint64_t dAG, uint64_t dB1)
 {
     constexpr DftShape S = Sh::v;
-    constexpr int NC = S.Nc, KB = S.KB, W = S.W, SP = S.KG * Q;
-    constexpr uint32_t kA1 = kDftRows * Q * 2, kB1 = NC * KB * 2;
+    constexpr int NC = S.Nc, W = S.W, SP = S.KG * Q;
+    constexpr uint32_t kA1 = kDftRows * Q * 2, kB1 = NC * S.KB * 2;
     constexpr uint32_t id = tc::idesc_f16(kDftRows, NC, false);
 #pragma unroll
     for (int j = 0; j < K; ++j) {
@@ -125,24 +126,20 @@ __device__ __forceinline__ void issue_forward(uint32_t tmem, uint32_t sA1, uint3
         for (int p = 0; p < 2; ++p)
 #pragma unroll
             for (int ks = 0; ks < Q / 16; ++ks)
-                tc::mma_f16(d, tc::step_desc(sA1 + j * kA1, ks, Q), tc::step_desc(sB1 + p * kB1, ks, KB), id,
-                            p | ks);
+                tc::mma_f16(d, dA1 + ((j * kA1 + ks * 256) >> 4), dB1 + ((p * kB1 + ks * 256) >> 4), id, p | ks);
     }
     const uint32_t d = tmem + SP + K * NC;
-    int acc = 0;
 #pragma unroll
     for (int p = 0; p < 2; ++p)
 #pragma unroll
-        for (int ks = 0; ks < W / 16; ++ks) {
-            tc::mma_f16(d, tc::step_desc(sAG, ks, W), tc::step_desc(sB1 + p * kB1, ks, KB), id, acc);
-            acc = 1;
-        }
+        for (int ks = 0; ks < W / 16; ++ks)
+            tc::mma_f16(d, dAG + ks * 16, dB1 + ((p * kB1 + ks * 256) >> 4), id, p | ks);
 }
 
 // Inverse products of chunk c (one thread): X of the pass's user slot k < kn
 // against the inverse rows, accumulated into columns k q.
 template <int Q, int K, class Sh>
-__device__ __forceinline__ void issue_inverse(uint32_t tmem, uint32_t sA3, uint32_t sB3, int c, int kn)
+__device__ __forceinline__ void issue_inverse(uint32_t tmem, uint64_t dA3, uint64_t dB3, int c, int kn)
 {
     constexpr int NC = Sh::v.Nc;
     constexpr uint32_t kA3 = kDftRows * NC * 2, kB3 = Q * NC * 2;
@@ -150,16 +147,12 @@ __device__ __forceinline__ void issue_inverse(uint32_t tmem, uint32_t sA3, uint3
 #pragma unroll
     for (int k = 0; k < Sh::v.KG; ++k) {
         if (k >= kn) break;
-        int acc = c > 0;
 #pragma unroll
-        for (int p = 0; p < 3; ++p) {
-            const uint32_t a = sA3 + (2 * k + (p == 1)) * kA3, b = sB3 + (p == 2) * kB3;
+        for (int p = 0; p < 3; ++p)
 #pragma unroll
-            for (int ks = 0; ks < NC / 16; ++ks) {
-                tc::mma_f16(tmem + k * Q, tc::step_desc(a, ks, NC), tc::step_desc(b, ks, NC), id, acc);
-                acc = 1;
-            }
-        }
+            for (int ks = 0; ks < NC / 16; ++ks)
+                tc::mma_f16(tmem + k * Q, dA3 + (((2 * k + (p == 1)) * kA3 + ks * 256) >> 4),
+                            dB3 + (((p == 2) * kB3 + ks * 256) >> 4), id, (c > 0) | p | ks);
     }
 }
 
@@ -280,8 +273,9 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
     tc::fence_after();
     const uint32_t tmem = tmem_holder;
     const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
-    const uint32_t sA1 = tc::smem_addr(A1), sAG = tc::smem_addr(AG), sB1 = tc::smem_addr(BC), sB3 = sB1 + 2 * kB1,
-                   sA3 = tc::smem_addr(A3);
+    const uint64_t dA1 = tc::tile_desc(tc::smem_addr(A1), Q), dAG = tc::tile_desc(tc::smem_addr(AG), W),
+                   dB1 = tc::tile_desc(tc::smem_addr(BC), S.KB), dB3 = tc::tile_desc(tc::smem_addr(BC) + 2 * kB1, NC),
+                   dA3 = tc::tile_desc(tc::smem_addr(A3), NC);
     uint32_t phase = 0;
     bool ok = true;
     const long total = (long)F * g.n;
@@ -373,7 +367,7 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
         __syncthreads();
         if (t == 0) {
             tc::fence_after();
-            issue_forward<Q, K, Sh>(tmem, sA1, sAG, sB1);
+            issue_forward<Q, K, Sh>(tmem, dA1, dAG, dB1);
             tc::mma_commit(mbar);
         }
 #pragma unroll 1
@@ -414,7 +408,7 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
             }
             if (t == 0 && c + 1 < CH) {
                 tc::fence_after();
-                issue_forward<Q, K, Sh>(tmem, sA1, sAG, sB1);
+                issue_forward<Q, K, Sh>(tmem, dA1, dAG, dB1);
             }
 #pragma unroll
             for (int cq = 0; cq < NC / 16; ++cq) {
@@ -464,7 +458,7 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
             __syncthreads();
             if (t == 0) {
                 tc::fence_after();
-                issue_inverse<Q, K, Sh>(tmem, sA3, sB3, c, kn);
+                issue_inverse<Q, K, Sh>(tmem, dA3, dB3, c, kn);
                 tc::mma_commit(mbar);
             }
         }

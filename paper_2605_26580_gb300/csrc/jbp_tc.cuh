@@ -43,6 +43,15 @@ __device__ __forceinline__ uint64_t step_desc(uint32_t addr, int ks, int KD)
     return smem_desc(addr + (uint32_t)ks * 256u, 128u, (uint32_t)(KD / 8) * 128u);
 }
 
+// descriptor of K step 0 of a (rows x KD) tile at addr.  The start-address
+// field holds addr / 16 in 14 bits, which shared-memory offsets never carry out
+// of, so the descriptor of byte offset o within the same tile is this plus o / 16
+// (step ks: + 16 ks).
+__device__ __forceinline__ uint64_t tile_desc(uint32_t addr, int KD)
+{
+    return smem_desc(addr, 128u, (uint32_t)(KD / 8) * 128u);
+}
+
 // instruction descriptor, kind::f16 with FP32 accumulation, A and B K-major.
 // bf16 = true: BF16 x BF16; false: FP16 x FP16 (both operands always share a type).
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16)

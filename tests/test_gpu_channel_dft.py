@@ -190,3 +190,83 @@ def test_dft_channel_routing(env):
     with pytest.raises(jbp.JBPError) as ei:
         jbp.Context(iters=4, channel_node=2)
     assert ei.value.code == jbp.EINVAL
+
+
+def test_dft_decode_many_graph_replay_matches_single_decodes(env):
+    """Parts of different (n, K, q) in one jbp_decode_many call with the DFT node:
+    one and two user passes, one and several chunks, and a GF(4) part that keeps
+    the trellis.  The eager call, the captured call and a graph replay equal
+    individual decodes bit for bit (each channel use's products are independent
+    of the other rows in its tile)."""
+    jbp, O, torch = env
+    specs = [(128, 16, 3, 14.0, 9), (128, 64, 4, 14.0, 5), (64, 64, 6, 14.0, 3), (64, 4, 2, 12.0, 20)]
+    ctx = jbp.Context(iters=6, early_stop=True, channel_node=jbp.CHAN_DFT)
+    decs, parts, refs = [], [], []
+    try:
+        for n, q, K, snr, F in specs:
+            code = I.make_code(n, q)
+            fr = I.make_frames(code, K, snr, F, seed=7 * n + q + K)
+            sig = np.full(F, fr["sigma2"], np.float32)
+            d = jbp.Decoder(ctx, code, K, fr["sigma2"], fr["perm"])
+            decs.append(d)
+            refs.append(d.decode(fr["y"], sigma2=sig))
+            t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+            parts.append((d, t(fr["y"]), torch.empty((F, K, n), dtype=torch.uint8, device="cuda"),
+                          torch.empty((F,), dtype=torch.int32, device="cuda"),
+                          torch.empty((F, K), dtype=torch.uint8, device="cuda"), t(sig)))
+        assert [d.channel_node for d in decs] == [jbp.CHAN_DFT] * 3 + [jbp.CHAN_TRELLIS]
+        for call in range(3):                  # eager, capture, replay
+            for p in parts:
+                p[2].fill_(255)
+            ctx.decode_many(parts)
+            torch.cuda.synchronize()
+            for p, r in zip(parts, refs):
+                assert np.array_equal(p[2].cpu().numpy(), r["hat"]), call
+                assert np.array_equal(p[3].cpu().numpy(), r["iters"]), call
+                assert np.array_equal(p[4].cpu().numpy(), r["ok"]), call
+        assert all(d.tc_timeouts() == 0 for d in decs)
+    finally:
+        for d in decs:
+            d.close()
+        ctx.close()
+
+
+def test_dft_serving_matches_frames_decoded_alone(env):
+    """Serving with the DFT node: frames submitted interleaved to two decoders run
+    in resident pools (active masks, admission between blocks) and each result
+    equals that frame decoded alone in the step form."""
+    jbp, O, torch = env
+    ctx = jbp.Context(iters=8, early_stop=True, channel_node=jbp.CHAN_DFT)
+    specs = [(64, 64, 2, 30.0, 10), (128, 16, 4, 13.0, 12)]
+    decs, frames = [], []
+    try:
+        for n, q, K, snr, F in specs:
+            code = I.make_code(n, q)
+            fr = I.make_frames(code, K, snr, F, seed=1300 + n)
+            decs.append(jbp.Decoder(ctx, code, K, fr["sigma2"], fr["perm"]))
+            frames.append(fr)
+        assert all(d.channel_node == jbp.CHAN_DFT for d in decs)
+        sig = [np.full(fr["y"].shape[0], np.float32(fr["sigma2"]), np.float32) for fr in frames]
+        alone = [[d.decode(fr["y"][i:i + 1], form=jbp.FORM_STEP, sigma2=s[i:i + 1]) for i in range(fr["y"].shape[0])]
+                 for d, fr, s in zip(decs, frames, sig)]
+        tickets = []
+        for i in range(max(fr["y"].shape[0] for fr in frames)):
+            for j, (d, fr) in enumerate(zip(decs, frames)):
+                if i < fr["y"].shape[0]:
+                    tickets.append((j, i, d.submit(fr["y"][i], float(sig[j][i]))))
+        pending = list(tickets)
+        while pending:
+            rest = []
+            for j, i, tk in pending:
+                res = ctx.poll(tk, decs[j].n, decs[j].K)
+                if res is None:
+                    rest.append((j, i, tk))
+                    continue
+                a = alone[j][i]
+                assert np.array_equal(res["hat"], a["hat"][0]), (j, i)
+                assert res["iters"] == int(a["iters"][0]) and np.array_equal(res["ok"], a["ok"][0])
+            pending = rest
+    finally:
+        for d in decs:
+            d.close()
+        ctx.close()
