@@ -414,8 +414,13 @@ def extra_legs(jbp, torch, dev, code, base, ys, sig, decs, stream) -> dict:
     e1.record(stream)
     stream.synchronize()
     ms = e0.elapsed_time(e1)
+    sh = hat.cpu().numpy()
+    # the fused form sums in another order; frames whose BP does not converge (all of
+    # them past capacity) can end in different decisions, at equal symbol error rate
     out["step_form"] = {"value": F / (ms / 1e3), "unit": "frames/s",
-                        "matches_fused": bool(np.array_equal(hat.cpu().numpy(), res["hat"]))}
+                        "matches_fused": bool(np.array_equal(sh, res["hat"])),
+                        "decisions_differing_from_fused": int((sh != res["hat"]).sum()),
+                        "decisions": int(sh.size), "ser": float((sh != base["c"]).mean())}
     # single-step kernels on the full batch: achieved HBM bandwidth vs algorithmic bytes
     E, n, q, K = code["P"] * code["dc"], N_SYM, Q, K_USERS
     msg = torch.ones((F, K, E, q), dtype=torch.float32, device=dev)
