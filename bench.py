@@ -342,7 +342,7 @@ def main() -> None:
                 # (1.38 MB read + 15 KB written), scaled by frames; state stays in shared memory, so this
                 # is y in (and decisions out through L2), not message traffic.  Only valid at the
                 # default workload size and for this kernel version.
-                "traffic": (1.397e6 * 65536 / 1216) if args.frames == FRAMES else None,
+                "traffic": (1.409e6 * 65536 / 1216) if args.frames == FRAMES else None,
                 "traffic_note": "per launch, from profiles/k_fused_pos_q16_k4_n256_small_full.md scaled by frames",
                 "kernel": "k_fused_pos<16,4>",
                 "peak_note": "FP32 FMA peak derived: %d SMs x 128 lanes x 2 flops x 2070 MHz" % sm_count,
