@@ -71,12 +71,14 @@ typedef enum { JBP_PREC_FP32 = 0, JBP_PREC_BF16X2 = 1, JBP_PREC_BF16 = 2, JBP_PR
  * reference numerics).  DFT: the same extrinsic messages as a correlation in
  * the frequency domain of the sum alphabet (DFT length L >= K(q-1)+1), with the
  * forward and inverse transforms issued as matrix products on the tensor cores
- * (FP16 hi/lo operand terms, FP32 accumulation).  Its error is absolute, a
- * small fraction of each message's maximum (about 1e-5; the tests bound it),
+ * (FP16 operand terms, FP32 accumulation).  Its error is absolute, a few 1e-4
+ * of each message's maximum at most ((K+2) 2^-9 + K 2^-12 by construction),
  * rather than relative per entry, so entries far below the maximum are not
- * resolved.  It runs in the step form for 2 <= K <= 8 and q = 16, 32, 64;
- * other handles of the context keep the trellis (jbp_query_channel tells
- * which). */
+ * resolved; a channel use whose peak the transform cannot resolve is computed
+ * by the trellis in the same call.  It runs in the step form for 2 <= K <= 8
+ * and q = 16, 32, 64; other handles of the context keep the trellis
+ * (jbp_query_channel tells which).  No paper counterpart: the paper prints no
+ * channel-node kernel. */
 typedef enum { JBP_CHAN_TRELLIS = 0, JBP_CHAN_DFT = 1 } jbp_channel_node;
 
 /* Launch form of jbp_decode.  AUTO picks FUSED when one frame's message state

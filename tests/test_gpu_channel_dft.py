@@ -101,6 +101,29 @@ def test_dft_step_channel_matches_oracle(env, K, q, n, F):
     assert e_v2c <= 1e-4
 
 
+def test_dft_step_channel_literal_mode(env):
+    """interleave = 0 (every user's symbol i on channel use i): the offset table
+    comes from identity interleavers; the messages still meet the variant's bar."""
+    jbp, O, torch = env
+    K, q, n, F = 3, 32, 64, 5
+    code = I.make_code(n, q)
+    fr = I.make_frames(code, K, 12.0, F, seed=77, interleave=False)
+    rng = np.random.default_rng(78)
+    E = code["P"] * code["dc"]
+    c2v_lin = np.exp(I.random_log_messages(rng, (F, K, E), q, spread=3.0)).astype(np.float32)
+    ctx, dec = _decoder(jbp, code, K, fr["sigma2"], None)
+    try:
+        assert dec.channel_node == jbp.CHAN_DFT
+        ch_g, v2c_g = _step_channel(jbp, torch, dec, fr, c2v_lin, K, n, q)
+    finally:
+        dec.close()
+        ctx.close()
+    ch_o = np.exp(O.step_channel(code, K, fr["sigma2"], None, fr["y"], np.log(c2v_lin.astype(np.float64))))
+    lin = float(np.abs(ch_g - ch_o).max())
+    print("DFT channel, literal mode: linear err %.2e (bound %.2e)" % (lin, dft_bound(K)))
+    assert lin <= dft_bound(K)
+
+
 def test_dft_unresolved_rows_go_to_the_trellis(env):
     """Confident messages that make the observed sum (nearly) impossible: the
     transform cannot resolve the peak, so every row is handed to the FP32
