@@ -240,8 +240,9 @@ def main() -> None:
     ap.add_argument("--variants", default="0,d0,3,1,2",
                     help="precision workload: check-node variants to run (dP: with the DFT channel node)")
     ap.add_argument("--channel-legs", type=int, default=1, help="precision workload: time the channel node alone")
-    ap.add_argument("--channel-node", default="trellis", choices=["trellis", "dft"],
-                    help="uneven and serving workloads: channel node (dft: tensor-core variant where it applies)")
+    ap.add_argument("--channel-node", default="trellis", choices=["trellis", "dft", "auto"],
+                    help="uneven and serving workloads: channel node (dft: tensor-core variant wherever it "
+                         "applies; auto: except where the register-resident trellis applies)")
     ap.add_argument("--channel-frames", type=int, default=4096, help="precision workload: frames of that leg")
     ap.add_argument("--oracle-sample", type=int, default=16, help="precision workload: oracle frames")
     args = ap.parse_args()
@@ -680,7 +681,7 @@ def _waves(parts, budget):
 
 
 def _channel_node(jbp, args):
-    return jbp.CHAN_DFT if args.channel_node == "dft" else jbp.CHAN_TRELLIS
+    return {"trellis": jbp.CHAN_TRELLIS, "dft": jbp.CHAN_DFT, "auto": jbp.CHAN_AUTO}[args.channel_node]
 
 
 def wl_uneven(args):

@@ -77,9 +77,11 @@ typedef enum { JBP_PREC_FP32 = 0, JBP_PREC_BF16X2 = 1, JBP_PREC_BF16 = 2, JBP_PR
  * resolved; a channel use whose peak the transform cannot resolve is computed
  * by the trellis in the same call.  It runs in the step form for 2 <= K <= 8
  * and q = 16, 32, 64; other handles of the context keep the trellis
- * (jbp_query_channel tells which).  No paper counterpart: the paper prints no
- * channel-node kernel. */
-typedef enum { JBP_CHAN_TRELLIS = 0, JBP_CHAN_DFT = 1 } jbp_channel_node;
+ * (jbp_query_channel tells which).  AUTO: DFT except where the register-
+ * resident trellis applies (q <= 16 and K <= 4), which is the faster node there
+ * and keeps the fused form where a frame fits it.  No paper counterpart: the
+ * paper prints no channel-node kernel. */
+typedef enum { JBP_CHAN_TRELLIS = 0, JBP_CHAN_DFT = 1, JBP_CHAN_AUTO = 2 } jbp_channel_node;
 
 /* Launch form of jbp_decode.  AUTO picks FUSED when one frame's message state
  * fits in one SM's shared memory, else STEP.  FUSED: one persistent kernel runs

@@ -417,7 +417,7 @@ extern "C" int jbp_context_create(const jbp_options* opt, jbp_ctx** out)
     if (!opt || !out) return fail(JBP_EINVAL, "jbp_context_create: NULL argument");
     if (opt->iters < 1) return fail(JBP_EINVAL, "iters must be >= 1 (got %d)", opt->iters);
     if (opt->precision < 0 || opt->precision > 3) return fail(JBP_EINVAL, "bad precision %d", opt->precision);
-    if (opt->channel_node != JBP_CHAN_TRELLIS && opt->channel_node != JBP_CHAN_DFT)
+    if (opt->channel_node < JBP_CHAN_TRELLIS || opt->channel_node > JBP_CHAN_AUTO)
         return fail(JBP_EINVAL, "bad channel_node %d", opt->channel_node);
     if (opt->mem_budget_bytes < 0) return fail(JBP_EINVAL, "negative memory budget");
     int ndev = 0;
@@ -610,8 +610,11 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
     std::vector<uint16_t> chk_order;
     if (want_order) chk_order = check_order(K, P, E, slot);
     const DftShape dsh = dft_shape(K, q);
-    const bool want_dft = ctx->opt.channel_node == JBP_CHAN_DFT && dv == 2 && dc == kDC && dsh.ok &&
-                          dsh.smem <= ctx->di.smem_optin;
+    // AUTO: the transform except where the register-resident trellis (thread shape) applies
+    const bool thread_shape = q <= 16 && K <= 4;
+    const bool want_dft = (ctx->opt.channel_node == JBP_CHAN_DFT ||
+                           (ctx->opt.channel_node == JBP_CHAN_AUTO && !thread_shape)) &&
+                          dv == 2 && dc == kDC && dsh.ok && dsh.smem <= ctx->di.smem_optin;
     std::vector<unsigned char> dft_tab;   // shape tables, then this handle's message offsets
     if (want_dft) {
         dft_tab.resize(dft_table_bytes(K, q) + dft_offsets_bytes(K, n));

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libjbp.so")
 OK, EINVAL, ENOMEM, ECUDA, EAGAIN, ETIMEOUT, ECLOSED = range(7)
 PREC_FP32, PREC_BF16X2, PREC_BF16, PREC_BF16X3 = 0, 1, 2, 3
 FORM_AUTO, FORM_FUSED, FORM_STEP, FORM_PLAIN = 0, 1, 2, 3
-CHAN_TRELLIS, CHAN_DFT = 0, 1
+CHAN_TRELLIS, CHAN_DFT, CHAN_AUTO = 0, 1, 2
 
 EXPORTS = [
     "jbp_context_create", "jbp_context_destroy", "jbp_create", "jbp_destroy", "jbp_decode",

@@ -187,7 +187,9 @@ def test_dft_decode_agrees_with_oracle(env, K, q, n, F, snr, T, margin):
 
 def test_dft_channel_routing(env):
     """Handles whose (K, q) has a tensor-core shape run it; the others keep the
-    trellis; the fused form refuses the DFT node; a bad option is refused."""
+    trellis; the fused form refuses the DFT node; AUTO keeps the register-resident
+    trellis (q <= 16, K <= 4) and takes the transform elsewhere; a bad option is
+    refused."""
     jbp, O, torch = env
     ctx = jbp.Context(iters=4, channel_node=jbp.CHAN_DFT)
     try:
@@ -210,8 +212,22 @@ def test_dft_channel_routing(env):
                 dec.close()
     finally:
         ctx.close()
+    # AUTO: the transform except where the register-resident trellis applies (q <= 16, K <= 4)
+    ctx = jbp.Context(iters=4, channel_node=jbp.CHAN_AUTO)
+    try:
+        for K, q, n, want in [(4, 16, 64, jbp.CHAN_TRELLIS), (2, 16, 32, jbp.CHAN_TRELLIS),
+                              (3, 32, 32, jbp.CHAN_DFT), (2, 64, 32, jbp.CHAN_DFT), (5, 16, 32, jbp.CHAN_DFT)]:
+            code = I.make_code(n, q)
+            fr = I.make_frames(code, K, 12.0, 2, seed=2)
+            dec = jbp.Decoder(ctx, code, K, fr["sigma2"], fr["perm"])
+            try:
+                assert dec.channel_node == want, (K, q)
+            finally:
+                dec.close()
+    finally:
+        ctx.close()
     with pytest.raises(jbp.JBPError) as ei:
-        jbp.Context(iters=4, channel_node=2)
+        jbp.Context(iters=4, channel_node=3)
     assert ei.value.code == jbp.EINVAL
 
 
