@@ -180,7 +180,10 @@ __device__ __forceinline__ float group_max(float x)
 }
 
 __device__ __forceinline__ float max4(float4 v) { return fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)); }
-__device__ __forceinline__ float4 mul4(float4 a, float4 b) { return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w); }
+__device__ __forceinline__ float4 mul4(float4 a, float4 b)
+{
+    return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
+}
 __device__ __forceinline__ float4 scale4(float4 a, float s) { return make_float4(a.x * s, a.y * s, a.z * s, a.w * s); }
 
 template <int Q, int K>
@@ -318,7 +321,7 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
             *reinterpret_cast<uint4*>(AG + tc::tile_off(m, kg, W)) = pack8(e);
         }
         __syncthreads();
-        if constexpr (CH > 1) fetch(CH > 1 ? 1 : 0);
+        if constexpr (CH > 1) fetch(1);
         // mu_j = c2v_e0 * c2v_e1, max 1: BT vectors per lane group in flight
 #pragma unroll 1
         for (int b0 = 0; b0 < IT; b0 += BT) {
@@ -355,150 +358,150 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
         bool weak = false;   // some user's peak below kMinPeak (this thread's users, all passes)
 #pragma unroll
         for (int pass = 0; pass < NP; ++pass) {
-        const int k0 = pass * KG, kn = min(KG, K - k0);
-        if (pass > 0) {
-            if constexpr (CH > 1) {   // forward rows of chunk 0 (the previous pass's products are done)
-                put1();
-                fetch(1);
-            }
-        }
-        tc::proxy_fence();
-        tc::fence_before();
-        __syncthreads();
-        if (t == 0) {
-            tc::fence_after();
-            issue_forward<Q, K, Sh>(tmem, dA1, dAG, dB1);
-            tc::mma_commit(mbar);
-        }
-#pragma unroll 1
-        for (int c = 0; c < CH; ++c) {
-            // each thread waits on its own; the barrier below settles an expiry for all
-            const bool done = tc::spin_wait(mbar, phase);
-            phase ^= 1;
-            tc::fence_after();
-            uint32_t spec[K + 1][NC / 16][8];
-#pragma unroll
-            for (int j = 0; j <= K; ++j)
-#pragma unroll
-                for (int q8 = 0; q8 < NC / 16; ++q8)
-                    tc::tmem_ld8_nowait(trow + SP + j * NC + half * (NC / 2) + q8 * 8, spec[j][q8]);
-            if (c == 0) {   // DC terms (real, >= 1): every spectrum is scaled to DC 1
-                uint32_t raw[K + 1][8];
-#pragma unroll
-                for (int j = 0; j <= K; ++j) tc::tmem_ld8_nowait(trow + SP + j * NC, raw[j]);
-                tc::ld_wait();
-#pragma unroll
-                for (int j = 0; j <= K; ++j) inv_dc[j] = 1.0f / __uint_as_float(raw[j][0]);
-            }
-            tc::ld_wait();
-            if constexpr (CH > 1) {
-                put3();                          // inverse rows of chunk c
-                fetch3((c + 1) % CH);
-                if (c + 1 < CH) {
-                    put1();                      // forward rows of chunk c + 1
-                    fetch((c + 2) % CH);
+            const int k0 = pass * KG, kn = min(KG, K - k0);
+            if (pass > 0) {
+                if constexpr (CH > 1) {   // forward rows of chunk 0 (the previous pass's products are done)
+                    put1();
+                    fetch(1);
                 }
             }
-            tc::fence_before();
             tc::proxy_fence();
-            if (__syncthreads_or(done ? 0 : 1)) {
-                if (t == 0) atomicExch(g.tc_error, 1);
-                ok = false;
-                break;
-            }
-            if (t == 0 && c + 1 < CH) {
-                tc::fence_after();
-                issue_forward<Q, K, Sh>(tmem, dA1, dAG, dB1);
-            }
-#pragma unroll
-            for (int cq = 0; cq < NC / 16; ++cq) {
-                const int cg = half * (NC / 16) + cq;   // group of 8 columns = 4 frequency pairs
-                float xs[KG][8];
-#pragma unroll
-                for (int pp = 0; pp < 4; ++pp) {
-                    const int pg = c * (NC / 2) + cg * 4 + pp;
-                    Cx mh[K], X[K], gh;
-                    if (pg == 0) {   // (DC, Nyquist), both real
-#pragma unroll
-                        for (int j = 0; j < K; ++j) mh[j] = {__uint_as_float(spec[j][cq][1]) * inv_dc[j], 0.0f};
-                        gh = {__uint_as_float(spec[K][cq][1]) * inv_dc[K] * ((u_lo & 1) ? -1.0f : 1.0f), 0.0f};
-                        leave_one_out<K>(mh, gh, X);
-#pragma unroll
-                        for (int k = 0; k < KG; ++k) {
-                            xs[k][0] = 1.0f;
-                            xs[k][1] = k0 + k < K ? X[k0 + k].r : 0.0f;
-                        }
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < K; ++j)
-                            mh[j] = {__uint_as_float(spec[j][cq][2 * pp]) * inv_dc[j],
-                                     __uint_as_float(spec[j][cq][2 * pp + 1]) * inv_dc[j]};
-                        const Cx gw = {__uint_as_float(spec[K][cq][2 * pp]) * inv_dc[K],
-                                       __uint_as_float(spec[K][cq][2 * pp + 1]) * inv_dc[K]};
-                        const float2 w = TW[(pg * u_lo) % L];   // window offset: G^ = Gw^ e^{-2 pi i f u_lo / L}
-                        gh = {gw.r * w.x + gw.i * w.y, gw.i * w.x - gw.r * w.y};
-                        leave_one_out<K>(mh, gh, X);
-#pragma unroll
-                        for (int k = 0; k < KG; ++k) {
-                            xs[k][2 * pp] = k0 + k < K ? X[k0 + k].r : 0.0f;
-                            xs[k][2 * pp + 1] = k0 + k < K ? X[k0 + k].i : 0.0f;
-                        }
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < KG; ++k) {
-                    uint4 hi, lo;
-                    split8(xs[k], hi, lo);
-                    *reinterpret_cast<uint4*>(A3 + (2 * k) * kA3 + tc::tile_off(m, cg, NC)) = hi;
-                    *reinterpret_cast<uint4*>(A3 + (2 * k + 1) * kA3 + tc::tile_off(m, cg, NC)) = lo;
-                }
-            }
             tc::fence_before();
-            tc::proxy_fence();
             __syncthreads();
             if (t == 0) {
                 tc::fence_after();
-                issue_inverse<Q, K, Sh>(tmem, dA3, dB3, c, kn);
+                issue_forward<Q, K, Sh>(tmem, dA1, dAG, dB1);
                 tc::mma_commit(mbar);
             }
-        }
-        if (!ok) break;
-        if (!tc::wait_bounded(mbar, phase, g.tc_error)) {
-            ok = false;
-            break;
-        }
-        phase ^= 1;
-        tc::fence_after();
-        if constexpr (NP > 1) {
-            // this pass's messages straight to ch2v (row threads); the in-place v2c
-            // waits until every pass has passed the resolution test
 #pragma unroll 1
-            for (int k = k0 + half; k < k0 + kn; k += 2) {
-                float mx = -INFINITY;
+            for (int c = 0; c < CH; ++c) {
+                // each thread waits on its own; the barrier below settles an expiry for all
+                const bool done = tc::spin_wait(mbar, phase);
+                phase ^= 1;
+                tc::fence_after();
+                uint32_t spec[K + 1][NC / 16][8];
 #pragma unroll
-                for (int c16 = 0; c16 < Q / 16; ++c16) {
-                    float o[16];
-                    tc::tmem_ld16(trow + (k - k0) * Q + c16 * 16, o);
-                    mx = fmaxf(mx, vmax(o));
+                for (int j = 0; j <= K; ++j)
+#pragma unroll
+                    for (int q8 = 0; q8 < NC / 16; ++q8)
+                        tc::tmem_ld8_nowait(trow + SP + j * NC + half * (NC / 2) + q8 * 8, spec[j][q8]);
+                if (c == 0) {   // DC terms (real, >= 1): every spectrum is scaled to DC 1
+                    uint32_t raw[K + 1][8];
+#pragma unroll
+                    for (int j = 0; j <= K; ++j) tc::tmem_ld8_nowait(trow + SP + j * NC, raw[j]);
+                    tc::ld_wait();
+#pragma unroll
+                    for (int j = 0; j <= K; ++j) inv_dc[j] = 1.0f / __uint_as_float(raw[j][0]);
                 }
-                weak |= !(mx >= kMinPeak * (float)L);
-                const float inv = 1.0f / mx;
-                float* dst = ch2v + f * vs + (live ? s_off[(m * K + k) * 3 + 2] : 0);
+                tc::ld_wait();
+                if constexpr (CH > 1) {
+                    put3();                          // inverse rows of chunk c
+                    fetch3((c + 1) % CH);
+                    if (c + 1 < CH) {
+                        put1();                      // forward rows of chunk c + 1
+                        fetch((c + 2) % CH);
+                    }
+                }
+                tc::fence_before();
+                tc::proxy_fence();
+                if (__syncthreads_or(done ? 0 : 1)) {
+                    if (t == 0) atomicExch(g.tc_error, 1);
+                    ok = false;
+                    break;
+                }
+                if (t == 0 && c + 1 < CH) {
+                    tc::fence_after();
+                    issue_forward<Q, K, Sh>(tmem, dA1, dAG, dB1);
+                }
 #pragma unroll
-                for (int c16 = 0; c16 < Q / 16; ++c16) {
-                    float o[16];
-                    tc::tmem_ld16(trow + (k - k0) * Q + c16 * 16, o);
-                    if (live)
+                for (int cq = 0; cq < NC / 16; ++cq) {
+                    const int cg = half * (NC / 16) + cq;   // group of 8 columns = 4 frequency pairs
+                    float xs[KG][8];
 #pragma unroll
-                        for (int a = 0; a < 16; a += 4)
-                            *reinterpret_cast<float4*>(dst + c16 * 16 + a) =
-                                make_float4(fmaxf(o[a] * inv, kRelFloor), fmaxf(o[a + 1] * inv, kRelFloor),
-                                            fmaxf(o[a + 2] * inv, kRelFloor), fmaxf(o[a + 3] * inv, kRelFloor));
+                    for (int pp = 0; pp < 4; ++pp) {
+                        const int pg = c * (NC / 2) + cg * 4 + pp;
+                        Cx mh[K], X[K], gh;
+                        if (pg == 0) {   // (DC, Nyquist), both real
+#pragma unroll
+                            for (int j = 0; j < K; ++j) mh[j] = {__uint_as_float(spec[j][cq][1]) * inv_dc[j], 0.0f};
+                            gh = {__uint_as_float(spec[K][cq][1]) * inv_dc[K] * ((u_lo & 1) ? -1.0f : 1.0f), 0.0f};
+                            leave_one_out<K>(mh, gh, X);
+#pragma unroll
+                            for (int k = 0; k < KG; ++k) {
+                                xs[k][0] = 1.0f;
+                                xs[k][1] = k0 + k < K ? X[k0 + k].r : 0.0f;
+                            }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < K; ++j)
+                                mh[j] = {__uint_as_float(spec[j][cq][2 * pp]) * inv_dc[j],
+                                         __uint_as_float(spec[j][cq][2 * pp + 1]) * inv_dc[j]};
+                            const Cx gw = {__uint_as_float(spec[K][cq][2 * pp]) * inv_dc[K],
+                                           __uint_as_float(spec[K][cq][2 * pp + 1]) * inv_dc[K]};
+                            const float2 w = TW[(pg * u_lo) % L];   // window offset: G^ = Gw^ e^{-2 pi i f u_lo / L}
+                            gh = {gw.r * w.x + gw.i * w.y, gw.i * w.x - gw.r * w.y};
+                            leave_one_out<K>(mh, gh, X);
+#pragma unroll
+                            for (int k = 0; k < KG; ++k) {
+                                xs[k][2 * pp] = k0 + k < K ? X[k0 + k].r : 0.0f;
+                                xs[k][2 * pp + 1] = k0 + k < K ? X[k0 + k].i : 0.0f;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < KG; ++k) {
+                        uint4 hi, lo;
+                        split8(xs[k], hi, lo);
+                        *reinterpret_cast<uint4*>(A3 + (2 * k) * kA3 + tc::tile_off(m, cg, NC)) = hi;
+                        *reinterpret_cast<uint4*>(A3 + (2 * k + 1) * kA3 + tc::tile_off(m, cg, NC)) = lo;
+                    }
+                }
+                tc::fence_before();
+                tc::proxy_fence();
+                __syncthreads();
+                if (t == 0) {
+                    tc::fence_after();
+                    issue_inverse<Q, K, Sh>(tmem, dA3, dB3, c, kn);
+                    tc::mma_commit(mbar);
                 }
             }
-            tc::fence_before();
-            __syncthreads();   // accumulators read before the next pass overwrites them
-        }
+            if (!ok) break;
+            if (!tc::wait_bounded(mbar, phase, g.tc_error)) {
+                ok = false;
+                break;
+            }
+            phase ^= 1;
+            tc::fence_after();
+            if constexpr (NP > 1) {
+                // this pass's messages straight to ch2v (row threads); the in-place v2c
+                // waits until every pass has passed the resolution test
+#pragma unroll 1
+                for (int k = k0 + half; k < k0 + kn; k += 2) {
+                    float mx = -INFINITY;
+#pragma unroll
+                    for (int c16 = 0; c16 < Q / 16; ++c16) {
+                        float o[16];
+                        tc::tmem_ld16(trow + (k - k0) * Q + c16 * 16, o);
+                        mx = fmaxf(mx, vmax(o));
+                    }
+                    weak |= !(mx >= kMinPeak * (float)L);
+                    const float inv = 1.0f / mx;
+                    float* dst = ch2v + f * vs + (live ? s_off[(m * K + k) * 3 + 2] : 0);
+#pragma unroll
+                    for (int c16 = 0; c16 < Q / 16; ++c16) {
+                        float o[16];
+                        tc::tmem_ld16(trow + (k - k0) * Q + c16 * 16, o);
+                        if (live)
+#pragma unroll
+                            for (int a = 0; a < 16; a += 4)
+                                *reinterpret_cast<float4*>(dst + c16 * 16 + a) =
+                                    make_float4(fmaxf(o[a] * inv, kRelFloor), fmaxf(o[a + 1] * inv, kRelFloor),
+                                                fmaxf(o[a + 2] * inv, kRelFloor), fmaxf(o[a + 3] * inv, kRelFloor));
+                    }
+                }
+                tc::fence_before();
+                __syncthreads();   // accumulators read before the next pass overwrites them
+            }
         }   // passes
         if (!ok) break;
 
