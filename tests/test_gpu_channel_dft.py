@@ -309,3 +309,48 @@ def test_dft_serving_matches_frames_decoded_alone(env):
         for d in decs:
             d.close()
         ctx.close()
+
+
+def test_dft_per_frame_noise_variance(env):
+    """jbp_batch.sigma2 with the DFT node: frames of three SNRs in one batch, each
+    decoded with its own noise variance (the kernel scores every channel use with
+    its frame's sigma2), against the oracle run at that SNR (step form, few
+    iterations of the config-3 shape: decisions above margin 2e-2, iterations equal)."""
+    jbp, O, torch = env
+    K, q, n, T = 4, 64, 64, 3
+    code = I.make_code(n, q)
+    snrs = [10.0, 14.0, 18.0]
+    parts = [I.make_frames(code, K, s, 6, seed=410 + i, perm_seed=410) for i, s in enumerate(snrs)]
+    y = np.concatenate([p["y"] for p in parts])
+    sig = np.concatenate([np.full(6, p["sigma2"], np.float32) for p in parts])
+    ctx, dec = _decoder(jbp, code, K, 1.0, parts[0]["perm"], iters=T, early_stop=True)
+    try:
+        assert dec.channel_node == jbp.CHAN_DFT
+        got = dec.decode(y, sigma2=sig)
+    finally:
+        dec.close()
+        ctx.close()
+    for i, p in enumerate(parts):
+        ref = O.decode(code, K, float(np.float32(p["sigma2"])), p["perm"], p["y"], T, early_stop=True,
+                       want_margin=True)
+        sl = slice(6 * i, 6 * (i + 1))
+        diff = got["hat"][sl] != ref["hat"]
+        print("per-frame sigma2, %.0f dB: %d decisions differ, %d at margin > 2e-2"
+              % (snrs[i], int(diff.sum()), int((diff & (ref["margin"] > 2e-2)).sum())))
+        assert not (diff & (ref["margin"] > 2e-2)).any()
+        assert (got["iters"][sl] == ref["iters"]).all()
+
+
+def test_dft_not_built_for_variable_degree_three(env):
+    """The transform node gathers two c2v messages per variable; a (3, 4) code keeps
+    the trellis under JBP_CHAN_DFT."""
+    jbp, O, torch = env
+    code = I.make_code(64, 16, dv=3, dc=4)
+    fr = I.make_frames(code, 4, 12.0, 2, seed=3)
+    ctx, dec = _decoder(jbp, code, 4, fr["sigma2"], fr["perm"], iters=2)
+    try:
+        assert dec.channel_node == jbp.CHAN_TRELLIS
+        assert dec.decode(fr["y"])["hat"].shape == (2, 4, 64)
+    finally:
+        dec.close()
+        ctx.close()
