@@ -354,3 +354,35 @@ def test_dft_not_built_for_variable_degree_three(env):
     finally:
         dec.close()
         ctx.close()
+
+
+@pytest.mark.parametrize("K,q,n,F", [(4, 64, 128, 200), (8, 64, 48, 500), (4, 16, 256, 100)])
+def test_dft_many_tiles_equal_small_batches(env, K, q, n, F):
+    """A launch of more tiles than CTAs (each CTA runs several tiles: its shared and
+    tensor memory, mbarrier phases and DFT-row prefetch carry over) gives, bit for
+    bit, what the same frames give two at a time (one tile each, checked against
+    the oracle by the tests above): every channel use's products are independent
+    of the other rows of its tile."""
+    jbp, O, torch = env
+    code = I.make_code(n, q)
+    fr = I.make_frames(code, K, 14.0, F, seed=500 + K + q)
+    rng = np.random.default_rng(501)
+    E = code["P"] * code["dc"]
+    c2v = np.exp(I.random_log_messages(rng, (F, K, E), q, spread=3.0)).astype(np.float32)
+    ctx, dec = _decoder(jbp, code, K, fr["sigma2"], fr["perm"])
+    try:
+        y_d = torch.from_numpy(fr["y"]).cuda()
+        big_msg = torch.from_numpy(c2v).cuda()
+        big_ch = torch.empty((F, K, n, q), dtype=torch.float32, device="cuda")
+        dec.step_channel(y_d, big_msg, big_ch)
+        small_msg = torch.from_numpy(c2v).cuda()
+        small_ch = torch.empty_like(big_ch)
+        for f0 in range(0, F, 2):
+            dec.step_channel(y_d[f0:f0 + 2], small_msg[f0:f0 + 2], small_ch[f0:f0 + 2])
+        torch.cuda.synchronize()
+        assert dec.tc_timeouts() == 0
+        assert torch.equal(big_ch, small_ch)
+        assert torch.equal(big_msg, small_msg)
+    finally:
+        dec.close()
+        ctx.close()
