@@ -185,12 +185,14 @@ int jbp_decode(jbp_h *h, jbp_batch *batch);
  * of one context in one call: the parts run concurrently on the context's
  * stream pool (parts of one handle run in order on one stream; at most 32
  * distinct handles).  Every batch must have on_device = 1.  Work is ordered
- * after prior work on `stream` (NULL = the context's stream) and completion is
- * ordered before later work on it; the call returns without waiting.  The
- * first call with a given argument set autotunes each fused part's launch
- * shape (jbp_tune) and runs eagerly; the second captures the whole
- * multi-part decode as one CUDA graph, which later calls with identical
- * arguments (handles, sizes, pointers, stream) replay with one launch. */
+ * after prior work on `stream` (NULL = the context's stream; any stream,
+ * cudaStreamLegacy included) and completion is ordered before later work on
+ * it, through events: the decode itself runs on a stream of the context.  The
+ * call returns without waiting.  The first call with a given argument set
+ * autotunes each fused part's launch shape (jbp_tune) and runs eagerly; the
+ * second captures the whole multi-part decode as one CUDA graph, which later
+ * calls with identical arguments (handles, sizes, pointers) replay with one
+ * launch, whatever the caller's stream. */
 int jbp_decode_many(jbp_ctx *ctx, int32_t nparts, jbp_h *const *handles, const jbp_batch *batches, void *stream);
 
 /* Autotune the fused-form launch shape of a handle on a device batch (runs a

@@ -189,6 +189,11 @@ struct jbp_ctx {
     std::vector<cudaStream_t> pool;
     std::vector<cudaEvent_t> pool_ev;
     cudaEvent_t fork_ev = nullptr;
+    // jbp_decode_many runs (and captures) on its own stream, ordered after and
+    // before the caller's stream by these events: any caller stream works, the
+    // legacy default stream included, and a captured graph serves every caller
+    cudaStream_t many_stream = nullptr;
+    cudaEvent_t many_in = nullptr, many_out = nullptr;
     struct GraphEntry {
         int seen = 0;
         cudaGraphExec_t exec = nullptr;
@@ -463,6 +468,9 @@ extern "C" int jbp_context_destroy(jbp_ctx* ctx)
     for (cudaStream_t st : ctx->pool) cudaStreamDestroy(st);
     for (cudaEvent_t ev : ctx->pool_ev) cudaEventDestroy(ev);
     if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+    if (ctx->many_stream) cudaStreamDestroy(ctx->many_stream);
+    if (ctx->many_in) cudaEventDestroy(ctx->many_in);
+    if (ctx->many_out) cudaEventDestroy(ctx->many_out);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return JBP_OK;
@@ -715,6 +723,7 @@ extern "C" int jbp_destroy(jbp_h* h)
         // graphs captured with this handle refer to its tables and workspace
         std::lock_guard<std::mutex> lk(ctx->many_mu);
         for (cudaStream_t st : ctx->pool) cudaStreamSynchronize(st);
+        if (ctx->many_stream) cudaStreamSynchronize(ctx->many_stream);
         for (auto it = ctx->graphs.begin(); it != ctx->graphs.end();) {
             bool uses = false;
             for (size_t i = 1; i < it->first.size(); i += 10)
@@ -927,6 +936,9 @@ static int many_enqueue(jbp_ctx* ctx, int nparts, jbp_h* const* handles, const j
     return JBP_OK;
 }
 
+static int many_run(jbp_ctx* ctx, int32_t nparts, jbp_h* const* handles, const jbp_batch* batches,
+                    cudaStream_t main);
+
 extern "C" int jbp_decode_many(jbp_ctx* ctx, int32_t nparts, jbp_h* const* handles, const jbp_batch* batches,
                                void* stream)
 {
@@ -947,10 +959,26 @@ extern "C" int jbp_decode_many(jbp_ctx* ctx, int32_t nparts, jbp_h* const* handl
             JBP_CU(cudaEventCreateWithFlags(&ctx->pool_ev[i], cudaEventDisableTiming), "pool event");
         }
         JBP_CU(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming), "fork event");
+        JBP_CU(cudaStreamCreateWithFlags(&ctx->many_stream, cudaStreamNonBlocking), "many stream");
+        JBP_CU(cudaEventCreateWithFlags(&ctx->many_in, cudaEventDisableTiming), "many event");
+        JBP_CU(cudaEventCreateWithFlags(&ctx->many_out, cudaEventDisableTiming), "many event");
     }
-    cudaStream_t main = stream ? (cudaStream_t)stream : ctx->stream;
+    const cudaStream_t user = stream ? (cudaStream_t)stream : ctx->stream;
+    const cudaStream_t main = ctx->many_stream;
+    JBP_CU(cudaEventRecord(ctx->many_in, user), "many: order after the caller");
+    JBP_CU(cudaStreamWaitEvent(main, ctx->many_in, 0), "many: order after the caller");
+    const int rc = many_run(ctx, nparts, handles, batches, main);
+    JBP_CU(cudaEventRecord(ctx->many_out, main), "many: order before the caller");
+    JBP_CU(cudaStreamWaitEvent(user, ctx->many_out, 0), "many: order before the caller");
+    return rc;
+}
+
+// jbp_decode_many's work on its own stream: eager on the first call with given
+// arguments, captured into a graph on the second, replayed from then on
+static int many_run(jbp_ctx* ctx, int32_t nparts, jbp_h* const* handles, const jbp_batch* batches,
+                    cudaStream_t main)
+{
     std::vector<uintptr_t> key;
-    key.push_back((uintptr_t)main);
     for (int i = 0; i < nparts; ++i) {
         const jbp_batch& b = batches[i];
         for (uintptr_t v : {(uintptr_t)handles[i], (uintptr_t)handles[i]->ws.gen, (uintptr_t)b.F, (uintptr_t)b.y,

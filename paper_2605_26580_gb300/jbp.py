@@ -20,6 +20,7 @@ OK, EINVAL, ENOMEM, ECUDA, EAGAIN, ETIMEOUT, ECLOSED = range(7)
 PREC_FP32, PREC_BF16X2, PREC_BF16, PREC_BF16X3 = 0, 1, 2, 3
 FORM_AUTO, FORM_FUSED, FORM_STEP, FORM_PLAIN = 0, 1, 2, 3
 CHAN_TRELLIS, CHAN_DFT, CHAN_AUTO = 0, 1, 2
+CUDA_STREAM_LEGACY = 0x1   # the CUDA runtime's explicit handle of the legacy default stream
 
 EXPORTS = [
     "jbp_context_create", "jbp_context_destroy", "jbp_create", "jbp_destroy", "jbp_decode",
@@ -126,10 +127,20 @@ def _addr(x):
     return x.data_ptr()
 
 
-def _stream_ptr(stream):
-    if stream is None:
-        return None
-    return getattr(stream, "cuda_stream", stream)
+def _stream_ptr(stream, t=None):
+    """The stream of a call on device buffers: the given one; else, for torch CUDA
+    tensors, torch's current stream on their device, so that the call is ordered
+    after the work that produced them (the handle's own stream does not wait for
+    torch's); else NULL (the handle's stream)."""
+    if stream is not None:
+        return getattr(stream, "cuda_stream", stream)
+    if t is not None and getattr(t, "is_cuda", False):
+        import torch
+        h = torch.cuda.current_stream(t.device).cuda_stream
+        # torch's default stream is the legacy default stream, whose handle 0 the C
+        # ABI reads as "the handle's own stream": pass its explicit handle instead
+        return h if h else CUDA_STREAM_LEGACY
+    return None
 
 
 class Context:
@@ -166,7 +177,7 @@ class Context:
             sig = p[5] if len(p) > 5 else None
             bs[i] = Batch(int(y.shape[0]), _addr(y), _addr(hat), _addr(it), _addr(ok), None, 1, FORM_AUTO, None,
                           _addr(sig))
-        check(lib().jbp_decode_many(self.ptr, n, hs, bs, _stream_ptr(stream)))
+        check(lib().jbp_decode_many(self.ptr, n, hs, bs, _stream_ptr(stream, parts[0][1] if parts else None)))
 
     def match_rows(self, hat, truth):
         """Row-aligned errors (host arrays [F, K, n]): (symbol errors [F], row errors [F])."""
@@ -181,7 +192,7 @@ class Context:
     def match_rows_device(self, hat, truth, sym, cw, stream=None):
         F, K, n = truth.shape
         check(lib().jbp_match_rows(self.ptr, int(F), int(K), int(n), _addr(hat), _addr(truth), _addr(sym), _addr(cw),
-                                   1, _stream_ptr(stream)))
+                                   1, _stream_ptr(stream, hat)))
 
     def serving_stats(self):
         c = C.c_uint64()
@@ -251,7 +262,7 @@ class Decoder:
     def decode_device(self, y, hat, iters, ok, post=None, form: int = FORM_AUTO, stream=None, sigma2=None):
         """Enqueue a decode on device tensors (returns without waiting)."""
         b = Batch(int(y.shape[0]), _addr(y), _addr(hat), _addr(iters), _addr(ok), _addr(post), 1, int(form),
-                  _stream_ptr(stream), _addr(sigma2))
+                  _stream_ptr(stream, y), _addr(sigma2))
         check(lib().jbp_decode(self.ptr, C.byref(b)))
 
     def set_launch(self, threads: int, frames_per_cta: int = 0):
@@ -260,7 +271,7 @@ class Decoder:
 
     def tune(self, y, hat, iters, ok, sigma2=None, stream=None):
         b = Batch(int(y.shape[0]), _addr(y), _addr(hat), _addr(iters), _addr(ok), None, 1, FORM_AUTO,
-                  _stream_ptr(stream), _addr(sigma2))
+                  _stream_ptr(stream, y), _addr(sigma2))
         th, fc = C.c_int32(), C.c_int32()
         check(lib().jbp_tune(self.ptr, C.byref(b), C.byref(th), C.byref(fc)))
         return th.value, fc.value
@@ -274,17 +285,18 @@ class Decoder:
 
     # -- single steps on device tensors ---------------------------------------
     def step_channel(self, y, msg, ch2v, stream=None):
-        check(lib().jbp_step_channel(self.ptr, int(y.shape[0]), _addr(y), _addr(msg), _addr(ch2v), _stream_ptr(stream)))
+        check(lib().jbp_step_channel(self.ptr, int(y.shape[0]), _addr(y), _addr(msg), _addr(ch2v),
+                                     _stream_ptr(stream, msg)))
 
     def step_check(self, msg, precision: int = PREC_FP32, stream=None):
-        check(lib().jbp_step_check(self.ptr, int(msg.shape[0]), _addr(msg), int(precision), _stream_ptr(stream)))
+        check(lib().jbp_step_check(self.ptr, int(msg.shape[0]), _addr(msg), int(precision), _stream_ptr(stream, msg)))
 
     def step_var(self, ch2v, msg, post, hat, stream=None):
         check(lib().jbp_step_var(self.ptr, int(ch2v.shape[0]), _addr(ch2v), _addr(msg), _addr(post), _addr(hat),
-                                 _stream_ptr(stream)))
+                                 _stream_ptr(stream, msg)))
 
     def step_syndrome(self, hat, ok, stream=None):
-        check(lib().jbp_step_syndrome(self.ptr, int(hat.shape[0]), _addr(hat), _addr(ok), _stream_ptr(stream)))
+        check(lib().jbp_step_syndrome(self.ptr, int(hat.shape[0]), _addr(hat), _addr(ok), _stream_ptr(stream, hat)))
 
 
 class EvidenceDecoder:
@@ -342,12 +354,12 @@ class EvidenceDecoder:
 
     # device tensors: enqueued on `stream`, no wait
     def evidence_device(self, y, S, stream=None):
-        check(lib().jbp_amp_evidence(self.ptr, int(y.shape[0]), _addr(y), _addr(S), 1, _stream_ptr(stream)))
+        check(lib().jbp_amp_evidence(self.ptr, int(y.shape[0]), _addr(y), _addr(S), 1, _stream_ptr(stream, y)))
 
     def sic_device(self, S, hat, iters, ok, stream=None):
         check(lib().jbp_sic_decode(self.ptr, int(S.shape[0]), _addr(S), _addr(hat), _addr(iters), _addr(ok), 1,
-                                   _stream_ptr(stream)))
+                                   _stream_ptr(stream, S)))
 
     def decode_device(self, y, hat, iters, ok, stream=None):
         check(lib().jbp_ura_decode(self.ptr, int(y.shape[0]), _addr(y), _addr(hat), _addr(iters), _addr(ok), 1,
-                                   _stream_ptr(stream)))
+                                   _stream_ptr(stream, y)))

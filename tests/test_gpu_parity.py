@@ -589,3 +589,52 @@ def test_step_entry_points_refuse_misaligned_buffers(env):
     finally:
         dec.close()
         ctx.close()
+
+
+@pytest.mark.parametrize("K,q,n,F", [(4, 16, 256, 200), (4, 64, 128, 60), (3, 32, 64, 150)])
+def test_step_kernels_many_tiles_equal_small_batches(env, K, q, n, F):
+    """Persistent step kernels over more tiles than CTAs -- the TMA-staged check
+    (double-buffered tiles carry over from one tile to the next), the tensor-core
+    check variants, the team-shape and thread-shape channel node and the variable
+    node -- give, bit for bit, what the same frames give two at a time (one tile
+    per CTA, the case the oracle comparisons above cover): no unit reads another
+    unit's data."""
+    jbp, O, torch = env
+    code = I.make_code(n, q)
+    fr = I.make_frames(code, K, 12.0, F, seed=600 + K + q)
+    rng = np.random.default_rng(601)
+    E = code["P"] * code["dc"]
+    msg0 = np.exp(I.random_log_messages(rng, (F, K, E), q, spread=3.0)).astype(np.float32)
+    precs = [0, 3, 1] if q >= 16 else [0]
+    ctx, dec = _decoder(jbp, code, K, fr["sigma2"], fr["perm"])
+    try:
+        y_d = torch.from_numpy(fr["y"]).cuda()
+
+        def run(frames):
+            outs = []
+            msg = torch.from_numpy(msg0).cuda()
+            ch = torch.zeros((F, K, n, q), dtype=torch.float32, device="cuda")
+            hat = torch.zeros((F, K, n), dtype=torch.uint8, device="cuda")
+            for f0 in range(0, F, frames):
+                sl = slice(f0, min(F, f0 + frames))
+                dec.step_channel(y_d[sl], msg[sl], ch[sl])
+            outs += [msg.clone(), ch.clone()]
+            for prec in precs:
+                m = msg.clone()
+                for f0 in range(0, F, frames):
+                    dec.step_check(m[f0:f0 + frames], precision=prec)
+                outs.append(m)
+            for f0 in range(0, F, frames):
+                sl = slice(f0, min(F, f0 + frames))
+                dec.step_var(ch[sl], outs[2][sl], None, hat[sl])
+            outs.append(hat)
+            torch.cuda.synchronize()
+            return outs
+
+        big, small = run(F), run(2)
+        assert dec.tc_timeouts() == 0
+        for i, (a, b) in enumerate(zip(big, small)):
+            assert torch.equal(a, b), i
+    finally:
+        dec.close()
+        ctx.close()
