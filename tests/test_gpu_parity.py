@@ -638,3 +638,25 @@ def test_step_kernels_many_tiles_equal_small_batches(env, K, q, n, F):
     finally:
         dec.close()
         ctx.close()
+
+
+@pytest.mark.parametrize("K,q,n,fpc", [(4, 16, 256, 1), (2, 4, 64, 2), (3, 8, 64, 4)])
+def test_fused_many_groups_equal_small_batches(env, K, q, n, fpc):
+    """The fused kernel over more frame groups than CTAs (each CTA re-initialises its
+    shared-memory state between groups; fpc frames per group, the last group partly
+    filled) gives, bit for bit, what the same frames give two at a time: frames
+    never share arithmetic, and the oracle comparisons above use one group per CTA."""
+    jbp, O, torch = env
+    code = I.make_code(n, q)
+    F = 152 * fpc * 2 + 6            # every CTA runs at least two groups, the last one partly filled
+    fr = I.make_frames(code, K, 12.0, F, seed=700 + K + q)
+    ctx, dec = _decoder(jbp, code, K, fr["sigma2"], fr["perm"], iters=12, early_stop=True)
+    try:
+        dec.set_launch(256, fpc)
+        big = dec.decode(fr["y"], form=jbp.FORM_FUSED)
+        small = [dec.decode(fr["y"][f0:f0 + 2], form=jbp.FORM_FUSED) for f0 in range(0, F, 2)]
+    finally:
+        dec.close()
+        ctx.close()
+    for key in ("hat", "iters", "ok"):
+        assert np.array_equal(big[key], np.concatenate([s[key] for s in small])), key
