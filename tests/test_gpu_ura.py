@@ -229,3 +229,27 @@ def test_gpu_row_matching_equals_host_alignment(jbp_lib, K, n, F):
         ctx.close()
     hsym, hcw = I.match_rows(hat, truth)
     assert np.array_equal(sym, hsym) and np.array_equal(cw, hcw)
+
+
+@pytest.mark.parametrize("L", [12, 48])
+def test_evidence_path_many_frames_equal_small_batches(jbp_lib, L):
+    """The detector (one warp per slot) and the SIC kernel (one warp per frame) over
+    more frames than resident warps, so that warps and their shared memory are
+    reused, give bit for bit what the same frames give two at a time (the oracle
+    comparisons above use a few frames)."""
+    ctx = _ctx(jbp_lib)
+    code = I.make_code(L, 64, dv=2, dc=3)
+    F = 6000 if L == 12 else 1500
+    fr = I.make_ura_frames(code, 2, 10.0, F, seed=800 + L)
+    dec = jbp_lib.EvidenceDecoder(ctx, code, 2, fr["rows"], fr["rho"], fr["su2"], fr["cancel_log"])
+    try:
+        S = dec.evidence(fr["y"])
+        rows = dec.sic(S)
+        S_small = np.concatenate([dec.evidence(fr["y"][f0:f0 + 2]) for f0 in range(0, F, 2)])
+        rows_small = [dec.sic(S[f0:f0 + 2]) for f0 in range(0, F, 2)]
+    finally:
+        dec.close()
+        ctx.close()
+    assert np.array_equal(S, S_small)
+    for key in ("hat", "iters", "ok"):
+        assert np.array_equal(rows[key], np.concatenate([r[key] for r in rows_small])), key
