@@ -289,6 +289,30 @@ int jbp_query(jbp_h *h, int32_t *E, int64_t *state_bytes_per_frame, int32_t *fus
  * counterpart: an implementation query. */
 int jbp_query_channel(jbp_h *h, int32_t *channel_node);
 
+/* Host only (no GPU, no context): the constant operand tables the DFT channel
+ * node of (K, q) loads, as jbp_create builds them, for inspection and tests.
+ * shape (may be NULL) receives {L, W, KB, Nc, chunks}: DFT length L = the first
+ * multiple of 16 >= K(q-1)+1; Gaussian-score window W = min(L, 128); forward
+ * inner width KB = max(q, W); Nc spectral rows per chunk; chunks = L / Nc.
+ * *bytes (required) receives the table size; out (may be NULL) receives the
+ * tables, host memory owned by the caller, at least *bytes long:
+ *   per chunk c = 0..chunks-1, four tiles of FP16 values:
+ *     forward hi, forward lo  [Nc x KB], element (r, x) = F(c*Nc + r, x)
+ *     inverse hi, inverse lo  [q x Nc],  element (a, r) = B(a, c*Nc + r)
+ *   then L float pairs (cos, sin)(2 pi m / L), m = 0..L-1.
+ * F(n, x): spectral row n of the length-L real DFT folded onto frequencies
+ * 0..L/2 (pair p = n/2; n = 0: 1, n = 1: (-1)^x (the Nyquist term); else n
+ * even: cos, n odd: -sin of 2 pi p x / L).  B(a, n): the inverse over that
+ * folded spectrum (n = 0: 1; n = 1: (-1)^a; else n even: 2 cos, n odd: -2 sin
+ * of 2 pi p a / L), so that sum_n B(a, n) F(n, x) = L [a == x].  hi = the FP16
+ * rounding of the value, lo = the FP16 rounding of the remainder.  A (rows x D)
+ * tile stores element (m, k) at byte (m/8)(D/8)128 + (k/8)128 + (m%8)16 + (k%8)2
+ * (8x8 core matrices of 128 bytes, consecutive along k, then along m).
+ * Returns JBP_EINVAL if (K, q) has no DFT form (q not 16, 32 or 64, K not
+ * 2..8) or bytes is NULL.  No paper counterpart: the paper prints no
+ * channel-node kernel; the node computed is kernel (a) above. */
+int jbp_dft_tables(int32_t K, int32_t q, int32_t *shape, void *out, int64_t *bytes);
+
 /* ---- the paper's own classical path on the evidence interface S ----
  *
  * The paper's baseline decoders (appendix "Complexity derivation", paragraphs

@@ -770,6 +770,24 @@ extern "C" int jbp_query_channel(jbp_h* h, int32_t* node)
     return JBP_OK;
 }
 
+extern "C" int jbp_dft_tables(int32_t K, int32_t q, int32_t* shape, void* out, int64_t* bytes)
+{
+    if (!bytes) return fail(JBP_EINVAL, "jbp_dft_tables: NULL bytes");
+    if (q != 16 && q != 32 && q != 64) return fail(JBP_EINVAL, "jbp_dft_tables: q = %d (16, 32 or 64)", q);
+    const DftShape S = dft_shape(K, q);
+    if (!S.ok) return fail(JBP_EINVAL, "jbp_dft_tables: no DFT form for K = %d, q = %d", K, q);
+    *bytes = (int64_t)dft_table_bytes(K, q);
+    if (shape) {
+        shape[0] = S.L;
+        shape[1] = S.W;
+        shape[2] = S.KB;
+        shape[3] = S.Nc;
+        shape[4] = S.chunks;
+    }
+    if (out) dft_build_table(K, q, static_cast<unsigned char*>(out));
+    return JBP_OK;
+}
+
 extern "C" int jbp_stats(jbp_h* h, uint64_t* log_fallbacks, int32_t* tc_timeouts)
 {
     if (!h) return fail(JBP_EINVAL, "jbp_stats: NULL handle");

@@ -716,10 +716,12 @@ static double inverse_entry(int n, int a, int L)
 }
 
 // FP16 hi and lo terms of x at (row, col) of a (rows x KD) tile; lo tile at +tile_bytes.
+// Both are rounded from double directly: through float first, a value just past
+// an FP16 midpoint can land on it and round the wrong way.
 static void put_split(unsigned char* tile, size_t tile_bytes, int row, int col, int KD, double x)
 {
-    const __half hi = __float2half_rn((float)x);
-    const __half lo = __float2half_rn((float)(x - (double)__half2float(hi)));
+    const __half hi = __double2half(x);
+    const __half lo = __double2half(x - (double)__half2float(hi));
     const size_t off = tc::tile_off(row, col / 8, KD) + (col % 8) * 2;
     std::memcpy(tile + off, &hi, 2);
     std::memcpy(tile + tile_bytes + off, &lo, 2);

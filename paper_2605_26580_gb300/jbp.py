@@ -25,7 +25,7 @@ CUDA_STREAM_LEGACY = 0x1   # the CUDA runtime's explicit handle of the legacy de
 EXPORTS = [
     "jbp_context_create", "jbp_context_destroy", "jbp_create", "jbp_destroy", "jbp_decode",
     "jbp_submit", "jbp_poll", "jbp_serving_stats", "jbp_last_error", "jbp_step_channel",
-    "jbp_step_check", "jbp_step_var", "jbp_step_syndrome", "jbp_query", "jbp_query_channel", "jbp_decode_noalloc", "jbp_stats", "jbp_decode_many", "jbp_tune",
+    "jbp_step_check", "jbp_step_var", "jbp_step_syndrome", "jbp_query", "jbp_query_channel", "jbp_dft_tables", "jbp_decode_noalloc", "jbp_stats", "jbp_decode_many", "jbp_tune",
     "jbp_ura_create", "jbp_ura_destroy", "jbp_amp_evidence", "jbp_sic_decode", "jbp_ura_decode", "jbp_match_rows",
 ]
 
@@ -92,6 +92,7 @@ def lib():
             L.jbp_step_syndrome.argtypes = [vp, i32, vp, vp, vp]
             L.jbp_query.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]
             L.jbp_query_channel.argtypes = [vp, C.POINTER(i32)]
+            L.jbp_dft_tables.argtypes = [i32, i32, C.POINTER(i32), vp, C.POINTER(i64)]
             L.jbp_decode_many.argtypes = [vp, i32, C.POINTER(vp), C.POINTER(Batch), vp]
             L.jbp_tune.argtypes = [vp, C.POINTER(Batch), C.POINTER(i32), C.POINTER(i32)]
             L.jbp_stats.argtypes = [vp, C.POINTER(u64), C.POINTER(i32)]
@@ -141,6 +142,17 @@ def _stream_ptr(stream, t=None):
         # ABI reads as "the handle's own stream": pass its explicit handle instead
         return h if h else CUDA_STREAM_LEGACY
     return None
+
+
+def dft_tables(K: int, q: int):
+    """Host-only: the DFT channel node's constant tables for (K, q) as jbp_create
+    builds them.  Returns (shape dict with L, W, KB, Nc, chunks; uint8 array)."""
+    shape = (C.c_int32 * 5)()
+    nbytes = C.c_int64()
+    check(lib().jbp_dft_tables(K, q, shape, None, C.byref(nbytes)))
+    out = np.zeros(nbytes.value, dtype=np.uint8)
+    check(lib().jbp_dft_tables(K, q, None, out.ctypes.data, C.byref(nbytes)))
+    return dict(zip(("L", "W", "KB", "Nc", "chunks"), list(shape))), out
 
 
 class Context:
