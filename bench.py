@@ -170,8 +170,8 @@ def run_reference(args) -> None:
     from oracle import oracle as O
     O.build()
     from paper_2605_26580_gb300 import inputs as I
-    cores = os.cpu_count() or 1
-    S = args.ref_frames or max(4, cores)
+    S = args.ref_frames or max(4, os.cpu_count() or 1)
+    cores = min(os.cpu_count() or 1, S)      # the oracle spreads frames over threads
     code = I.make_code(N_SYM, Q)
     base = I.make_frames(code, K_USERS, SNRS[0], S, seed=frame_seed(0, 0))
     samples = []
