@@ -66,3 +66,44 @@ def test_no_gpu_fails_loudly(jbp_lib):
     with pytest.raises(jbp_lib.JBPError) as ei:
         jbp_lib.Context(iters=5)
     assert ei.value.code in (jbp_lib.ECUDA, jbp_lib.EINVAL)
+
+
+def _prototypes():
+    """name -> parameter type strings, parsed from the header's declarations."""
+    src = open(os.path.join(ROOT, "include", "jbp.h")).read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"^\s*int\s+(jbp_\w+)\s*\(([^)]*)\)\s*;", src, re.M):
+        params = [" ".join(p.split()) for p in m.group(2).split(",") if p.strip() and p.strip() != "void"]
+        out[m.group(1)] = params
+    return out
+
+
+def _null_args(params):
+    """Every pointer NULL, every integer 1, every double 1.0 (typed for the C ABI)."""
+    args = []
+    for p in params:
+        if "*" in p:
+            args.append(None)
+        elif p.startswith("double"):
+            args.append(C.c_double(1.0))
+        elif "int64_t" in p:
+            args.append(C.c_uint64(1) if p.startswith("uint") else C.c_int64(1))
+        else:
+            args.append(C.c_int32(1))
+    return args
+
+
+def test_every_entry_point_refuses_null_pointers(jbp_lib):
+    """Each entry point called with all pointers NULL returns EINVAL and sets a
+    message, before any device work (this host has no GPU)."""
+    lib = C.CDLL(jbp_lib.LIB_PATH)
+    lib.jbp_last_error.restype = C.c_char_p
+    protos = _prototypes()
+    assert set(protos) | {"jbp_last_error"} == set(_declared())
+    for name, params in protos.items():
+        fn = getattr(lib, name)
+        fn.restype = C.c_int
+        rc = fn(*_null_args(params))
+        assert rc == jbp_lib.EINVAL, (name, rc)
+        assert lib.jbp_last_error(), name
