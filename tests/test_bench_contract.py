@@ -6,6 +6,8 @@ import os
 import subprocess
 import sys
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -41,3 +43,32 @@ def test_reference_arm_other_ranks_exit_without_work():
              "--gpus", "2")
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_uneven_batch_waves_respect_the_memory_budget():
+    """Classes of the uneven batch are grouped into waves whose HBM message state
+    fits the budget; fused classes hold no HBM state; every class runs once."""
+    sys.path.insert(0, ROOT)
+    import bench
+    rng = np.random.default_rng(5)
+    parts = [{"id": i, "state": int(rng.integers(1, 50)) * 1000, "F": int(rng.integers(1, 20)),
+              "fused": bool(rng.random() < 0.3)} for i in range(40)]
+    budget = 200_000
+    waves = bench._waves(parts, budget)
+    ids = sorted(p["id"] for w in waves for p in w)
+    assert ids == list(range(40))
+    for w in waves:
+        need = sum(0 if p["fused"] else p["state"] * p["F"] for p in w)
+        assert need <= budget or len(w) == 1 or sum(not p["fused"] for p in w) == 1
+    assert len(bench._waves(parts, 10 ** 12)) == 1
+
+
+def test_uneven_classes_cover_every_frame():
+    sys.path.insert(0, ROOT)
+    import bench
+    classes, snr = bench._uneven_classes(2000, seed=9)
+    frames = sorted(f for idx in classes.values() for f in idx)
+    assert frames == list(range(2000)) and snr.shape == (2000,)
+    for (n, q, K) in classes:
+        assert n in (128, 256, 512, 1024, 2048) and q in (16, 64) and 2 <= K <= 8
+    assert ((8.0 <= snr) & (snr <= 16.0)).all()
