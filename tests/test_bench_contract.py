@@ -1,6 +1,7 @@
-"""bench.py's reference arm (the FP64 oracle timed on the host cores) runs on the
-CPU: its JSON line carries the keys of the bench contract, and under a
-multi-rank launch only rank 0 does work."""
+"""bench.py's host logic on the CPU.  The reference arm (the FP64 oracle timed on
+the host cores) prints one line with the keys of the bench contract, and under a
+multi-rank launch only rank 0 does work; the uneven batch splits into (n, q, K)
+classes that cover every frame and into memory waves within the budget."""
 import json
 import os
 import subprocess
