@@ -289,6 +289,16 @@ int jbp_query(jbp_h *h, int32_t *E, int64_t *state_bytes_per_frame, int32_t *fus
  * counterpart: an implementation query. */
 int jbp_query_channel(jbp_h *h, int32_t *channel_node);
 
+/* Host only (no GPU, no context): the GF(q) tables jbp_create uploads for the
+ * check node's coefficient permutations (step a0 of the decoder's setup), for
+ * inspection and tests.  q = 2, 4, ..., 64 with the field polynomials listed at
+ * the top of this file.  mul and div (host pointers owned by the caller, q*q
+ * bytes each) receive mul[h*q + x] = h x and div[h*q + x] = h^{-1} x (row h = 0
+ * of div is zero).  Returns JBP_EINVAL for another q or a NULL table.  The
+ * field arithmetic is that of the parity checks, appendix "Q-ary LDPC code",
+ * eq. app_ldpc_check_eq: sums over GF(q) of symbols times nonzero entries of H. */
+int jbp_gf_tables(int32_t q, uint8_t *mul, uint8_t *div);
+
 /* Host only (no GPU, no context): the constant operand tables the DFT channel
  * node of (K, q) loads, as jbp_create builds them, for inspection and tests.
  * shape (may be NULL) receives {L, W, KB, Nc, chunks}: DFT length L = the first

@@ -25,7 +25,7 @@ CUDA_STREAM_LEGACY = 0x1   # the CUDA runtime's explicit handle of the legacy de
 EXPORTS = [
     "jbp_context_create", "jbp_context_destroy", "jbp_create", "jbp_destroy", "jbp_decode",
     "jbp_submit", "jbp_poll", "jbp_serving_stats", "jbp_last_error", "jbp_step_channel",
-    "jbp_step_check", "jbp_step_var", "jbp_step_syndrome", "jbp_query", "jbp_query_channel", "jbp_dft_tables", "jbp_decode_noalloc", "jbp_stats", "jbp_decode_many", "jbp_tune",
+    "jbp_step_check", "jbp_step_var", "jbp_step_syndrome", "jbp_query", "jbp_query_channel", "jbp_dft_tables", "jbp_gf_tables", "jbp_decode_noalloc", "jbp_stats", "jbp_decode_many", "jbp_tune",
     "jbp_ura_create", "jbp_ura_destroy", "jbp_amp_evidence", "jbp_sic_decode", "jbp_ura_decode", "jbp_match_rows",
 ]
 
@@ -93,6 +93,7 @@ def lib():
             L.jbp_query.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]
             L.jbp_query_channel.argtypes = [vp, C.POINTER(i32)]
             L.jbp_dft_tables.argtypes = [i32, i32, C.POINTER(i32), vp, C.POINTER(i64)]
+            L.jbp_gf_tables.argtypes = [i32, vp, vp]
             L.jbp_decode_many.argtypes = [vp, i32, C.POINTER(vp), C.POINTER(Batch), vp]
             L.jbp_tune.argtypes = [vp, C.POINTER(Batch), C.POINTER(i32), C.POINTER(i32)]
             L.jbp_stats.argtypes = [vp, C.POINTER(u64), C.POINTER(i32)]
@@ -142,6 +143,15 @@ def _stream_ptr(stream, t=None):
         # ABI reads as "the handle's own stream": pass its explicit handle instead
         return h if h else CUDA_STREAM_LEGACY
     return None
+
+
+def gf_tables(q: int):
+    """Host-only: the GF(q) multiply and divide tables jbp_create uploads, as
+    (mul, div) uint8 arrays [q, q] with mul[h, x] = h x and div[h, x] = x / h."""
+    mul = np.zeros((q, q), dtype=np.uint8)
+    div = np.zeros((q, q), dtype=np.uint8)
+    check(lib().jbp_gf_tables(q, mul.ctypes.data, div.ctypes.data))
+    return mul, div
 
 
 def dft_tables(K: int, q: int):
