@@ -1,0 +1,118 @@
+"""The register-resident channel node's formulation, checked on the CPU.
+
+For K <= 4 and q <= 16 the GPU computes each user's extrinsic channel message
+without division by splitting the users into two halves (reading R11):
+  * K = 2: ch2v_0(a) = sum_b mu_1(b) G(a + b), and the mirror for user 1;
+  * K = 3: the prefix F_2 = mu_0 (*) mu_1 scores user 2 directly, and the
+    suffix B_2(v) = sum_b mu_2(b) G(v + b) is correlated with mu_0 (user 1) and
+    mu_1 (user 0);
+  * K = 4: P_23 = mu_2 (*) mu_3, H_23(v) = sum_s P_23(s) G(v + s), users 0 and 1
+    correlate mu_1 and mu_0 with H_23; users 2 and 3 use P_01 and H_01.
+G(u) is the Gaussian score of the sum value u, computed relative to the nearest
+symbol sum s* (reading R10): exp(-2 d (r + d) / sigma2) with d = s* - u and
+r = y - (2 s* - K(q-1)), which differs from exp(-(y - (2u - K(q-1)))^2 / (2 sigma2))
+only by the factor exp(-r^2 / (2 sigma2)) common to every u.
+Run in FP64 this must equal the oracle's trellis to rounding; run in FP32 (the
+GPU's arithmetic, sums in the kernel's order) it must meet the parity bar of
+1e-4 in log on every entry above 1e-4 of the maximum.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2605_26580_gb300 import inputs as I
+
+
+def gauss(K, q, sigma2, y, dt):
+    KD = K * (q - 1)
+    ss = int(min(max(np.rint((y + KD) * 0.5), 0), KD))
+    r = dt(y - (2 * ss - KD))
+    d = (ss - np.arange(KD + 1)).astype(dt)
+    return np.exp((dt(-2.0) * d * (r + d) * dt(1.0 / sigma2)).astype(dt)).astype(dt)
+
+
+def corr(P, X, nh, dt):
+    """H(v) = sum_s P(s) X(v + s), v = 0..nh-1, accumulated over s in order."""
+    H = np.zeros(nh, dtype=dt)
+    for s in range(P.shape[0]):
+        H = (H + P[s] * X[s:s + nh]).astype(dt)
+    return H
+
+
+def conv(A, B, dt):
+    C = np.zeros(A.shape[0] + B.shape[0] - 1, dtype=dt)
+    for i in range(A.shape[0]):
+        C[i:i + B.shape[0]] = (C[i:i + B.shape[0]] + A[i] * B).astype(dt)
+    return C
+
+
+def split_node(K, q, sigma2, y, mu, dt):
+    mu = mu.astype(dt)
+    G = gauss(K, q, sigma2, y, dt)
+    D = q - 1
+    out = [None] * K
+    if K == 1:
+        out[0] = G[:q]
+    elif K == 2:
+        out[0] = corr(mu[1], G, q, dt)
+        out[1] = corr(mu[0], G, q, dt)
+    elif K == 3:
+        F2 = conv(mu[0], mu[1], dt)
+        out[2] = corr(F2, G, q, dt)
+        B2 = corr(mu[2], G, 2 * D + 1, dt)
+        out[1] = corr(mu[0], B2, q, dt)
+        out[0] = corr(mu[1], B2, q, dt)
+    else:
+        H23 = corr(conv(mu[2], mu[3], dt), G, 2 * D + 1, dt)
+        out[0] = corr(mu[1], H23, q, dt)
+        out[1] = corr(mu[0], H23, q, dt)
+        H01 = corr(conv(mu[0], mu[1], dt), G, 2 * D + 1, dt)
+        out[2] = corr(mu[3], H01, q, dt)
+        out[3] = corr(mu[2], H01, q, dt)
+    o = np.stack(out).astype(np.float64)
+    return np.maximum(o / o.max(axis=1, keepdims=True), 1e-12)
+
+
+CASES = [(1, 16, 6.0), (2, 4, 10.0), (2, 16, 8.0), (3, 8, 12.0), (3, 16, 14.0), (4, 4, 10.0), (4, 16, 16.0),
+         (4, 16, 6.0)]
+
+
+@pytest.mark.parametrize("K,q,snr", CASES)
+def test_split_formulation_equals_the_trellis(oracle, K, q, snr):
+    m = int(math.log2(q))
+    sigma2 = (q * q - 1) / 3.0 * 10 ** (-snr / 10)
+    rng = np.random.default_rng(K * 31 + q)
+    for _ in range(8):
+        logmu = I.random_log_messages(rng, (K,), q, spread=2.5)
+        sym = rng.integers(0, q, K)
+        y = float((2 * sym - (q - 1)).sum() + rng.normal() * math.sqrt(sigma2))
+        ref = np.exp(oracle.channel_node(K, m, sigma2, y, logmu))
+        got = split_node(K, q, sigma2, y, np.exp(logmu), np.float64)
+        assert np.abs(np.log(got) - np.log(ref)).max() <= 1e-9
+
+
+@pytest.mark.parametrize("K,q,snr", CASES)
+def test_split_in_fp32_meets_the_parity_bar(oracle, K, q, snr):
+    m = int(math.log2(q))
+    sigma2 = (q * q - 1) / 3.0 * 10 ** (-snr / 10)
+    rng = np.random.default_rng(K * 37 + q)
+    worst, underflow = 0.0, 0
+    for _ in range(16):
+        lc = I.random_log_messages(rng, (2, K), q, spread=3.0)
+        logmu = lc.sum(axis=0)
+        logmu -= logmu.max(axis=-1, keepdims=True)
+        mu = np.exp(logmu).astype(np.float32)
+        sym = rng.integers(0, q, K)
+        y = float(np.float32((2 * sym - (q - 1)).sum() + rng.normal() * math.sqrt(sigma2)))
+        ref = oracle.channel_node(K, m, sigma2, y, np.log(mu.astype(np.float64)))
+        with np.errstate(invalid="ignore", divide="ignore"):
+            got = np.log(split_node(K, q, sigma2, y, mu, np.float32))
+        if not np.isfinite(got).all():   # all scores underflowed: the kernel's log-space fallback takes it
+            underflow += 1
+            continue
+        mask = ref >= math.log(1e-4)
+        worst = max(worst, float(np.abs(got - ref)[mask].max()))
+    print("K=%d q=%d %.0f dB: FP32 split, max log err above 1e-4: %.2e (%d underflows)" % (K, q, snr, worst, underflow))
+    assert underflow <= 2
+    assert worst <= 1e-4
