@@ -14,7 +14,9 @@ r = y - (2 s* - K(q-1)), which differs from exp(-(y - (2u - K(q-1)))^2 / (2 sigm
 only by the factor exp(-r^2 / (2 sigma2)) common to every u.
 Run in FP64 this must equal the oracle's trellis to rounding; run in FP32 (the
 GPU's arithmetic, sums in the kernel's order) it must meet the parity bar of
-1e-4 in log on every entry above 1e-4 of the maximum.
+1e-4 in log on every entry above 1e-4 of the maximum.  The team shape (any K,
+q up to 64) uses the full prefix/suffix chain instead; its formulation is pinned
+the same way in FP64, for K up to 16.
 """
 import math
 
@@ -116,3 +118,39 @@ def test_split_in_fp32_meets_the_parity_bar(oracle, K, q, snr):
     print("K=%d q=%d %.0f dB: FP32 split, max log err above 1e-4: %.2e (%d underflows)" % (K, q, snr, worst, underflow))
     assert underflow <= 2
     assert worst <= 1e-4
+
+
+def chain_node(K, q, sigma2, y, mu):
+    """Team shape (any K): prefixes F_0 = delta_0, F_{j+1} = F_j (*) mu_j; scored
+    suffixes B_K = G, B_j(v) = sum_b mu_j(b) B_{j+1}(v + b); messages
+    ch2v_k(a) ~ sum_s F_k(s) B_{k+1}(s + a).  Every prefix and suffix is
+    rescaled to max 1, as the kernel does (a constant per array)."""
+    dt = np.float64
+    D = q - 1
+    G = gauss(K, q, sigma2, y, dt)
+    F = [np.ones(1)]
+    for j in range(K - 1):
+        f = conv(F[-1], mu[j].astype(dt), dt)
+        F.append(f / f.max())
+    B = [None] * (K + 1)
+    B[K] = G / G.max()
+    for j in range(K - 1, 0, -1):
+        b = corr(mu[j].astype(dt), B[j + 1], j * D + 1, dt)
+        B[j] = b / b.max()
+    out = np.stack([corr(F[k], B[k + 1], q, dt) for k in range(K)])
+    return np.maximum(out / out.max(axis=1, keepdims=True), 1e-12)
+
+
+@pytest.mark.parametrize("K,q,snr", [(2, 32, 10.0), (5, 16, 12.0), (8, 4, 10.0), (4, 64, 14.0), (6, 32, 16.0),
+                                     (8, 64, 14.0), (16, 4, 12.0), (1, 64, 8.0)])
+def test_prefix_suffix_chain_equals_the_trellis(oracle, K, q, snr):
+    m = int(math.log2(q))
+    sigma2 = (q * q - 1) / 3.0 * 10 ** (-snr / 10)
+    rng = np.random.default_rng(K * 41 + q)
+    for _ in range(4):
+        logmu = I.random_log_messages(rng, (K,), q, spread=2.5)
+        sym = rng.integers(0, q, K)
+        y = float((2 * sym - (q - 1)).sum() + rng.normal() * math.sqrt(sigma2))
+        ref = np.exp(oracle.channel_node(K, m, sigma2, y, logmu))
+        got = chain_node(K, q, sigma2, y, np.exp(logmu))
+        assert np.abs(np.log(got) - np.log(ref)).max() <= 1e-9
