@@ -45,3 +45,19 @@ def test_other_field_sizes_are_refused(jbp_lib, q):
     with pytest.raises(jbp.JBPError) as e:
         jbp.gf_tables(q) if q > 0 else jbp.check(jbp.lib().jbp_gf_tables(q, None, None))
     assert e.value.code == jbp.EINVAL
+
+
+@pytest.mark.parametrize("m", [2, 4, 5, 6])
+def test_division_by_a_coefficient_is_linear_over_gf2(jbp_lib, m):
+    """The staged check kernel permutes by XOR of basis images: x / h is the XOR
+    of (2^i) / h over the set bits i of x, for every nonzero h."""
+    q = 1 << m
+    _, div = jbp.gf_tables(q)
+    for h in range(1, q):
+        basis = [int(div[h, 1 << i]) for i in range(m)]
+        for x in range(q):
+            acc = 0
+            for i in range(m):
+                if (x >> i) & 1:
+                    acc ^= basis[i]
+            assert acc == div[h, x], (h, x)
