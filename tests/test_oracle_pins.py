@@ -5,6 +5,7 @@ brute-force enumeration or an invariant, chosen so that a dropped term, a sign
 error, a transposed index or a wrong permutation direction in the oracle fails
 at least one of them.
 """
+import itertools
 import math
 import os
 
@@ -123,6 +124,36 @@ def test_check_wht_direct_literal_agree(oracle, m, dc):
         assert np.abs(np.exp(lit) - np.exp(wht)).max() < 1e-12
         mask = lit > math.log(1e-8)
         assert np.abs(lit - wht)[mask].max() < 1e-6
+
+
+@pytest.mark.parametrize("m,dc", [(1, 4), (2, 3), (2, 4), (3, 3)])
+def test_check_node_equals_enumeration_of_the_parity_equation(oracle, m, dc):
+    """Eq. app_ldpc_c2v by enumeration in plain Python: c2v_d(a) is proportional to
+    the sum, over the other symbols x_e with h_d a + sum_e h_e x_e = 0 in GF(q), of
+    the product of their v2c_e(x_e).  Field products come from the golden-pinned
+    multiplication (x is the generator, tables checked above)."""
+    q = 1 << m
+    mul = [[oracle.gf_mul(m, a, b) for b in range(q)] for a in range(q)]
+    rng = np.random.default_rng(100 + 10 * m + dc)
+    coef = [int(h) for h in rng.integers(1, q, dc)]
+    lv = I.random_log_messages(rng, (dc,), q, spread=2.0)
+    v = np.exp(lv)
+    ref = np.zeros((dc, q))
+    for d in range(dc):
+        others = [e for e in range(dc) if e != d]
+        for xs in itertools.product(range(q), repeat=dc - 1):
+            syn = 0
+            w = 1.0
+            for e, x in zip(others, xs):
+                syn ^= mul[coef[e]][x]
+                w *= v[e, x]
+            for a in range(q):
+                if mul[coef[d]][a] == syn:       # h_d a + syn = 0 (characteristic 2)
+                    ref[d, a] += w
+    ref /= ref.max(axis=1, keepdims=True)
+    for method in (oracle.CHECK_LITERAL, oracle.CHECK_DIRECT, oracle.CHECK_WHT):
+        got = np.exp(oracle.check_node(m, coef, lv, method, rel_floor=0.0))
+        assert np.abs(got - ref).max() < 1e-12, method
 
 
 @pytest.mark.parametrize("m", [2, 4, 6])
