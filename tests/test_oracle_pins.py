@@ -194,6 +194,53 @@ def _brute_vs_bp(oracle, code, K, perm, y, sigma2, iters):
     return pe, pb, size, out
 
 
+@pytest.mark.parametrize("q,n,checks", [(2, 8, [0, 1, 2, 3, 4, 5, 6, 7]), (4, 5, [0, 1, 2, 4])])
+def test_brute_marginals_equal_python_enumeration(oracle, q, n, checks):
+    """The oracle's exact joint marginals (the reference of the tree pins) against
+    plain enumeration: every pair of codewords (c_0, c_1) with H c_k = 0 weighted
+    by prod_t N(y_t; sum_k (2 c_k(pi_k^-1(t)) - (q-1)), sigma2), then summed per
+    user, position and symbol."""
+    m = int(math.log2(q))
+    rng = np.random.default_rng(q * 7 + n)
+    dc = 4
+    coef = rng.integers(1, q, len(checks))
+    code = I.code_from_edges(n, q, dc, checks, coef)
+    mul = [[oracle.gf_mul(m, a, b) for b in range(q)] for a in range(q)]
+    words = []
+    for x in itertools.product(range(q), repeat=n):
+        ok = True
+        for j in range(len(checks) // dc):
+            syn = 0
+            for d in range(dc):
+                e = j * dc + d
+                syn ^= mul[int(coef[e])][x[checks[e]]]
+            ok = ok and syn == 0
+        if ok:
+            words.append(x)
+    W = np.array(words)                                   # [C, n]
+    perm = np.stack([np.arange(n), rng.permutation(n)]).astype(np.int32)
+    sigma2 = 1.7
+    y = (rng.normal(size=n) * 2.0).astype(np.float32)
+    lev = [np.zeros((len(W), n)), np.zeros((len(W), n))]
+    for k in range(2):
+        lev[k][:, perm[k]] = 2.0 * W - (q - 1)           # level on channel use pi_k(i)
+    r = y.astype(np.float64)[None, None, :] - lev[0][:, None, :] - lev[1][None, :, :]
+    ll = -(r * r).sum(-1) / (2 * sigma2)                  # [C, C]
+    w = np.exp(ll - ll.max())
+    ref = np.zeros((2, n, q))
+    for i in range(n):
+        for a in range(q):
+            sel = W[:, i] == a
+            ref[0, i, a] = w[sel, :].sum()
+            ref[1, i, a] = w[:, sel].sum()
+    ref /= ref.sum(-1, keepdims=True)
+    exact, size = oracle.brute_marginals(code, 2, sigma2, perm, y)
+    pe = np.exp(exact)
+    pe /= pe.sum(-1, keepdims=True)
+    assert size == len(W)
+    assert np.abs(pe - ref).max() < 1e-12
+
+
 @pytest.mark.parametrize("q,n,shift", [(2, 8, 4), (4, 7, 4)])
 def test_bp_is_exact_on_cycle_free_joint_graph(oracle, q, n, shift):
     """Two users, one dc = 4 check each on positions 0..3; user 1's interleaver
