@@ -136,6 +136,25 @@ def test_amp_slot_is_amp_on_the_partial_dft():
     assert np.abs(a[1] - b[1]).max() < 1e-9
 
 
+def test_evidence_is_the_activity_log_of_the_final_pseudo_observation():
+    """Evidence interface: S_a = log p^(|R_a|^2; nu) of the last AMP iterate (eq.
+    bg_activity_prob at the detector's output), and the batched evidence
+    [F, L, Q] is the per-slot detector run on each frame's slot with that slot's
+    rows (layout of y: [F, L, ns, 2])."""
+    rng = np.random.default_rng(21)
+    Q, ns, L, F = 64, 24, 3, 2
+    rho, su2 = 2 / 64, 30.0
+    rows = np.stack([rng.choice(Q, ns, replace=False) for _ in range(L)]).astype(np.int32)
+    y = (rng.standard_normal((F, L, ns, 2)) * 3).astype(np.float32)
+    S_all = O.amp_evidence(Q, rows, y, 20, rho, su2, threads=2)
+    for f in range(F):
+        for l in range(L):
+            S, R, nu = O.amp_slot(Q, rows[l], y[f, l], 20, rho, su2)
+            ref = np.array([O.bg_log_activity(abs(R[a]) ** 2, nu, rho, su2) for a in range(Q)])
+            assert np.abs(S - ref).max() < 1e-12
+            assert np.array_equal(S_all[f, l], S)
+
+
 def _gf4_code_tree():
     # two checks of degree 3 sharing variable 2: a tree (no cycle)
     chk_var = np.array([0, 1, 2, 2, 3, 4], dtype=np.int32)
