@@ -426,3 +426,30 @@ def test_generated_codewords_satisfy_parity(oracle):
         bad = fr["c"].copy()
         bad[:, 0, 0] ^= 1
         assert not oracle.syndrome_ok(code, 2, bad)[:, 0].any()
+
+
+def test_single_steps_compose_to_the_decoder(oracle):
+    """The oracle's single-step functions (the references of the GPU step tests)
+    run in the flooding schedule (reading R2: channel from c2v^{t-1}, checks from
+    v2c = ch2v^t x c2v^{t-1} of the other edge, posterior from ch2v^t and c2v^t,
+    c2v^0 uniform) reproduce the whole decoder's messages, posterior, decisions and
+    syndrome flags; and v2c then the check update equals the fused check step."""
+    K, q, n, T = 3, 8, 24, 4
+    code = I.make_code(n, q)
+    fr = I.make_frames(code, K, 12.0, 3, seed=29)
+    E = code["P"] * code["dc"]
+    c2v = np.zeros((3, K, E, q))
+    for _ in range(T):
+        ch2v = oracle.step_channel(code, K, fr["sigma2"], fr["perm"], fr["y"], c2v)
+        v2c = oracle.step_v2c(code, K, ch2v, c2v)
+        new = oracle.step_check(code, K, ch2v, c2v)
+        assert np.abs(oracle.step_check_v2c(code, K, v2c) - new).max() < 1e-12
+        c2v = new
+    post, hat = oracle.step_var(code, K, ch2v, c2v)
+    full = oracle.decode(code, K, fr["sigma2"], fr["perm"], fr["y"], T, early_stop=False, want_post=True,
+                         want_msgs=True)
+    assert np.abs(full["ch2v"] - ch2v).max() < 1e-12
+    assert np.abs(full["c2v"] - c2v).max() < 1e-12
+    assert np.abs(full["post"] - post).max() < 1e-12
+    assert np.array_equal(full["hat"], hat)
+    assert np.array_equal(full["ok"], oracle.syndrome_ok(code, K, hat))
