@@ -19,11 +19,15 @@ q up to 64) uses the full prefix/suffix chain instead; its formulation is pinned
 the same way in FP64, for K up to 16.
 """
 import math
+import os
+import sys
 
 import numpy as np
 import pytest
 
 from paper_2605_26580_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def gauss(K, q, sigma2, y, dt):
@@ -154,3 +158,36 @@ def test_prefix_suffix_chain_equals_the_trellis(oracle, K, q, snr):
         ref = np.exp(oracle.channel_node(K, m, sigma2, y, logmu))
         got = chain_node(K, q, sigma2, y, np.exp(logmu))
         assert np.abs(np.log(got) - np.log(ref)).max() <= 1e-9
+
+
+def test_roofline_mac_count_matches_the_formulations(monkeypatch):
+    """The benchmark's channel-node work per channel use (its roofline FLOP count)
+    equals the multiply-adds the formulations above perform, counted as they run
+    (products with the unit prefix F_0 = delta_0 are free and not counted)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    count = [0]
+    mod = sys.modules[__name__]
+    real_corr, real_conv = mod.corr, mod.conv
+
+    def corr_n(P, X, nh, dt):
+        if P.shape[0] > 1:
+            count[0] += P.shape[0] * nh
+        return real_corr(P, X, nh, dt)
+
+    def conv_n(A, B, dt):
+        if A.shape[0] > 1:
+            count[0] += A.shape[0] * B.shape[0]
+        return real_conv(A, B, dt)
+
+    monkeypatch.setattr(mod, "corr", corr_n)
+    monkeypatch.setattr(mod, "conv", conv_n)
+    rng = np.random.default_rng(1)
+    for K, q in [(2, 4), (2, 16), (3, 8), (3, 16), (4, 4), (4, 16), (5, 16), (4, 32), (8, 64), (6, 8)]:
+        mu = np.exp(I.random_log_messages(rng, (K,), q, spread=1.0))
+        count[0] = 0
+        if K <= 4 and q <= 16:
+            split_node(K, q, 10.0, 0.5, mu, np.float64)
+        else:
+            chain_node(K, q, 10.0, 0.5, mu)
+        assert count[0] == bench.channel_macs_per_use(K, q), (K, q, count[0])
