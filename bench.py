@@ -227,7 +227,7 @@ def cpu_baseline_leg() -> dict:
 
 # --------------------------------------------------------------------------- our arm
 
-def main() -> None:
+def make_parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=6)
@@ -252,7 +252,11 @@ def main() -> None:
                          "applies; auto: except where the register-resident trellis applies)")
     ap.add_argument("--channel-frames", type=int, default=4096, help="precision workload: frames of that leg")
     ap.add_argument("--oracle-sample", type=int, default=16, help="precision workload: oracle frames")
-    args = ap.parse_args()
+    return ap
+
+
+def main() -> None:
+    args = make_parser().parse_args()
     if args.impl == "reference":
         run_reference(args)
         return

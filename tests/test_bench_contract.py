@@ -73,3 +73,23 @@ def test_uneven_classes_cover_every_frame():
     for (n, q, K) in classes:
         assert n in (128, 256, 512, 1024, 2048) and q in (16, 64) and 2 <= K <= 8
     assert ((8.0 <= snr) & (snr <= 16.0)).all()
+
+
+def test_profile_commands_run_committed_files_with_valid_flags():
+    """Every command a profile summary quotes runs a committed file (bench.py)
+    with flags the benchmark still accepts."""
+    import re
+    import shlex
+    sys.path.insert(0, ROOT)
+    import bench
+    parser = bench.make_parser()
+    prof = os.path.join(ROOT, "profiles")
+    seen = 0
+    for name in sorted(os.listdir(prof)):
+        text = open(os.path.join(prof, name)).read().replace("\\\n", " ")
+        for m in re.finditer(r"python (\S+)((?: --?[\w-]+(?: [^\s-][^\s]*)?)*)", text):
+            assert m.group(1) == "bench.py", (name, m.group(0))
+            parser.parse_args(shlex.split(m.group(2)))
+            seen += 1
+        assert "_work" not in text, name
+    assert seen >= 5
