@@ -107,3 +107,40 @@ def test_every_entry_point_refuses_null_pointers(jbp_lib):
         rc = fn(*_null_args(params))
         assert rc == jbp_lib.EINVAL, (name, rc)
         assert lib.jbp_last_error(), name
+
+
+def test_plain_c_program_links_and_calls_the_library(jbp_lib, tmp_path):
+    """The boundary is usable from C99 as declared: a C program includes jbp.h,
+    links libjbp.so and calls two host-only entry points and an argument check."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_jbp.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include "jbp.h"
+int main(void) {
+    uint8_t mul[16 * 16], div[16 * 16];
+    int32_t shape[5];
+    int64_t bytes = 0;
+    if (jbp_gf_tables(16, mul, div) != JBP_OK) return 1;
+    if (jbp_dft_tables(4, 64, shape, NULL, &bytes) != JBP_OK) return 2;
+    if (jbp_decode(NULL, NULL) != JBP_EINVAL) return 3;
+    printf("%d %d %d %lld %s\n", mul[2 * 16 + 8], div[3 * 16 + 3], shape[0], (long long)bytes,
+           jbp_last_error()[0] ? "msg" : "nomsg");
+    return 0;
+}
+""")
+    lib_dir = os.path.dirname(jbp_lib.LIB_PATH)
+    exe = tmp_path / "use_jbp"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                    "-L", lib_dir, "-ljbp", "-Wl,-rpath," + lib_dir], check=True, capture_output=True, timeout=120)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    a, b, L, nbytes, msg = out.stdout.split()
+    assert int(a) == 3          # x * x^3 = x^4 = x + 1 in GF(16) with x^4 + x + 1
+    assert int(b) == 1          # 3 / 3
+    assert int(L) == 256        # first multiple of 16 >= 4 * 63 + 1
+    assert int(nbytes) > 0 and msg == "msg"
