@@ -80,6 +80,31 @@ def test_channel_trellis_equals_enumeration(oracle, K, m):
         assert np.abs(a - b).max() < 1e-11
 
 
+@pytest.mark.parametrize("K,m,y,s2", [(3, 2, 0.7, 2.0), (3, 2, 40.0, 0.05), (2, 3, -60.0, 0.1), (4, 1, 9.5, 0.01)])
+def test_channel_node_equals_python_enumeration_in_log_space(oracle, K, m, y, s2):
+    """The channel factor written out in plain Python, in log space so that far
+    observations (beyond the largest symbol sum, tiny noise) do not underflow:
+    msg_k(a) = log sum over the other users' symbols of prod_j mu_j(x_j) times
+    N(y; level(a) + sum_j level(x_j), s2), max-normalised and floored."""
+    q = 1 << m
+    rng = np.random.default_rng(K * 13 + m)
+    lm = I.random_log_messages(rng, (K,), q, spread=3.0)
+    lev = 2.0 * np.arange(q) - (q - 1)
+    ref = np.full((K, q), -np.inf)
+    for k in range(K):
+        others = [j for j in range(K) if j != k]
+        for a in range(q):
+            terms = []
+            for xs in itertools.product(range(q), repeat=K - 1):
+                mean = lev[a] + sum(lev[x] for x in xs)
+                terms.append(sum(lm[j, x] for j, x in zip(others, xs)) - (y - mean) ** 2 / (2 * s2))
+            t = np.array(terms)
+            ref[k, a] = t.max() + math.log(np.exp(t - t.max()).sum())
+    ref = np.maximum(ref - ref.max(axis=1, keepdims=True), LOG_FLOOR)
+    got = oracle.channel_node(K, m, s2, y, lm)
+    assert np.abs(got - ref).max() < 1e-9
+
+
 @pytest.mark.parametrize("m", [1, 2, 4, 6])
 def test_channel_single_user_is_gaussian_likelihood(oracle, m):
     """K = 1: the channel message is log N(y; 2a - (q-1), sigma2), max-normalised."""
