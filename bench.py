@@ -139,6 +139,19 @@ def fp32_peak_tflops(sm_count: int, clock_mhz: float) -> float:
     return sm_count * 128 * 2 * clock_mhz * 1e6 / 1e12
 
 
+def measured_fp32_peak(jbp, device: int, seconds: float = 1.5) -> dict:
+    """The device's FP32 multiply-add rate, measured now (jbp_fp32_peak) with
+    scalar FFMA and with two-lane FFMA2 instructions, clocks sampled meanwhile;
+    the peak is the larger rate."""
+    clocks = ClockSampler(device)
+    clocks.start()
+    time.sleep(0.2)
+    ffma = jbp.fp32_peak(device, seconds, packed=False)
+    ffma2 = jbp.fp32_peak(device, seconds, packed=True)
+    clk = clocks.stop()
+    return {"tflops": max(ffma, ffma2), "ffma": ffma, "ffma2": ffma2, "seconds": seconds, "clocks": clk}
+
+
 def hbm_peak_gbs() -> float:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -298,9 +311,11 @@ def main() -> None:
 
     launch = {"mode": args.launch}
     if args.launch == "auto":
-        for i, d in enumerate(decs):
-            th, fc = d.tune(y_d[i], hat_d[i], it_d[i], ok_d[i], stream=stream)
-        launch.update(threads=th, frames_per_cta=fc)
+        # one autotune (on the first SNR point's batch); every decoder uses that shape
+        th, fc = decs[0].tune(y_d[0], hat_d[0], it_d[0], ok_d[0], stream=stream)
+        for d in decs[1:]:
+            d.set_launch(th, fc)
+        launch.update(threads=th, frames_per_cta=fc, applies_to="all %d decoders" % len(decs))
     elif args.launch != "default":
         th, fc = (int(v) for v in args.launch.split(","))
         for d in decs:
@@ -347,7 +362,8 @@ def main() -> None:
                    for s in range(args.warmup, args.warmup + args.steps))
     flops = flops_per_frame_iter(K_USERS, Q, N_SYM) * it_total
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = fp32_peak_tflops(sm_count, 2070.0)
+    peak_meas = measured_fp32_peak(jbp, local)
+    peak = peak_meas["tflops"]
     achieved = flops / (total_ms / 1e3) / 1e12 / world
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 # DRAM bytes per 65,536-frame launch: ncu capture of k_fused_pos<16,4> on 1,216 frames
@@ -357,7 +373,14 @@ def main() -> None:
                 "traffic": (1.409e6 * 65536 / 1216) if args.frames == FRAMES else None,
                 "traffic_note": "per launch, from profiles/k_fused_pos_q16_k4_n256_small_full.md scaled by frames",
                 "kernel": "k_fused_pos<16,4>",
-                "peak_note": "FP32 FMA peak derived: %d SMs x 128 lanes x 2 flops x 2070 MHz" % sm_count,
+                "peak_note": ("of measured: FP32 multiply-add peak measured in this run by jbp_fp32_peak "
+                              "(independent FMA chains on all %d SMs, median of 3 launches, %.1f s; "
+                              "FFMA %.2f, two-lane FFMA2 %.2f TFLOP/s; the larger is the peak) at a median "
+                              "SM clock of %s MHz; derived nominal at that clock: %.2f TFLOP/s"
+                              % (sm_count, peak_meas["seconds"], peak_meas["ffma"], peak_meas["ffma2"],
+                                 peak_meas["clocks"].get("sm_mhz"),
+                                 fp32_peak_tflops(sm_count, peak_meas["clocks"].get("sm_mhz") or 2070.0))),
+                "peak_clocks": peak_meas["clocks"],
                 "flops_per_frame_iter": flops_per_frame_iter(K_USERS, Q, N_SYM)}
 
     line = {

@@ -196,9 +196,12 @@ int jbp_decode(jbp_h *h, jbp_batch *batch);
 int jbp_decode_many(jbp_ctx *ctx, int32_t nparts, jbp_h *const *handles, const jbp_batch *batches, void *stream);
 
 /* Autotune the fused-form launch shape of a handle on a device batch (runs a
- * few short timed launches that write the first frames' outputs) and keep the
- * fastest; *threads and *frames_per_cta receive the choice (0 = default).
- * Synchronous.  With batch == NULL the shape is set from *threads and
+ * few short timed launches that write the first frames' outputs: each distinct
+ * shape the planner resolves is timed 5 times and scored by the median; a shape
+ * whose launch fails is skipped) and keep the fastest; *threads and
+ * *frames_per_cta receive the resolved shape (both >= 1 for a handle with a
+ * fused form; 0 when the handle has none).  Returns JBP_ECUDA if no candidate
+ * ran.  Synchronous.  With batch == NULL the shape is set from *threads and
  * *frames_per_cta instead (0 = default; threads > 256 selects, for K = 4, the
  * variant that splits each channel use over two lanes).  The per-frame
  * arithmetic does not depend on the shape. */
@@ -322,6 +325,18 @@ int jbp_gf_tables(int32_t q, uint8_t *mul, uint8_t *div);
  * 2..8) or bytes is NULL.  No paper counterpart: the paper prints no
  * channel-node kernel; the node computed is kernel (a) above. */
 int jbp_dft_tables(int32_t K, int32_t q, int32_t *shape, void *out, int64_t *bytes);
+
+/* Measured FP32 multiply-add throughput of `device` (TFLOP/s, 2 flops per
+ * multiply-add), the denominator of the ALU roofline the channel-node and
+ * fused kernels are reported against.  Runs independent FMA chains on every
+ * SM for about `seconds` (0 < seconds <= 60) as three back-to-back launches and
+ * returns the median rate in *tflops.  packed = 0: one multiply-add per lane
+ * and instruction (FFMA); packed = 1: two-lane FP32 instructions (two
+ * multiply-adds per lane and instruction).  Synchronous; allocates a small
+ * device buffer; changes no device setting.  Errors: JBP_EINVAL (NULL tflops,
+ * seconds out of range), JBP_ECUDA.  No paper counterpart: a measurement
+ * utility. */
+int jbp_fp32_peak(int32_t device, double seconds, int32_t packed, double *tflops);
 
 /* ---- the paper's own classical path on the evidence interface S ----
  *

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libjbp.so")
 SOURCES = ["jbp_capi.cu", "jbp_step.cu", "jbp_fused.cu", "jbp_noalloc.cu", "jbp_check_tc.cu", "jbp_ura.cu",
-           "jbp_channel_dft.cu"]
+           "jbp_channel_dft.cu", "jbp_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

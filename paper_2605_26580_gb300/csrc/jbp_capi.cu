@@ -877,46 +877,72 @@ extern "C" int jbp_decode(jbp_h* h, jbp_batch* b)
 // Time candidate fused launch shapes (threads per CTA x frames per CTA) on the
 // first min(F, 4 * SMs) frames of a batch, a few iterations each, and keep the
 // fastest for this handle.  Every candidate runs the same per-frame arithmetic,
-// so the choice changes speed only.
+// so the choice changes speed only.  Candidates are the distinct shapes the
+// planner resolves (a hint it clamps to an already-seen shape is not re-timed);
+// each is scored by the median of kTuneReps timed launches; a candidate whose
+// launch or timing fails is skipped.  The handle keeps the resolved shape (never
+// a 0 "default" hint), so jbp_tune reports what later fused launches use.
 static int autotune(jbp_h* h, int F, const float* y, uint8_t* hat, int32_t* iters, uint8_t* ok,
                     const float* sigma2_f, cudaStream_t s)
 {
+    constexpr int kTuneReps = 5;
     jbp_ctx* ctx = h->ctx;
     if (!h->fused_ok || F <= 0) return JBP_OK;
     Graph g = h->graph();
     g.sigma2_f = sigma2_f;
     const int Fs = std::min(F, 4 * ctx->di.sm_count);
     const int T = std::min(ctx->opt.iters, 4);
-    cudaEvent_t a, b;
-    JBP_CU(cudaEventCreate(&a), "tune event");
-    JBP_CU(cudaEventCreate(&b), "tune event");
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        cudaGetLastError();
+        return fail(JBP_ECUDA, "autotune: cudaEventCreate failed");
+    }
     float best = 1e30f;
     int bt = 0, bf = 0;
+    cudaError_t last = cudaSuccess;
+    std::vector<std::pair<int, int>> seen;   // (threads, frames per CTA) of resolved plans
     const int threads_c[] = {128, 192, 256, 384, 512};
-    const int fpc_c[] = {1, 2, 4, 8, 16, 0};
+    const int fpc_c[] = {1, 2, 4, 8, 16};
     for (int th : threads_c)
         for (int fc : fpc_c) {
             FusedPlan plan;
             if (!fused_plan(g, ctx->di, Fs, th, fc, &plan)) continue;
-            if (fc > 0 && plan.frames_per_cta != fc) continue;   // duplicate of a smaller hint
-            float ms = 0;
-            for (int rep = 0; rep < 2; ++rep) {
-                cudaEventRecord(a, s);
-                if (launch_fused(g, plan, Fs, y, T, 0, hat, iters, ok, nullptr, s) != cudaSuccess) break;
-                cudaEventRecord(b, s);
-                cudaEventSynchronize(b);
-                cudaEventElapsedTime(&ms, a, b);
+            const std::pair<int, int> key(plan.threads, plan.frames_per_cta);
+            if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
+            seen.push_back(key);
+            float ms[kTuneReps];
+            bool good = true;
+            for (int rep = 0; rep < kTuneReps && good; ++rep) {
+                cudaError_t e = cudaEventRecord(a, s);
+                if (e == cudaSuccess) e = launch_fused(g, plan, Fs, y, T, 0, hat, iters, ok, nullptr, s);
+                if (e == cudaSuccess) e = cudaEventRecord(b, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(b);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[rep], a, b);
+                if (e != cudaSuccess) {
+                    last = e;
+                    good = false;
+                }
             }
-            const float per_frame = ms / Fs;
+            if (!good) {
+                cudaGetLastError();   // a rejected launch shape leaves a non-sticky error
+                continue;
+            }
+            std::sort(ms, ms + kTuneReps);
+            const float per_frame = ms[kTuneReps / 2] / Fs;
             if (per_frame < best) {
                 best = per_frame;
-                bt = th;
-                bf = fc;
+                bt = plan.threads;
+                bf = plan.frames_per_cta;
             }
         }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    cudaGetLastError();
+    if (bt == 0) {
+        const cudaError_t sticky = cudaDeviceSynchronize();
+        return fail(JBP_ECUDA, "autotune: no candidate launch shape ran: %s",
+                    cudaGetErrorString(sticky != cudaSuccess ? sticky : last));
+    }
     h->tune_threads = bt;
     h->tune_fpc = bf;
     h->tuned = true;

@@ -27,6 +27,7 @@ EXPORTS = [
     "jbp_submit", "jbp_poll", "jbp_serving_stats", "jbp_last_error", "jbp_step_channel",
     "jbp_step_check", "jbp_step_var", "jbp_step_syndrome", "jbp_query", "jbp_query_channel", "jbp_dft_tables", "jbp_gf_tables", "jbp_decode_noalloc", "jbp_stats", "jbp_decode_many", "jbp_tune",
     "jbp_ura_create", "jbp_ura_destroy", "jbp_amp_evidence", "jbp_sic_decode", "jbp_ura_decode", "jbp_match_rows",
+    "jbp_fp32_peak",
 ]
 
 
@@ -94,6 +95,7 @@ def lib():
             L.jbp_query_channel.argtypes = [vp, C.POINTER(i32)]
             L.jbp_dft_tables.argtypes = [i32, i32, C.POINTER(i32), vp, C.POINTER(i64)]
             L.jbp_gf_tables.argtypes = [i32, vp, vp]
+            L.jbp_fp32_peak.argtypes = [i32, C.c_double, i32, C.POINTER(C.c_double)]
             L.jbp_decode_many.argtypes = [vp, i32, C.POINTER(vp), C.POINTER(Batch), vp]
             L.jbp_tune.argtypes = [vp, C.POINTER(Batch), C.POINTER(i32), C.POINTER(i32)]
             L.jbp_stats.argtypes = [vp, C.POINTER(u64), C.POINTER(i32)]
@@ -152,6 +154,13 @@ def gf_tables(q: int):
     div = np.zeros((q, q), dtype=np.uint8)
     check(lib().jbp_gf_tables(q, mul.ctypes.data, div.ctypes.data))
     return mul, div
+
+
+def fp32_peak(device: int = 0, seconds: float = 1.5, packed: bool = False) -> float:
+    """Measured FP32 multiply-add rate of the device in TFLOP/s (jbp_fp32_peak)."""
+    out = C.c_double()
+    check(lib().jbp_fp32_peak(int(device), float(seconds), 1 if packed else 0, C.byref(out)))
+    return out.value
 
 
 def dft_tables(K: int, q: int):
