@@ -168,9 +168,21 @@ int jbp_context_create(const jbp_options *opt, jbp_ctx **out);
 int jbp_context_destroy(jbp_ctx *ctx);
 
 /* Bind a decoder for `code`, K >= 1 users (K <= 16) and GF(q) (q = code->q)
- * to the context; copies the code and interleavers to the device and builds
- * the GF tables.  Supported shapes: q in {2,4,8,16,32,64}, dc = 4, dv >= 1
- * regular, n >= 1.  Others give JBP_EINVAL. */
+ * to the context: step a0 of the decoder, its one-time setup.  Defined by the
+ * paper's appendix "Q-ary LDPC code": the code is the null space over GF(Q) of
+ * a sparse parity-check matrix H (eq. app_ldpc_check_eq; every row a check
+ * sum_l H_{j,l} c_l = 0 over GF(Q)), H built as in its paragraph "Construction
+ * of H" (a sparse support with nonzero coefficients on GF(Q)*), and symbols
+ * map to field elements by a fixed bijection (the index bits are the
+ * polynomial coefficients of the field listed at the top of this file).  The
+ * call deep-copies chk_var, chk_coef and the interleavers pi_k to the device;
+ * builds the GF(q) multiply and divide tables (jbp_gf_tables), the per-user
+ * slot tables of the fused form and the check order of its shared-memory
+ * layout; the caller keeps ownership of every host array.  Supported shapes:
+ * q in {2,4,8,16,32,64}, dc = 4, dv >= 1 regular, n >= 1.  Errors: JBP_EINVAL
+ * (NULL pointers, unsupported shape, an edge list that is not regular or a
+ * coefficient outside 1..q-1), JBP_ENOMEM (over the context's budget),
+ * JBP_ECUDA. */
 int jbp_create(jbp_ctx *ctx, const jbp_code *code, int32_t K, int32_t q,
                const jbp_channel *chan, jbp_h **out);
 
@@ -178,7 +190,20 @@ int jbp_create(jbp_ctx *ctx, const jbp_code *code, int32_t K, int32_t q,
  * cancelled (their tickets poll JBP_ECLOSED). */
 int jbp_destroy(jbp_h *h);
 
-/* Decode one batch (see jbp_batch). */
+/* Decode one batch (see jbp_batch): up to T iterations of joint
+ * sum-product BP per frame, flooding schedule.  Each iteration is the
+ * channel-node update (kernel (a) above: the K-user PAM-sum factor), the
+ * variable-to-check rule eq. (app_ldpc_v2c), the check-to-variable rule
+ * eq. (app_ldpc_c2v) in the Walsh-Hadamard domain (appendix "Complexity
+ * derivation", paragraph FFT-BP), the marginal eq. (app_ldpc_marginal) and
+ * its hard decision (ties -> lowest symbol), then the parity checks
+ * eq. (app_ldpc_check_eq): with early_stop a frame ends at the first iteration
+ * after which all K users' syndromes are zero (Table 1 caption: at most 50
+ * iterations with early exit on convergence), and its outputs are those of that
+ * iteration.  Frames are independent; the result of a frame does not depend on
+ * the batch it is in.  Errors: JBP_EINVAL (NULL buffers, F < 0, a form the
+ * handle cannot run), JBP_ENOMEM, JBP_ECUDA, JBP_ETIMEOUT (a bounded device wait
+ * of a tensor-core or staged kernel expired; outputs are then not valid). */
 int jbp_decode(jbp_h *h, jbp_batch *batch);
 
 /* Decode several device batches of possibly different decoders (codes, K, q)
@@ -209,13 +234,23 @@ int jbp_tune(jbp_h *h, const jbp_batch *batch, int32_t *threads, int32_t *frames
 
 /* Serving: queue one frame (y_frame [n] host pointer, copied before return)
  * for continuous batching on the context's device; sigma2 > 0 is this
- * frame's noise variance (<= 0: the handle's channel).  *ticket identifies it. */
+ * frame's noise variance (<= 0: the handle's channel).  *ticket identifies it.
+ * The frame is decoded by the same iteration as jbp_decode (eqs.
+ * app_ldpc_v2c, app_ldpc_c2v, app_ldpc_marginal, app_ldpc_check_eq with early
+ * exit); the paper has no serving counterpart: requests of any decoder of the
+ * context are admitted into resident device pools as slots and memory free
+ * up and re-batched every block of iterations.  Thread-safe.  Errors:
+ * JBP_EINVAL (NULL pointer, sigma2 not finite), JBP_ECLOSED (the context is
+ * shutting down).  The queue is unbounded: a request waits on the host until a
+ * pool slot frees up. */
 int jbp_submit(jbp_h *h, const float *y_frame, double sigma2, uint64_t *ticket);
 
 /* Serving: JBP_EAGAIN while the request runs; JBP_OK once finished, with
- * hat [K*n], iters [1] and ok [K] written (host pointers; any may be NULL).
- * A finished ticket is consumed by the successful poll; polling it again
- * gives JBP_ECLOSED. */
+ * hat [K*n], iters [1] and ok [K] written (host pointers; any may be NULL):
+ * the decisions of eq. (app_ldpc_marginal), the iterations run and the
+ * syndrome flags of eq. (app_ldpc_check_eq), as jbp_decode gives them for the
+ * same frame.  A finished ticket is consumed by the successful poll; polling it
+ * again gives JBP_ECLOSED.  Thread-safe; no paper counterpart (serving). */
 int jbp_poll(jbp_ctx *ctx, uint64_t ticket, uint8_t *hat, int32_t *iters, uint8_t *ok);
 
 /* Serving statistics since context creation: completed requests, and the
@@ -271,7 +306,10 @@ int jbp_step_syndrome(jbp_h *h, int32_t F, const uint8_t *hat, uint8_t *ok, void
  * each device looks up the array's device address (set-up); make that first
  * call before any stream capture.  All calls share the array and it keeps the
  * previous call's contents (each call clears what must start at zero); calls
- * whose work overlaps on the GPU race on it, so serialise them. */
+ * whose work overlaps on the GPU race on it, so serialise them.  If a bounded
+ * device wait of the check kernel expires during a call (JBP_ETIMEOUT in
+ * jbp_decode), that call's outputs are marked instead, since it returns before
+ * the work runs: every frame gets iters = -1 and ok = 0. */
 int jbp_decode_noalloc(const jbp_code *code, int32_t K, const jbp_channel *chan, int32_t T,
                        int32_t early_stop, int32_t F, const float *y, uint8_t *hat, int32_t *iters,
                        uint8_t *ok, void *stream);

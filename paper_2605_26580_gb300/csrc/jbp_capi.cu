@@ -91,8 +91,10 @@ static int gf_mul_host(int a, int b, int m)
 }
 
 // q x q tables of GF(2^m): mul[h q + x] = h x and div[h q + x] = h^{-1} x
-// (row h = 0 of div is all zero)
-static void gf_tables(int m, uint8_t* mul, uint8_t* div)
+// (row h = 0 of div is all zero).  The one builder of these tables in the
+// library: jbp_create, the evidence decoder, jbp_gf_tables and
+// jbp_decode_noalloc all take them from here.
+void jbp::gf_build_tables(int m, uint8_t* mul, uint8_t* div)
 {
     const int q = 1 << m;
     std::vector<int> inv(q, 0);
@@ -647,7 +649,7 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
                           reinterpret_cast<int32_t*>(dft_tab.data() + dft_table_bytes(K, q)));
     }
     std::vector<uint8_t> gmul((size_t)q * q), gdiv((size_t)q * q);
-    gf_tables(m, gmul.data(), gdiv.data());
+    gf_build_tables(m, gmul.data(), gdiv.data());
     const int scf = blk_scratch_floats(K, q);
     const int team_lanes = q < 32 ? q : 32;
     if ((size_t)(32 / team_lanes) * scf * sizeof(float) > (size_t)ctx->di.smem_optin)
@@ -784,7 +786,7 @@ extern "C" int jbp_gf_tables(int32_t q, uint8_t* mul, uint8_t* div)
     while (m < 7 && (1 << m) < q) ++m;
     if (q < 2 || q > 64 || (1 << m) != q) return fail(JBP_EINVAL, "jbp_gf_tables: q = %d (2, 4, ..., 64)", q);
     if (!mul || !div) return fail(JBP_EINVAL, "jbp_gf_tables: NULL argument");
-    gf_tables(m, mul, div);
+    gf_build_tables(m, mul, div);
     return JBP_OK;
 }
 
@@ -1695,7 +1697,7 @@ extern "C" int jbp_ura_create(jbp_ctx* ctx, const jbp_code* code, const jbp_ura_
                 if (p->rows[(size_t)l * p->ns + i2] == r) return fail(JBP_EINVAL, "slot %d repeats row %d", l, r);
         }
     std::vector<uint8_t> gmul((size_t)q * q), gdiv((size_t)q * q);
-    gf_tables(m, gmul.data(), gdiv.data());
+    gf_build_tables(m, gmul.data(), gdiv.data());
     // twiddles exp(-2 pi i k / q) from the host's double-precision cos and sin
     std::vector<float> tw((size_t)2 * q);
     const double two_pi = 6.283185307179586476925286766559;

@@ -170,6 +170,10 @@ cudaError_t launch_sic(const UraDev& u, const DeviceInfo& di, int F, const float
 // Record the message returned by jbp_last_error() on this thread (jbp_capi.cu).
 void set_last_error(const char* msg);
 
+// GF(2^m) tables (jbp_capi.cu), q = 2^m, m = 1..6, field polynomials of jbp.h:
+// mul[h*q + x] = h x, div[h*q + x] = h^{-1} x (row 0 of div zero).
+void gf_build_tables(int m, uint8_t* mul, uint8_t* div);
+
 // Bytes of message state of one frame in either form: msg [K*E*Q] + ch2v [K*n*Q] floats.
 inline int64_t state_bytes(const Graph& g)
 {

@@ -16,6 +16,7 @@
 // zero.  Calls whose work overlaps on the GPU (different streams, or different
 // host threads on one device) race on the array and must be serialised by the
 // caller.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -51,20 +52,17 @@ int nfail(int code, const char* msg)
 
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
-int poly(int m)
+// After the last iteration: if a bounded device wait of the staged check
+// kernel expired during this call, no frame's outputs can be trusted, so every
+// frame gets ok = 0 and iters = -1 (the caller's only sign of it, since the
+// call returns before the work runs).
+__global__ void k_noalloc_status(const int* err, int F, int K, int32_t* iters, uint8_t* ok)
 {
-    static const int p[7] = {0, 0x3, 0x7, 0xB, 0x13, 0x25, 0x43};
-    return (m >= 1 && m <= 6) ? p[m] : 0;
-}
-
-int gfmul(int a, int b, int m)
-{
-    int r = 0;
-    for (int i = 0; i < m; ++i)
-        if ((b >> i) & 1) r ^= a << i;
-    for (int i = 2 * m - 2; i >= m; --i)
-        if ((r >> i) & 1) r ^= poly(m) << (i - m);
-    return r;
+    if (*err == 0) return;
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < F; f += gridDim.x * blockDim.x) {
+        iters[f] = -1;
+        for (int k = 0; k < K; ++k) ok[(size_t)f * K + k] = 0;
+    }
 }
 
 }  // namespace
@@ -91,7 +89,8 @@ extern "C" int jbp_decode_noalloc(const jbp_code* code, int32_t K, const jbp_cha
     // table area (first kTableBytes) and per-frame state after it
     const size_t o_var = 0, o_coef = up256(o_var + 4ull * E), o_vedge = up256(o_coef + E),
                  o_use = up256(o_vedge + 4ull * n * dv), o_mul = up256(o_use + 4ull * K * n),
-                 o_div = up256(o_mul + (size_t)q * q), tables_end = up256(o_div + (size_t)q * q);
+                 o_div = up256(o_mul + (size_t)q * q), o_err = up256(o_div + (size_t)q * q),
+                 tables_end = up256(o_err + sizeof(int));
     if (tables_end > kTableBytes) return nfail(JBP_EINVAL, "code too large for the fixed table area (1 MiB)");
     const size_t fs = (size_t)K * E * q * 4, vs = (size_t)K * n * q * 4;
     const size_t o_msg = kTableBytes, o_ch2v = up256(o_msg + fs * F), o_act = up256(o_ch2v + vs * F),
@@ -153,15 +152,8 @@ extern "C" int jbp_decode_noalloc(const jbp_code* code, int32_t K, const jbp_cha
             if (t < 0 || t >= n || huse[(size_t)k * n + t] != -1) return nfail(JBP_EINVAL, "perm row is not a permutation");
             huse[(size_t)k * n + t] = i;
         }
-    for (int h = 0; h < q; ++h) {
-        int inv = 0;
-        for (int b = 1; b < q; ++b)
-            if (gfmul(h, b, m) == 1) inv = b;
-        for (int x = 0; x < q; ++x) {
-            hmul[(size_t)h * q + x] = (uint8_t)gfmul(h, x, m);
-            hdiv[(size_t)h * q + x] = (uint8_t)gfmul(inv, x, m);
-        }
-    }
+    jbp::gf_build_tables(m, hmul, hdiv);
+    // the wait-expiry flag at o_err is zero in H (cleared with the tables each call)
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char* D = ds.base;
@@ -183,7 +175,7 @@ extern "C" int jbp_decode_noalloc(const jbp_code* code, int32_t K, const jbp_cha
     g.log_fallbacks = nullptr;
     g.pos_of = nullptr;
     g.slot = nullptr;
-    g.tc_error = nullptr;
+    g.tc_error = reinterpret_cast<int*>(D + o_err);
     g.sigma2_f = nullptr;
     g.chk_order = nullptr;
     float* msg = reinterpret_cast<float*>(D + o_msg);
@@ -199,5 +191,7 @@ extern "C" int jbp_decode_noalloc(const jbp_code* code, int32_t K, const jbp_cha
             (e = jbp::launch_finalize(F, K, t, early_stop, c, s)) != cudaSuccess)
             return nfail(JBP_ECUDA, cudaGetErrorString(e));
     }
+    k_noalloc_status<<<std::min((F + 255) / 256, 4 * ds.di.sm_count), 256, 0, s>>>(g.tc_error, F, K, iters, ok);
+    if ((e = cudaGetLastError()) != cudaSuccess) return nfail(JBP_ECUDA, cudaGetErrorString(e));
     return JBP_OK;
 }
