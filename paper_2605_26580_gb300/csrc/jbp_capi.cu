@@ -503,9 +503,8 @@ extern "C" int jbp_context_destroy(jbp_ctx* ctx)
 // in shared-memory bank (position mod 32) of that edge, so the d-th loads of a
 // warp cost as many wavefronts as the largest number of its units sharing that
 // bank.  Greedy fill of each run of 32 with units whose banks are still free,
-// then pairwise swaps between runs that do not raise the sum over runs and edge
-// ranks of the largest bank count.  Deterministic (fixed-seed xorshift); the
-// order does not change any result.
+// then annealed pairwise swaps between runs.  Deterministic (fixed-seed
+// xorshift); the order does not change any result.
 static std::vector<uint16_t> check_order(int K, int P, int E, const std::vector<uint16_t>& slot)
 {
     const int N = K * P, R = (N + 31) / 32;
@@ -546,29 +545,31 @@ static std::vector<uint16_t> check_order(int K, int P, int E, const std::vector<
                 }
             }
     }
-    auto run_cost = [&](int r) {
-        int c = 0;
-        for (int d = 0; d < kDC; ++d) c += *std::max_element(cnt[r][d].begin(), cnt[r][d].end());
-        return c;
-    };
+    // Annealed pairwise swaps between runs on the sum of squared bank counts
+    // (every collision costs, so the search has a gradient that the largest count
+    // alone lacks); the cost of a swap changes only in the two runs' counts.
     if (R > 1) {
-        const long iters = 400l * N;
+        const long iters = 800l * N;
         for (long it = 0; it < iters; ++it) {
             const int i1 = (int)(rnd() % (uint64_t)N), i2 = (int)(rnd() % (uint64_t)N);
             const int r1 = i1 / 32, r2 = i2 / 32;
             if (r1 == r2) continue;
             const int u1 = order[i1], u2 = order[i2];
-            const int before = run_cost(r1) + run_cost(r2);
+            int delta = 0;
             for (int d = 0; d < kDC; ++d) {
-                cnt[r1][d][col[u1][d]]--; cnt[r1][d][col[u2][d]]++;
-                cnt[r2][d][col[u2][d]]--; cnt[r2][d][col[u1][d]]++;
+                const int a = col[u1][d], b = col[u2][d];
+                if (a == b) continue;
+                // u1 (bank a) leaves r1 for r2, u2 (bank b) leaves r2 for r1
+                delta += 2 * (cnt[r1][d][b] - cnt[r1][d][a] + 1) + 2 * (cnt[r2][d][a] - cnt[r2][d][b] + 1);
             }
-            if (run_cost(r1) + run_cost(r2) <= before) {
+            // temperature falls linearly from 2 to 0; uniform in [0, 1) from 53 random bits
+            const double temp = 2.0 * (1.0 - (double)it / (double)iters);
+            const double u01 = (double)(rnd() >> 11) * (1.0 / 9007199254740992.0);
+            if (delta <= 0 || (temp > 0.0 && u01 < std::exp(-delta / temp))) {
                 std::swap(order[i1], order[i2]);
-            } else {
                 for (int d = 0; d < kDC; ++d) {
-                    cnt[r1][d][col[u1][d]]++; cnt[r1][d][col[u2][d]]--;
-                    cnt[r2][d][col[u2][d]]++; cnt[r2][d][col[u1][d]]--;
+                    cnt[r1][d][col[u1][d]]--; cnt[r1][d][col[u2][d]]++;
+                    cnt[r2][d][col[u2][d]]--; cnt[r2][d][col[u1][d]]++;
                 }
             }
         }

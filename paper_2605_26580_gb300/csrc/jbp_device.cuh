@@ -56,7 +56,7 @@ struct Graph {
 // 1 / sigma2 of frame f
 __device__ __forceinline__ float frame_inv_s2(const Graph& g, long f)
 {
-    return g.sigma2_f ? 1.0f / g.sigma2_f[f] : g.inv_sigma2;
+    return g.sigma2_f ? __frcp_rn(g.sigma2_f[f]) : g.inv_sigma2;
 }
 
 __device__ __forceinline__ float* edge_ptr(float* blk, int e, int cbs, int Q)
@@ -134,13 +134,65 @@ __device__ __forceinline__ void vstore(float* p, const float (&v)[Q])
     }
 }
 
+// max of three floats in one instruction (the maximum is one of the inputs, so
+// the result equals fmaxf(fmaxf(a, b), c) bit for bit on non-NaN inputs)
+__device__ __forceinline__ float fmax3f(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// Largest entry, as a tree of three-input maxima (depth log3 N, not N - 1).
 template <int N>
 __device__ __forceinline__ float vmax(const float (&v)[N])
 {
-    float m = v[0];
+    if constexpr (N == 1) {
+        return v[0];
+    } else if constexpr (N == 2) {
+        return fmaxf(v[0], v[1]);
+    } else {
+        constexpr int M = (N + 2) / 3;
+        float t[M];
 #pragma unroll
-    for (int i = 1; i < N; ++i) m = fmaxf(m, v[i]);
-    return m;
+        for (int i = 0; i < M; ++i) {
+            const int a = 3 * i;
+            if (a + 2 < N) t[i] = fmax3f(v[a], v[a + 1], v[a + 2]);
+            else if (a + 1 < N) t[i] = fmaxf(v[a], v[a + 1]);
+            else t[i] = v[a];
+        }
+        return vmax<M>(t);
+    }
+}
+
+// Index of the largest entry, the lowest index among equal maxima (the rule of a
+// scan that replaces its best only on a strictly larger value), as a tree: a
+// node keeps its left (lower-index) child unless the right one is larger.
+template <int LO, int HI, int N>
+__device__ __forceinline__ void vargmax_rng(const float (&v)[N], float& bv, int& bi)
+{
+    if constexpr (HI - LO == 1) {
+        bv = v[LO];
+        bi = LO;
+    } else {
+        constexpr int MID = LO + (HI - LO + 1) / 2;
+        float lv, rv;
+        int li, ri;
+        vargmax_rng<LO, MID, N>(v, lv, li);
+        vargmax_rng<MID, HI, N>(v, rv, ri);
+        const bool r = rv > lv;
+        bv = r ? rv : lv;
+        bi = r ? ri : li;
+    }
+}
+
+template <int N>
+__device__ __forceinline__ int vargmax(const float (&v)[N])
+{
+    float bv;
+    int bi;
+    vargmax_rng<0, N, N>(v, bv, bi);
+    return bi;
 }
 
 // ---------------------------------------------------------------------------
@@ -157,11 +209,14 @@ __device__ __forceinline__ float vmax(const float (&v)[N])
 
 struct GaussTerm {
     int ss;          // nearest symbol sum s*
+    float ssf;       // s* as a float (exact: a small integer)
     float r;         // y - (2 s* - K(q-1))
     float inv_s2;    // 1 / sigma2
     __device__ __forceinline__ float expo(int s) const
     {
-        const float d = (float)(ss - s);
+        // d = s* - s is exact in FP32 (small integers), so subtracting floats
+        // gives the value an integer subtraction and conversion would
+        const float d = ssf - (float)s;
         return -2.0f * d * (r + d) * inv_s2;
     }
 };
@@ -173,6 +228,7 @@ __device__ __forceinline__ GaussTerm gauss_term(float y, int K, int Q, float inv
     sf = fminf(fmaxf(sf, 0.0f), (float)KD);
     GaussTerm t;
     t.ss = (int)sf;
+    t.ssf = sf;
     t.r = y - (float)(2 * t.ss - KD);
     t.inv_s2 = inv_s2;
     return t;
@@ -306,7 +362,7 @@ __device__ __forceinline__ void chan_finish(const float (&mu)[K][Q], int k, cons
         chan_user_log<K, Q>(mu, k, gt, o);
         return;
     }
-    const float inv = 1.0f / mx;
+    const float inv = __frcp_rn(mx);
 #pragma unroll
     for (int a = 0; a < Q; ++a) o[a] = fmaxf(o[a] * inv, kRelFloor);
 }
@@ -394,7 +450,7 @@ __device__ __forceinline__ void chan_store_user(const Graph& g, float* blk, int 
         c0[a] = o[a] * c1[a];
         c1[a] = o[a] * t;
     }
-    const float i0 = 1.0f / vmax(c0), i1 = 1.0f / vmax(c1);
+    const float i0 = __frcp_rn(vmax(c0)), i1 = __frcp_rn(vmax(c1));
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         c0[a] *= i0;
@@ -424,7 +480,7 @@ __device__ __forceinline__ void chan_thread(const Graph& g, float* msg_f, size_t
         vload<Q>(edge_ptr(blk, g.var_edge[2 * var[k] + 1], cbs, Q), a1);
 #pragma unroll
         for (int a = 0; a < Q; ++a) a0[a] *= a1[a];
-        const float inv = 1.0f / vmax(a0);
+        const float inv = __frcp_rn(vmax(a0));
 #pragma unroll
         for (int a = 0; a < Q; ++a) mu[k][a] = a0[a] * inv;
     }
@@ -440,7 +496,7 @@ struct LinSR {
     static constexpr bool kLog = false;
     __device__ static __forceinline__ float zero() { return 0.0f; }
     __device__ static __forceinline__ float mac(float acc, float a, float b) { return fmaf(a, b, acc); }
-    __device__ static __forceinline__ float rescale(float x, float mx) { return mx > 0.0f ? x * (1.0f / mx) : x; }
+    __device__ static __forceinline__ float rescale(float x, float mx) { return mx > 0.0f ? x * (__frcp_rn(mx)) : x; }
 };
 
 struct LogSR {
@@ -550,7 +606,7 @@ __device__ bool chan_trellis(const Graph& g, const float* msg_f, size_t ustride,
         if (!SR::kLog && !(mx >= kFallbackMax)) bad = true;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            const float r = SR::kLog ? __expf(o[v] - mx) : o[v] * (1.0f / mx);
+            const float r = SR::kLog ? __expf(o[v] - mx) : o[v] * (__frcp_rn(mx));
             res[k * Q + v * T + L.tl] = fmaxf(r, kRelFloor);
         }
         if (k > 0) {
@@ -680,7 +736,7 @@ __device__ __forceinline__ float team_corr(float* Y, int L, const float* A, int 
     }
     const float mx = team_max<T>(mx_all, Lr.mask);
     __syncwarp(Lr.mask);
-    const float inv = mx > 0.0f ? 1.0f / mx : 0.0f;
+    const float inv = mx > 0.0f ? __frcp_rn(mx) : 0.0f;
     for (int o = Lr.tl; o < L; o += T) Y[o] = mode ? fmaxf(Y[o] * inv, kRelFloor) : Y[o] * inv;
     __syncwarp(Lr.mask);
     return mx;
@@ -742,7 +798,7 @@ __device__ bool chan_blocked(const Graph& g, const float* msg_f, size_t ustride,
 #pragma unroll
         for (int v = 1; v < V; ++v) mx = fmaxf(mx, l[v]);
         mx = team_max<T>(mx, Lr.mask);
-        const float inv = 1.0f / mx;
+        const float inv = __frcp_rn(mx);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const int a = v * T + Lr.tl;
@@ -764,7 +820,7 @@ __device__ bool chan_blocked(const Graph& g, const float* msg_f, size_t ustride,
             for (int a = Lr.tl; a < Q; a += T) mx = fmaxf(mx, B[a]);
             mx = team_max<T>(mx, Lr.mask);
             if (!(mx >= kFallbackMax)) bad = true;
-            const float inv = mx > 0.0f ? 1.0f / mx : 0.0f;
+            const float inv = mx > 0.0f ? __frcp_rn(mx) : 0.0f;
             for (int a = Lr.tl; a < Q; a += T) res[a] = fmaxf(B[a] * inv, kRelFloor);
             __syncwarp(Lr.mask);
         } else {
@@ -819,7 +875,7 @@ __device__ void chan_write_team(const Graph& g, float* msg_f, size_t ustride, in
                     l[v] = s;
                     lmx = fmaxf(lmx, s);
                 }
-                const float inv = 1.0f / team_max<T>(lmx, L.mask);
+                const float inv = __frcp_rn(team_max<T>(lmx, L.mask));
                 float* m = edge_ptr(blk, g.var_edge[i * g.dv + d], cbs, Q);
 #pragma unroll
                 for (int v = 0; v < V; ++v) m[v * T + L.tl] = l[v] * inv;
@@ -879,7 +935,7 @@ __device__ __forceinline__ void check_thread(float* blk, const uint8_t* coef, co
     for (int d = 0; d < kDC; ++d) {
         wht_reg<Q>(R[d]);
         const float mx = vmax(R[d]);
-        const float fl = kRelFloor * mx, inv = 1.0f / mx;
+        const float fl = kRelFloor * mx, inv = __frcp_rn(mx);
         const uint8_t* dv = gdiv + h[d] * Q;
 #pragma unroll
         for (int x = 0; x < Q; ++x) blk[d * Q + dv[x]] = fmaxf(R[d][x], fl) * inv;
@@ -971,7 +1027,7 @@ __device__ __forceinline__ void check_team_finish(float* blk, CheckRegs<Q>& c, c
 #pragma unroll
         for (int v = 1; v < V; ++v) lmx = fmaxf(lmx, R[d][v]);
         const float mx = team_max<T>(lmx, L.mask);
-        const float fl = kRelFloor * mx, inv = 1.0f / mx;
+        const float fl = kRelFloor * mx, inv = __frcp_rn(mx);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const int a = v * T + L.tl;
@@ -1158,19 +1214,11 @@ __device__ __forceinline__ void chan_thread_pos(const Graph& g, float* msg_f, fl
         if (hat_f) {
             float b[Q];
             sload<Q>(ch2v_f + pos_vec<Q>(k * NB + (p >> 5), p), b);
-            float bv = b[0] * a0[0];
-            int bi = 0;
 #pragma unroll
-            for (int a = 1; a < Q; ++a) {
-                const float v = b[a] * a0[a];
-                if (v > bv) {
-                    bv = v;
-                    bi = a;
-                }
-            }
-            hat_f[k * NB * 32 + p] = (uint8_t)bi;
+            for (int a = 0; a < Q; ++a) b[a] *= a0[a];
+            hat_f[k * NB * 32 + p] = (uint8_t)vargmax<Q>(b);
         }
-        const float inv = 1.0f / vmax(a0);
+        const float inv = __frcp_rn(vmax(a0));
 #pragma unroll
         for (int a = 0; a < Q; ++a) mu[k][a] = a0[a] * inv;
     }
@@ -1189,7 +1237,7 @@ __device__ __forceinline__ void chan_thread_pos(const Graph& g, float* msg_f, fl
             c0[a] = o[a] * c1[a];
             c1[a] = o[a] * t;
         }
-        const float i0 = 1.0f / vmax(c0), i1 = 1.0f / vmax(c1);
+        const float i0 = __frcp_rn(vmax(c0)), i1 = __frcp_rn(vmax(c1));
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
             c0[a] *= i0;
@@ -1202,15 +1250,19 @@ __device__ __forceinline__ void chan_thread_pos(const Graph& g, float* msg_f, fl
 
 // Channel node of use p for K = 4 split over a pair of lanes (lanes 2m, 2m+1 of
 // a warp; `half` = lane & 1, `mask` = the pair's lanes).  Lane h owns users
-// 2h and 2h+1: it forms P_own = mu_{2h} (*) mu_{2h+1}, receives the other
-// half's pair convolution by shuffles, scores it against G (the suffix H), and
-// emits its users' messages sum_b mu_{2h+1}(b) H(a+b) and sum_b mu_{2h}(b) H(a+b).
-// Each lane does half of the single-thread work with about half the registers.
+// 2h and 2h+1: it forms their pair convolution P_own = mu_{2h} (*) mu_{2h+1},
+// receives the other half's by shuffles, scores it
+// against G (the suffix H), and emits its users' messages
+// sum_b mu_{2h+1}(b) H(a+b) and sum_b mu_{2h}(b) H(a+b).  Each lane does half
+// of the single-thread work with about half the registers, with the same sums
+// in the same order (bit-identical to chan_thread_pos).  hat_f (may be null):
+// the folded decision of the previous iteration for the lane's two users, as
+// in chan_thread_pos.
 template <int Q>
 __device__ __forceinline__ void chan_pair_pos(const Graph& g, float* msg_f, float* ch2v_f, int NB, float y,
-                                              float inv_s2, int p, int half, unsigned mask)
+                                              float inv_s2, int p, int half, unsigned mask, uint8_t* hat_f)
 {
-    constexpr int D = Q - 1, K = 4;
+    constexpr int D = Q - 1, K = 4, NP = 2 * D + 1;
     float mu[2][Q];
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
@@ -1221,20 +1273,28 @@ __device__ __forceinline__ void chan_pair_pos(const Graph& g, float* msg_f, floa
         sload<Q>(msg_f + pos_vec<Q>(row + 1, p), a1);
 #pragma unroll
         for (int a = 0; a < Q; ++a) a0[a] *= a1[a];
-        const float inv = 1.0f / vmax(a0);
+        if (hat_f) {
+            float b[Q];
+            sload<Q>(ch2v_f + pos_vec<Q>(k * NB + (p >> 5), p), b);
+#pragma unroll
+            for (int a = 0; a < Q; ++a) b[a] *= a0[a];
+            hat_f[k * NB * 32 + p] = (uint8_t)vargmax<Q>(b);
+        }
+        const float inv = __frcp_rn(vmax(a0));
 #pragma unroll
         for (int a = 0; a < Q; ++a) mu[j][a] = a0[a] * inv;
     }
-    float Po[2 * D + 1];
+    // own pair convolution, then the other half's by shuffles
+    float Po[NP];
     {
-        float Pown[2 * D + 1];
+        float Pown[NP];
         rconv(mu[0], mu[1], Pown);
 #pragma unroll
-        for (int i = 0; i < 2 * D + 1; ++i) Po[i] = __shfl_xor_sync(mask, Pown[i], 1);
+        for (int i = 0; i < NP; ++i) Po[i] = __shfl_xor_sync(mask, Pown[i], 1);
     }
     const GaussTerm gt = gauss_term(y, K, Q, inv_s2);
-    float H[2 * D + 1];
-    rcorr_g<2 * D + 1, 2 * D + 1>(Po, H, gt);
+    float H[NP];
+    rcorr_g<NP, NP>(Po, H, gt);
     float o[2][Q];
     rcorr(mu[1], H, o[0]);   // message to user 2h
     rcorr(mu[0], H, o[1]);   // message to user 2h+1
@@ -1267,7 +1327,7 @@ __device__ __forceinline__ void chan_pair_pos(const Graph& g, float* msg_f, floa
     }
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-        const float inv = 1.0f / mx[j];
+        const float inv = __frcp_rn(mx[j]);
 #pragma unroll
         for (int a = 0; a < Q; ++a) o[j][a] = fmaxf(o[j][a] * inv, kRelFloor);
         const int k = 2 * half + j;
@@ -1284,7 +1344,7 @@ __device__ __forceinline__ void chan_pair_pos(const Graph& g, float* msg_f, floa
             c0[a] = o[j][a] * c1[a];
             c1[a] = o[j][a] * t;
         }
-        const float i0 = 1.0f / vmax(c0), i1 = 1.0f / vmax(c1);
+        const float i0 = __frcp_rn(vmax(c0)), i1 = __frcp_rn(vmax(c1));
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
             c0[a] *= i0;
@@ -1308,25 +1368,72 @@ __device__ __forceinline__ int gf_lin(const int (&basis)[6], int x)
     return r;
 }
 
-// Check node of check j of user k, thread shape, position-major layout.
-// slot_k: [E] (position*2 + d) of each edge; coef: [E] coefficients.  The
-// permuted offsets pos_sym(h^{-1} x) are XORs of the basis images scaled to
-// their offsets (both maps are GF(2)-linear in x when one symbol per chunk).
+// Record of one check unit (check j of user k) for the position-major check
+// phase, built once per CTA: for each edge d, off.{x,y,z,w}[d] = the offset of
+// the edge's message vector in the frame's message block (bits 0..23; symbol a
+// at + a*32) with the edge coefficient h in bits 24..31; basis.{x,y}: 16 bits
+// per edge, the images h^{-1} 2^b (b < log2 q, 4 bits each) from which the
+// permuted symbol h^{-1} x of any x is an XOR (division by h is GF(2)-linear).
+struct CheckRec {
+    uint4 off;
+    uint2 basis;
+};
+
 template <int Q>
-__device__ __forceinline__ void check_thread_pos(float* msg_f, int NB, int k, int j, const uint16_t* slot_k,
-                                                 const uint8_t* coef, const uint8_t* gdiv)
+__device__ __forceinline__ CheckRec check_rec(const Graph& g, int NB, int k, int j)
+{
+    unsigned o[kDC], b[kDC];
+#pragma unroll
+    for (int d = 0; d < kDC; ++d) {
+        const int e = 4 * j + d, sl = g.slot[k * g.E + e], pp = sl >> 1, h = g.chk_coef[e];
+        o[d] = (unsigned)(pos_vec<Q>((k * NB + (pp >> 5)) * 2 + (sl & 1), pp)) | ((unsigned)h << 24);
+        unsigned bb = 0;
+        for (int t = 0; (1 << t) < Q; ++t) bb |= (unsigned)g.gf_div[h * Q + (1 << t)] << (4 * t);
+        b[d] = bb;
+    }
+    CheckRec r;
+    r.off = make_uint4(o[0], o[1], o[2], o[3]);
+    r.basis = make_uint2(b[0] | (b[1] << 16), b[2] | (b[3] << 16));
+    return r;
+}
+
+__device__ __forceinline__ int rec_coef(unsigned o) { return (int)(o >> 24); }
+
+// position-order index of the edge's variable in the frame's decisions
+// (k*NB*32 + position): its message row is (k*NB + position/32)*2 + slot
+template <int Q>
+__device__ __forceinline__ int rec_hat(unsigned o)
+{
+    const unsigned v = o & 0xFFFFFFu, row = v / (Q * kLanes);
+    return (int)(((row >> 1) << 5) | (v & (kLanes - 1)));
+}
+
+template <int Q>
+__device__ __forceinline__ int rec_user(unsigned o, int NB)
+{
+    return (int)(((o & 0xFFFFFFu) / (Q * kLanes)) >> 1) / NB;
+}
+
+// Check node of one unit (check j of user k), thread shape, position-major
+// layout, from its record: the edge coefficient permutation p_e(b) = v2c_e(h^-1 b)
+// gathered through XORs of the basis images, the WHT of each edge (eq.
+// app_ldpc_c2v in the transform domain), the leave-one-out products, the inverse
+// WHT, the 1e-12 floor relative to the maximum and the scaling to max 1, and the
+// scatter back through the same permutation.
+template <int Q>
+__device__ __forceinline__ void check_thread_rec(float* msg_f, const uint4& r, const uint2& rb)
 {
     static_assert(PosW<Q>::W == 1, "offset XOR trick needs one symbol per chunk");
+    const unsigned o[kDC] = {r.x, r.y, r.z, r.w};
+    const unsigned bw[kDC] = {rb.x & 0xFFFFu, rb.x >> 16, rb.y & 0xFFFFu, rb.y >> 16};
     float P[kDC][Q];
     float* base[kDC];
     int basis[kDC][6];
 #pragma unroll
     for (int d = 0; d < kDC; ++d) {
-        const int e = 4 * j + d, sl = slot_k[e], pp = sl >> 1;
-        base[d] = msg_f + pos_vec<Q>((k * NB + (pp >> 5)) * 2 + (sl & 1), pp);
-        const uint8_t* dv = gdiv + coef[e] * Q;
+        base[d] = msg_f + (o[d] & 0xFFFFFFu);
 #pragma unroll
-        for (int b = 0; b < 6; ++b) basis[d][b] = ((1 << b) < Q) ? dv[1 << b] * kLanes : 0;
+        for (int b = 0; b < 6; ++b) basis[d][b] = ((1 << b) < Q) ? (int)((bw[d] >> (4 * b)) & 15u) * kLanes : 0;
 #pragma unroll
         for (int x = 0; x < Q; ++x) P[d][x] = base[d][gf_lin<Q>(basis[d], x)];
     }
@@ -1345,7 +1452,7 @@ __device__ __forceinline__ void check_thread_pos(float* msg_f, int NB, int k, in
     for (int d = 0; d < kDC; ++d) {
         wht_reg<Q>(P[d]);
         const float mx = vmax(P[d]);
-        const float fl = kRelFloor * mx, inv = 1.0f / mx;
+        const float fl = kRelFloor * mx, inv = __frcp_rn(mx);
 #pragma unroll
         for (int x = 0; x < Q; ++x) base[d][gf_lin<Q>(basis[d], x)] = fmaxf(P[d][x], fl) * inv;
     }
@@ -1363,15 +1470,9 @@ __device__ __forceinline__ int var_thread_pos(const float* msg_f, const float* c
     sload<Q>(msg_f + pos_vec<Q>(2 * row + 1, p), c1);
 #pragma unroll
     for (int a = 0; a < Q; ++a) b[a] *= c0[a] * c1[a];
-    float bv = b[0];
-    int bi = 0;
-#pragma unroll
-    for (int a = 1; a < Q; ++a)
-        if (b[a] > bv) {
-            bv = b[a];
-            bi = a;
-        }
+    const int bi = vargmax<Q>(b);
     if (logpost_ki) {
+        const float bv = vmax<Q>(b);
         const float l = __logf(bv);
         float o[Q];
 #pragma unroll

@@ -191,12 +191,13 @@ __global__ void __launch_bounds__(kFusedMaxThreads) k_fused(Graph g, int F, int 
 //   msg  [G][K*NB*2][q][32] f32   c2v / v2c of each variable's two edges, in place
 //   ch2v [G][K*NB][q][32]   f32
 //   y    [G][NB*32] f32, hat [G][K][NB*32] u8 (position order), unsat [G][K], active [G]
-//   slot [K][E] u16, coef [E] u8, gf mul/div [q*q] u8 (shared by the G frames)
+//   rec  [K*P] uint4, recb [K*P] uint2: one record per check unit in the order
+//        the check phase runs them (CheckRec), gf mul [q*q] u8 (shared by the G frames)
 // Phase A reads and writes consecutive banks; phase B gathers each check's
-// four edges through slot (the only irregular access of an iteration).
+// four edges through its record (the only irregular access of an iteration).
 
 struct PosLayout {
-    size_t msg, ch2v, y, hat, unsat, active, slot, order, coef, gmul, gdiv, total;
+    size_t msg, ch2v, y, hat, unsat, active, rec, recb, gmul, total;
 };
 
 __host__ __device__ inline PosLayout pos_layout(const Graph& g, int G)
@@ -210,11 +211,9 @@ __host__ __device__ inline PosLayout pos_layout(const Graph& g, int G)
     L.hat = o;    o = align16(o + (size_t)G * g.K * NB * 32);
     L.unsat = o;  o = align16(o + (size_t)G * g.K);
     L.active = o; o = align16(o + (size_t)G);
-    L.slot = o;   o = align16(o + sizeof(uint16_t) * (size_t)g.K * g.E);
-    L.order = o;  o = align16(o + sizeof(uint16_t) * (size_t)g.K * g.P);
-    L.coef = o;   o = align16(o + (size_t)g.E);
+    L.rec = o;    o = align16(o + sizeof(uint4) * (size_t)g.K * g.P);
+    L.recb = o;   o = align16(o + sizeof(uint2) * (size_t)g.K * g.P);
     L.gmul = o;   o = align16(o + (size_t)g.Q * g.Q);
-    L.gdiv = o;   o = align16(o + (size_t)g.Q * g.Q);
     L.total = o;
     return L;
 }
@@ -239,21 +238,19 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
     uint8_t* s_hat = sm + lay.hat;
     uint8_t* s_unsat = sm + lay.unsat;
     uint8_t* s_active = sm + lay.active;
-    uint16_t* s_slot = reinterpret_cast<uint16_t*>(sm + lay.slot);
-    uint16_t* s_order = reinterpret_cast<uint16_t*>(sm + lay.order);
-    uint8_t* s_coef = sm + lay.coef;
+    uint4* s_rec = reinterpret_cast<uint4*>(sm + lay.rec);
+    uint2* s_recb = reinterpret_cast<uint2*>(sm + lay.recb);
     uint8_t* s_mul = sm + lay.gmul;
-    uint8_t* s_div = sm + lay.gdiv;
     __shared__ int s_nactive;
 
     const size_t fs = (size_t)K * NB * 2 * Q * 32, vs = (size_t)K * NB * Q * 32, hs = (size_t)K * NB * 32;
-    for (int i = threadIdx.x; i < Q * Q; i += blockDim.x) {
-        s_mul[i] = g.gf_mul[i];
-        s_div[i] = g.gf_div[i];
+    for (int i = threadIdx.x; i < Q * Q; i += blockDim.x) s_mul[i] = g.gf_mul[i];
+    for (int i = threadIdx.x; i < K * P; i += blockDim.x) {
+        const int u = g.chk_order ? g.chk_order[i] : i;
+        const CheckRec r = check_rec<Q>(g, NB, u / P, u % P);
+        s_rec[i] = r.off;
+        s_recb[i] = r.basis;
     }
-    for (int i = threadIdx.x; i < K * E; i += blockDim.x) s_slot[i] = g.slot[i];
-    for (int i = threadIdx.x; i < K * P; i += blockDim.x) s_order[i] = g.chk_order ? g.chk_order[i] : (uint16_t)i;
-    for (int i = threadIdx.x; i < E; i += blockDim.x) s_coef[i] = g.chk_coef[i];
 
     const int groups = (F + G - 1) / G;
     for (int grp = blockIdx.x; grp < groups; grp += gridDim.x) {
@@ -269,7 +266,7 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
         // messages), and its syndromes and stop test run between that channel
         // phase and the next check phase; a final pass decides after the last
         // iteration.
-        const bool fold = !PAIR && logpost == nullptr;
+        const bool fold = logpost == nullptr;
         auto phase_decide = [&]() {
             for (int unit = threadIdx.x; unit < gc * K * n; unit += blockDim.x) {
                 const int gi = unit / (K * n), rem = unit % (K * n), k = rem / n, p = rem % n;
@@ -280,16 +277,14 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
                                                                               NB, k, p, lp);
             }
         };
-        // syndrome of check j of user k in frame gi (eq. app_ldpc_check_eq)
-        auto unit_syndrome = [&](int gi, int k, int j) {
-            const uint8_t* hk = s_hat + gi * hs + k * NB * 32;
+        // syndrome of the check unit with record r in frame gi (eq. app_ldpc_check_eq)
+        auto unit_syndrome = [&](int gi, const uint4& r) {
+            const uint8_t* hf = s_hat + gi * hs;
+            const unsigned o[kDC] = {r.x, r.y, r.z, r.w};
             int sy = 0;
 #pragma unroll
-            for (int d = 0; d < kDC; ++d) {
-                const int e = 4 * j + d;
-                sy ^= s_mul[s_coef[e] * Q + hk[s_slot[k * E + e] >> 1]];
-            }
-            if (sy) s_unsat[gi * K + k] = 1;
+            for (int d = 0; d < kDC; ++d) sy ^= s_mul[rec_coef(o[d]) * Q + hf[rec_hat<Q>(o[d])]];
+            if (sy) s_unsat[gi * K + rec_user<Q>(o[0], NB)] = 1;
         };
         // per-frame stop after iteration t (syndromes already recorded); returns the frames still active
         auto phase_finish = [&](int t) {
@@ -313,15 +308,16 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
         };
         auto phase_stop = [&](int t) {
             for (int w = threadIdx.x; w < gc * K * P; w += blockDim.x) {
-                const int gi = w / (K * P), rem = w % (K * P);
+                const int gi = w / (K * P);
                 if (!s_active[gi]) continue;
-                unit_syndrome(gi, rem / P, rem % P);
+                unit_syndrome(gi, s_rec[w % (K * P)]);
             }
             return phase_finish(t);
         };
         bool all_stopped = false;
         for (int t = 1; t <= T_it; ++t) {
             // (A) channel nodes, v2c in place (and, folded, the decisions of iteration t - 1)
+            const bool dec = fold && t > 1;
             if constexpr (PAIR && K == 4) {
                 const int half = threadIdx.x & 1;
                 const unsigned pmask = 3u << (threadIdx.x & 30);
@@ -329,10 +325,9 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
                     const int gi = unit / n, p = unit % n;
                     if (!s_active[gi]) continue;
                     chan_pair_pos<Q>(g, s_msg + gi * fs, s_ch2v + gi * vs, NB, s_y[gi * NB * 32 + p],
-                                     frame_inv_s2(g, f0 + gi), p, half, pmask);
+                                     frame_inv_s2(g, f0 + gi), p, half, pmask, dec ? s_hat + gi * hs : nullptr);
                 }
             } else {
-                const bool dec = fold && t > 1;
                 for (int unit = threadIdx.x; unit < gc * n; unit += blockDim.x) {
                     const int gi = unit / n, p = unit % n;
                     if (!s_active[gi]) continue;
@@ -345,10 +340,11 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
             // unit also tests its check against the decisions of iteration t - 1
             const bool syn = fold && t > 1;
             for (int unit = threadIdx.x; unit < gc * K * P; unit += blockDim.x) {
-                const int gi = unit / (K * P), rem = s_order[unit % (K * P)], k = rem / P, j = rem % P;
+                const int gi = unit / (K * P), i = unit % (K * P);
                 if (!s_active[gi]) continue;
-                if (syn) unit_syndrome(gi, k, j);
-                check_thread_pos<Q>(s_msg + gi * fs, NB, k, j, s_slot + k * E, s_coef, s_div);
+                const uint4 r = s_rec[i];
+                if (syn) unit_syndrome(gi, r);
+                check_thread_rec<Q>(s_msg + gi * fs, r, s_recb[i]);
             }
             __syncthreads();
             if (syn && phase_finish(t - 1) == 0) {

@@ -12,7 +12,9 @@ log-messages, and of its two code paths.
   iteration t into the channel phase of iteration t + 1 and the syndrome test
   into the next check phase (the path the benchmark times); with one it keeps
   separate phases.  Both must give bit-identical decisions, iteration counts and
-  syndrome flags on the same frames, in each launch shape.
+  syndrome flags on the same frames, in each launch shape, and every launch
+  shape (one thread per channel use, or a lane pair per use at 512 threads)
+  the same outputs as the first.
 """
 import math
 
@@ -53,9 +55,10 @@ def _fused_device(jbp, torch, dec, y, K, n, q, want_post, launch=None):
     return out
 
 
-@pytest.mark.parametrize("K,q,n,T,snr", [(4, 16, 256, 3, 10.0), (4, 16, 256, 6, 12.0), (2, 4, 64, 5, 10.0),
-                                         (3, 8, 64, 4, 12.0), (4, 16, 256, 1, 16.0)])
-def test_fused_logpost_matches_oracle(env, K, q, n, T, snr):
+@pytest.mark.parametrize("K,q,n,T,snr,launch", [(4, 16, 256, 3, 10.0, None), (4, 16, 256, 6, 12.0, None),
+                                                (2, 4, 64, 5, 10.0, None), (3, 8, 64, 4, 12.0, None),
+                                                (4, 16, 256, 1, 16.0, None), (4, 16, 256, 4, 10.0, (512, 1))])
+def test_fused_logpost_matches_oracle(env, K, q, n, T, snr, launch):
     jbp, O, torch = env
     code = I.make_code(n, q)
     F = 6
@@ -64,7 +67,7 @@ def test_fused_logpost_matches_oracle(env, K, q, n, T, snr):
     dec = jbp.Decoder(ctx, code, K, fr["sigma2"], fr["perm"])
     try:
         assert dec.fused_ok
-        got = _fused_device(jbp, torch, dec, fr["y"], K, n, q, want_post=True)
+        got = _fused_device(jbp, torch, dec, fr["y"], K, n, q, want_post=True, launch=launch)
     finally:
         dec.close()
         ctx.close()
@@ -86,7 +89,7 @@ def test_fused_logpost_matches_oracle(env, K, q, n, T, snr):
 
 
 @pytest.mark.parametrize("K,q,n,snr,T,launches", [
-    (4, 16, 256, 10.0, 50, [(256, 1), (128, 2), (192, 1)]),
+    (4, 16, 256, 10.0, 50, [(256, 1), (128, 2), (192, 1), (512, 1), (512, 2)]),
     (2, 4, 64, 12.0, 20, [(256, 1), (128, 4)]),
     (3, 8, 64, 14.0, 15, [(256, 1), (64, 3)]),
 ])
@@ -97,9 +100,14 @@ def test_fused_folded_path_equals_unfolded(env, K, q, n, snr, T, launches):
     fr = I.make_frames(code, K, snr, F, seed=50_000 + 100 * K + q)
     ctx = jbp.Context(iters=T, early_stop=True)
     dec = jbp.Decoder(ctx, code, K, fr["sigma2"], fr["perm"])
+    first = None
     try:
         for launch in launches:
             folded = _fused_device(jbp, torch, dec, fr["y"], K, n, q, want_post=False, launch=launch)
+            if first is None:
+                first = folded
+            for key in ("hat", "iters", "ok"):   # the launch shape changes no arithmetic
+                assert np.array_equal(folded[key], first[key]), (launch, key)
             unfolded = _fused_device(jbp, torch, dec, fr["y"], K, n, q, want_post=True, launch=launch)
             for key in ("hat", "iters", "ok"):
                 assert np.array_equal(folded[key], unfolded[key]), (launch, key)
