@@ -265,6 +265,10 @@ def make_parser() -> argparse.ArgumentParser:
                          "applies; auto: except where the register-resident trellis applies)")
     ap.add_argument("--channel-frames", type=int, default=4096, help="precision workload: frames of that leg")
     ap.add_argument("--oracle-sample", type=int, default=16, help="precision workload: oracle frames")
+    ap.add_argument("--rates", default="250,500,1000,20000,50000,100000,200000",
+                    help="serving workload: Poisson arrival rates (requests/s)")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="headline: skip the other workloads' summary (small, precision, uneven, serving)")
     return ap
 
 
@@ -404,13 +408,47 @@ def main() -> None:
     if rank == 0 and world == 1 and not args.no_extras:
         line.update(extra_legs(jbp, torch, dev, code, base, ys, sig, decs, stream))
         line["cpu_baseline"] = cpu_baseline_leg()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     for d in decs:
         d.close()
     ctx.close()
+    if rank == 0 and world == 1 and not args.no_extras and not args.no_workloads:
+        del y_d, hat_d, it_d, ok_d
+        torch.cuda.empty_cache()
+        line["workloads"] = other_workloads()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def other_workloads() -> dict:
+    """The other workloads, each on a bounded sample stated in its key and its
+    config, so that the default run stays within a few minutes: the small
+    workload in full; the precision workload (K=4, GF(64), n=512) on a quarter of
+    its 32,768 frames with an 8-frame oracle sample; the uneven batch on a tenth
+    of its 100,000 frames; serving at two rates below the knee and one above it.
+    A workload that fails is reported with its error instead of a result."""
+    base = vars(make_parser().parse_args([]))
+    runs = [
+        ("small_K2_gf4_n64_1000_frames", wl_small, {}),
+        ("precision_K4_gf64_n512_quarter_8192_frames", wl_precision,
+         {"frac": 0.25, "oracle_sample": 2, "channel_legs": 0, "steps": 1}),
+        ("uneven_tenth_10000_frames_auto_channel_node", wl_uneven, {"frac": 0.1, "channel_node": "auto", "steps": 1}),
+        ("serving_4000_request_pool_auto_channel_node", wl_serve,
+         {"frac": 0.2, "channel_node": "auto", "rates": "250,1000,20000"}),
+    ]
+    out = {}
+    for key, fn, over in runs:
+        a = argparse.Namespace(**{**base, **over})
+        t0 = time.perf_counter()
+        try:
+            r = fn(a)
+            r.pop("metric", None)
+            r["wall_s"] = time.perf_counter() - t0
+            out[key] = r
+        except Exception as e:   # report, do not lose the headline line
+            out[key] = {"error": "%s: %s" % (type(e).__name__, e), "wall_s": time.perf_counter() - t0}
+    return out
 
 
 def extra_legs(jbp, torch, dev, code, base, ys, sig, decs, stream) -> dict:
@@ -681,14 +719,22 @@ def _uneven_classes(F, seed):
     return classes, snr
 
 
+_FRAME_CACHE = {}
+
+
 def _uneven_inputs(jbp, torch, dev, ctx, classes, snr):
     from paper_2605_26580_gb300 import inputs as I
-    codes, parts = {}, []
+    parts = []
     for (n, q, K), idx in sorted(classes.items()):
-        code = codes.setdefault((n, q), I.make_code(n, q))
         Fc = len(idx)
-        fr = I.make_frames(code, K, 12.0, Fc, seed=4_000_000_000 + n * 1000 + q * 10 + K, device=dev)
-        y, sig = I.channel_output(q, fr["c"], fr["perm"], snr[idx], 4_100_000_000 + n * 1000 + q * 10 + K)
+        key = (n, q, K, Fc, tuple(idx[:4]))
+        if key not in _FRAME_CACHE:
+            code = _FRAME_CACHE.setdefault((n, q), None) or I.make_code(n, q)
+            _FRAME_CACHE[(n, q)] = code
+            fr = I.make_frames(code, K, 12.0, Fc, seed=4_000_000_000 + n * 1000 + q * 10 + K, device=dev)
+            y, sig = I.channel_output(q, fr["c"], fr["perm"], snr[idx], 4_100_000_000 + n * 1000 + q * 10 + K)
+            _FRAME_CACHE[key] = (code, fr, y, sig)
+        code, fr, y, sig = _FRAME_CACHE[key]
         dec = jbp.Decoder(ctx, code, K, float(np.mean(sig)), fr["perm"])
         parts.append({"dec": dec, "c": fr["c"], "K": K, "n": n, "q": q, "F": Fc, "y": torch.from_numpy(y).to(dev),
                       "sig": torch.from_numpy(np.asarray(sig, np.float32)).to(dev),
@@ -776,10 +822,10 @@ def wl_serve(args):
     jbp, torch, dev = _ctx_dev()
     N = int(20000 * args.frac)
     classes, snr = _uneven_classes(N, 505)
-    # the workload's rates (all above this mix's capacity of about 1.4K frames/s)
-    # and three below it, where latency is service time rather than queueing;
-    # a rate below the knee runs about 4 s of arrivals
-    rates = [250, 500, 1000, 20000, 50000, 100000, 200000]
+    # the workload's rates (20K-200K requests/s, above this mix's capacity) and
+    # rates below it, where latency is service time rather than queueing; a rate
+    # below the knee runs about 4 s of arrivals
+    rates = [int(r) for r in str(args.rates).split(",") if r]
     results = []
     for lam in rates:
         ctx = jbp.Context(iters=50, early_stop=True, mem_budget_bytes=int(64e9),
