@@ -79,8 +79,14 @@ typedef enum { JBP_PREC_FP32 = 0, JBP_PREC_BF16X2 = 1, JBP_PREC_BF16 = 2, JBP_PR
  * and q = 16, 32, 64; other handles of the context keep the trellis
  * (jbp_query_channel tells which).  AUTO: DFT except where the register-
  * resident trellis applies (q <= 16 and K <= 4), which is the faster node there
- * and keeps the fused form where a frame fits it.  No paper counterpart: the
- * paper prints no channel-node kernel. */
+ * and keeps the fused form where a frame fits it.  Under AUTO, jbp_create also
+ * times both nodes on a decoder that has the DFT form (at 1 frame and at the
+ * frame count that fills the SMs), and its serving pools run, block by block,
+ * the node measured faster for the pool's current frame count (the DFT node
+ * has a latency floor per tile of channel uses, so a pool of a few frames runs
+ * the trellis); a served frame then matches its decode alone within the DFT
+ * node's bound, not bit for bit.  No paper counterpart: the paper prints no
+ * channel-node kernel. */
 typedef enum { JBP_CHAN_TRELLIS = 0, JBP_CHAN_DFT = 1, JBP_CHAN_AUTO = 2 } jbp_channel_node;
 
 /* Launch form of jbp_decode.  AUTO picks FUSED when one frame's message state

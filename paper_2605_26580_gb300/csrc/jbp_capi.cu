@@ -244,6 +244,11 @@ struct jbp_h {
     bool tuned = false;
     uint64_t ws_gen = 0;                  // bumped whenever h->ws is reallocated (invalidates graphs)
     bool closing = false;                 // jbp_destroy in progress (under ctx->mu)
+    // measured channel-node step times (us) of a serving pool of this decoder at
+    // 1 and chan_fb frames, trellis and tensor-core node (serving under AUTO)
+    bool chan_cal = false;
+    int chan_fb = 1;
+    float chan_t1 = 0, chan_tb = 0, chan_d1 = 0, chan_db = 0;
 
     Graph graph() const
     {
@@ -579,6 +584,8 @@ static std::vector<uint16_t> check_order(int K, int P, int E, const std::vector<
     return out;
 }
 
+static int chan_calibrate(jbp_ctx* ctx, jbp_h* h);
+
 extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t q, const jbp_channel* chan,
                           jbp_h** out)
 {
@@ -699,11 +706,83 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
     FusedPlan plan;
     h->fused_ok = fused_plan(h->graph(), ctx->di, 1, 0, 0, &plan);
     cudaGetLastError();
+    if (want_dft && ctx->opt.channel_node == JBP_CHAN_AUTO && (rc = chan_calibrate(ctx, h)) != JBP_OK) {
+        jbp_destroy(h);
+        return rc;
+    }
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
         ctx->handles++;
     }
     *out = h;
+    return JBP_OK;
+}
+
+// The tensor-core channel node's launches have a latency floor (one CTA per
+// tile of 128 channel uses), so a launch over a few frames is faster on the
+// trellis.  Under AUTO, jbp_create measures both nodes on a decoder with DFT
+// tables at 1 frame and at fb frames (the count whose tiles fill the SMs, at
+// most 256 MB of temporary state) on a uniform message state; serving pools then
+// take the node that chan_est rates faster for their frame count.
+static int chan_calibrate(jbp_ctx* ctx, jbp_h* h)
+{
+    const DeviceInfo& di = ctx->di;
+    const size_t per_frame = (size_t)state_bytes(h->graph()) + sizeof(float) * h->n + 1;
+    int fb = std::max(1, (128 * di.sm_count + h->n - 1) / h->n);
+    fb = (int)std::max<size_t>(1, std::min<size_t>((size_t)fb, (size_t(256) << 20) / per_frame));
+    float *msg = nullptr, *ch2v = nullptr, *y = nullptr;
+    uint8_t* act = nullptr;
+    int64_t acct = 0;
+    int rc;
+    if ((rc = dev_alloc(ctx, &msg, (size_t)fb * h->K * h->E * h->Q, &acct)) ||
+        (rc = dev_alloc(ctx, &ch2v, (size_t)fb * h->K * h->n * h->Q, &acct)) ||
+        (rc = dev_alloc(ctx, &y, (size_t)fb * h->n, &acct)) || (rc = dev_alloc(ctx, &act, (size_t)fb, &acct))) {
+        dev_free(ctx, msg, sizeof(float) * (size_t)fb * h->K * h->E * h->Q);
+        dev_free(ctx, ch2v, sizeof(float) * (size_t)fb * h->K * h->n * h->Q);
+        dev_free(ctx, y, sizeof(float) * (size_t)fb * h->n);
+        dev_free(ctx, act, (size_t)fb);
+        return rc;
+    }
+    cudaStream_t s = ctx->stream;
+    cudaEvent_t a = nullptr, b = nullptr;
+    float t[2][2] = {{0, 0}, {0, 0}};
+    cudaError_t e = launch_fill(msg, (size_t)fb * h->K * h->E * h->Q, 1.0f, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(y, 0, sizeof(float) * (size_t)fb * h->n, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(act, 1, (size_t)fb, s);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    for (int node = 0; node < 2 && e == cudaSuccess; ++node) {
+        Graph g = h->graph();
+        if (node == 0) g.dft_tab = nullptr;
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+            const int F = i == 0 ? 1 : fb;
+            float best = 1e30f;
+            for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+                float ms = 0;
+                e = cudaEventRecord(a, s);
+                if (e == cudaSuccess) e = launch_channel(g, di, F, y, msg, ch2v, act, s);
+                if (e == cudaSuccess) e = cudaEventRecord(b, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(b);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+                if (rep > 0) best = std::min(best, ms * 1e3f);   // the first launch is a warm-up
+            }
+            t[node][i] = best;
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    dev_free(ctx, msg, sizeof(float) * (size_t)fb * h->K * h->E * h->Q);
+    dev_free(ctx, ch2v, sizeof(float) * (size_t)fb * h->K * h->n * h->Q);
+    dev_free(ctx, y, sizeof(float) * (size_t)fb * h->n);
+    dev_free(ctx, act, (size_t)fb);
+    if (e != cudaSuccess || e2 != cudaSuccess) return cuda_fail(e != cudaSuccess ? e : e2, "channel-node calibration");
+    h->chan_t1 = t[0][0];
+    h->chan_tb = t[0][1];
+    h->chan_d1 = t[1][0];
+    h->chan_db = t[1][1];
+    h->chan_fb = fb;
+    h->chan_cal = true;
     return JBP_OK;
 }
 
@@ -1332,6 +1411,24 @@ static void pool_retire(jbp_ctx* ctx, ServePool& p, cudaError_t q)
     publish(ctx, out, lat);
 }
 
+// Step time of one channel-node launch over F frames, from two measured points
+// (1 and fb frames): linear between them, proportional to F beyond fb.
+static float chan_est(float t1, float tb, int fb, int F)
+{
+    if (F <= 1 || fb <= 1) return F <= 1 ? t1 : tb * (float)F / (float)fb;
+    if (F <= fb) return t1 + (tb - t1) * (float)(F - 1) / (float)(fb - 1);
+    return tb * (float)F / (float)fb;
+}
+
+// Under AUTO a serving pool runs the tensor-core channel node only where it is
+// the faster one for the pool's current frame count (chan_calibrate).
+static bool pool_use_dft(const jbp_ctx* ctx, const jbp_h* h, int F)
+{
+    if (!h->d_dft_tab) return false;
+    if (ctx->opt.channel_node != JBP_CHAN_AUTO || !h->chan_cal) return true;
+    return chan_est(h->chan_d1, h->chan_db, h->chan_fb, F) < chan_est(h->chan_t1, h->chan_tb, h->chan_fb, F);
+}
+
 // Stage `take` into free slots and launch the pool's next block.
 static int pool_launch(jbp_ctx* ctx, ServePool& p, std::vector<Request>& take)
 {
@@ -1364,6 +1461,7 @@ static int pool_launch(jbp_ctx* ctx, ServePool& p, std::vector<Request>& take)
     g.sigma2_f = P<float>(p.sig);
     const DeviceInfo& di = ctx->di;
     const int F = p.hi;
+    if (!pool_use_dft(ctx, h, F)) g.dft_tab = nullptr;
     float* msg = P<float>(p.msg);
     float* ch2v = P<float>(p.ch2v);
     const uint8_t* act = P<uint8_t>(p.active);

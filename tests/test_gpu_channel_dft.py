@@ -14,6 +14,7 @@ oracle, max-normalised linear messages therefore differ by at most
 (K + 2) 2^-9 + K 2^-12; the tests print the measured value (a few 1e-4).
 """
 import math
+import time
 
 import numpy as np
 import pytest
@@ -386,3 +387,45 @@ def test_dft_many_tiles_equal_small_batches(env, K, q, n, F):
     finally:
         dec.close()
         ctx.close()
+
+
+def test_auto_serving_small_and_large_pools_match_the_oracle(env):
+    """Serving under AUTO: a pool runs the tensor-core channel node only where it
+    is faster for the pool's frame count (measured per decoder when its first
+    pool is created), so a frame served alone runs the trellis and frames served
+    in a burst run the transform.  Either way the results match the oracle:
+    decisions where its margin exceeds 2e-2 (the transform's bar, as for the
+    config-3 shape), iterations and syndrome flags, on converging frames."""
+    jbp, O, torch = env
+    K, q, n, T = 4, 64, 64, 8
+    code = I.make_code(n, q)
+    fr = I.make_frames(code, K, 30.0, 24, seed=1701)
+    ctx = jbp.Context(iters=T, early_stop=True, channel_node=jbp.CHAN_AUTO)
+    dec = jbp.Decoder(ctx, code, K, fr["sigma2"], fr["perm"])
+    got = {}
+
+    def wait(tk):
+        deadline = time.time() + 60.0
+        while (res := ctx.poll(tk, n, K)) is None:
+            assert time.time() < deadline, "served frame not finished within 60 s"
+            time.sleep(1e-4)
+        return res
+
+    try:
+        assert dec.channel_node == jbp.CHAN_DFT
+        # one frame at a time (a pool of one frame), then the rest in one burst
+        for i in range(4):
+            got[i] = wait(dec.submit(fr["y"][i]))
+        tickets = [(i, dec.submit(fr["y"][i])) for i in range(4, 24)]
+        for i, tk in tickets:
+            got[i] = wait(tk)
+        assert dec.tc_timeouts() == 0
+    finally:
+        dec.close()
+        ctx.close()
+    ref = O.decode(code, K, fr["sigma2"], fr["perm"], fr["y"], T, early_stop=True, want_margin=True)
+    for i in range(24):
+        sure = ref["margin"][i] > 2e-2
+        assert not ((got[i]["hat"] != ref["hat"][i]) & sure).any(), i
+        assert got[i]["iters"] == int(ref["iters"][i]), i
+        assert np.array_equal(got[i]["ok"], ref["ok"][i]), i
