@@ -100,10 +100,15 @@ typedef enum { JBP_FORM_AUTO = 0, JBP_FORM_FUSED = 1, JBP_FORM_STEP = 2, JBP_FOR
 typedef struct jbp_ctx jbp_ctx;  /* one GPU, its streams, memory budget and serving loop */
 typedef struct jbp_h jbp_h;      /* one (code, K, q, channel) decoder bound to a context  */
 
-/* Parity-check matrix H (P x n over GF(q)), regular: every check has dc edges,
- * every variable dv edges.  chk_var [P*dc]: variable index of each edge;
- * chk_coef [P*dc]: nonzero coefficient H_{j,l} in 1..q-1.  Host pointers,
- * copied by jbp_create; the caller keeps ownership. */
+/* Parity-check matrix H (P x n over GF(q)): every check has dc edges (dc = 3,
+ * 4 or 6); dv is the largest variable degree, and a variable may have fewer
+ * edges (an irregular variable-degree profile; the paper's construction of H
+ * samples a sparse support with no degree regularity).  chk_var [P*dc]: variable
+ * index of each edge; chk_coef [P*dc]: nonzero coefficient H_{j,l} in 1..q-1.
+ * Host pointers, copied by jbp_create; the caller keeps ownership.  The fused
+ * form's fast (position-major) shape and the tensor-core variants need dc = 4,
+ * the former also every variable of degree 2; other codes run the step form or
+ * the fused form's team shape. */
 typedef struct {
     int32_t n, P, q, dv, dc;
     const int32_t *chk_var;
@@ -185,10 +190,11 @@ int jbp_context_destroy(jbp_ctx *ctx);
  * builds the GF(q) multiply and divide tables (jbp_gf_tables), the per-user
  * slot tables of the fused form and the check order of its shared-memory
  * layout; the caller keeps ownership of every host array.  Supported shapes:
- * q in {2,4,8,16,32,64}, dc = 4, dv >= 1 regular, n >= 1.  Errors: JBP_EINVAL
- * (NULL pointers, unsupported shape, an edge list that is not regular or a
- * coefficient outside 1..q-1), JBP_ENOMEM (over the context's budget),
- * JBP_ECUDA. */
+ * q in {2,4,8,16,32,64}, dc in {3, 4, 6}, variable degrees 0..dv with
+ * 1 <= dv <= 8, n >= 1; the tensor-core check variants (precision other than
+ * FP32) need dc = 4.  Errors: JBP_EINVAL (NULL pointers, unsupported shape, a
+ * variable with more than dv edges or a coefficient outside 1..q-1),
+ * JBP_ENOMEM (over the context's budget), JBP_ECUDA. */
 int jbp_create(jbp_ctx *ctx, const jbp_code *code, int32_t K, int32_t q,
                const jbp_channel *chan, jbp_h **out);
 

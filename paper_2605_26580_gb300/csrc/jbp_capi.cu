@@ -222,6 +222,7 @@ struct jbp_ctx {
 struct jbp_h {
     jbp_ctx* ctx = nullptr;
     int K = 0, Q = 0, m = 0, n = 0, P = 0, dc = 0, dv = 0, E = 0;
+    bool var_reg = true;                  // every variable has dv edges
     double sigma2 = 0;
     int32_t* d_chk_var = nullptr;
     uint8_t* d_chk_coef = nullptr;
@@ -264,6 +265,7 @@ struct jbp_h {
         g.sigma2_f = nullptr;
         g.chk_order = d_chk_order;
         g.dft_tab = d_dft_tab;
+        g.var_reg = var_reg ? 1 : 0;
         return g;
     }
 };
@@ -596,16 +598,19 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
     if (code->q != q) return fail(JBP_EINVAL, "code->q (%d) != q (%d)", code->q, q);
     if (K < 1 || K > kMaxK) return fail(JBP_EINVAL, "K must be in 1..%d (got %d)", kMaxK, K);
     if (code->n < 1 || code->P < 1) return fail(JBP_EINVAL, "n and P must be >= 1");
-    if (code->dc != 4) return fail(JBP_EINVAL, "only check degree dc = 4 is built (got %d)", code->dc);
+    if (code->dc != 3 && code->dc != 4 && code->dc != 6)
+        return fail(JBP_EINVAL, "check degree dc must be 3, 4 or 6 (got %d)", code->dc);
     if (code->dv < 1 || code->dv > kMaxDv) return fail(JBP_EINVAL, "dv must be in 1..%d (got %d)", kMaxDv, code->dv);
-    if ((int64_t)code->n * code->dv != (int64_t)code->P * code->dc)
-        return fail(JBP_EINVAL, "n*dv (%d*%d) != P*dc (%d*%d)", code->n, code->dv, code->P, code->dc);
+    if ((int64_t)code->n * code->dv < (int64_t)code->P * code->dc)
+        return fail(JBP_EINVAL, "P*dc (%d*%d) edges exceed n*dv (%d*%d)", code->P, code->dc, code->n, code->dv);
+    if (ctx->opt.precision != JBP_PREC_FP32 && code->dc != kDC)
+        return fail(JBP_EINVAL, "the tensor-core check variants are built for dc = 4 (got %d)", code->dc);
     if (!code->chk_var || !code->chk_coef) return fail(JBP_EINVAL, "NULL code arrays");
     if (!(chan->sigma2 > 0.0) || !std::isfinite(chan->sigma2)) return fail(JBP_EINVAL, "sigma2 must be finite and > 0");
     if (chan->interleave && !chan->perm) return fail(JBP_EINVAL, "interleave = 1 needs perm");
     const int n = code->n, P = code->P, dc = code->dc, dv = code->dv, E = P * dc;
 
-    std::vector<int32_t> var_edge((size_t)n * dv), fill(n, 0);
+    std::vector<int32_t> var_edge((size_t)n * dv, -1), fill(n, 0);
     for (int e = 0; e < E; ++e) {
         const int i = code->chk_var[e];
         if (i < 0 || i >= n) return fail(JBP_EINVAL, "chk_var[%d] = %d out of range", e, i);
@@ -613,8 +618,10 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
         if (fill[i] >= dv) return fail(JBP_EINVAL, "variable %d has more than dv = %d edges", i, dv);
         var_edge[(size_t)i * dv + fill[i]++] = e;
     }
-    for (int i = 0; i < n; ++i)
-        if (fill[i] != dv) return fail(JBP_EINVAL, "variable %d has %d edges, expected dv = %d", i, fill[i], dv);
+    // dv is the largest variable degree: a variable may have fewer edges (an
+    // irregular degree profile; its var_edge row ends with -1 entries)
+    bool var_reg = true;
+    for (int i = 0; i < n; ++i) var_reg = var_reg && fill[i] == dv;
     std::vector<int32_t> use_pos((size_t)K * n, -1);
     for (int k = 0; k < K; ++k)
         for (int i = 0; i < n; ++i) {
@@ -628,7 +635,7 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
     std::vector<int32_t> pos_of((size_t)K * n);
     for (int k = 0; k < K; ++k)
         for (int i = 0; i < n; ++i) pos_of[(size_t)k * n + i] = chan->interleave ? chan->perm[(size_t)k * n + i] : i;
-    const bool want_slot = dv == 2 && n <= 32767;
+    const bool want_slot = dv == 2 && var_reg && n <= 32767;
     std::vector<uint16_t> slot(want_slot ? (size_t)K * E : 0);
     if (want_slot)
         for (int k = 0; k < K; ++k)
@@ -648,7 +655,7 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
     const bool thread_shape = q <= 16 && K <= 4;
     const bool want_dft = (ctx->opt.channel_node == JBP_CHAN_DFT ||
                            (ctx->opt.channel_node == JBP_CHAN_AUTO && !thread_shape)) &&
-                          dv == 2 && dc == kDC && dsh.ok && dsh.smem <= ctx->di.smem_optin;
+                          dv == 2 && var_reg && dc == kDC && dsh.ok && dsh.smem <= ctx->di.smem_optin;
     std::vector<unsigned char> dft_tab;   // shape tables, then this handle's message offsets
     if (want_dft) {
         dft_tab.resize(dft_table_bytes(K, q) + dft_offsets_bytes(K, n));
@@ -668,6 +675,7 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
     if (!h) return fail(JBP_ENOMEM, "host allocation failed");
     h->ctx = ctx; h->K = K; h->Q = q; h->m = m; h->n = n; h->P = P; h->dc = dc; h->dv = dv; h->E = E;
     h->sigma2 = chan->sigma2;
+    h->var_reg = var_reg;
     int rc;
     if ((rc = dev_alloc(ctx, &h->d_chk_var, (size_t)E, &h->table_bytes)) ||
         (rc = dev_alloc(ctx, &h->d_chk_coef, (size_t)E, &h->table_bytes)) ||

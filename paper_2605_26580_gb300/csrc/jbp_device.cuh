@@ -51,7 +51,18 @@ struct Graph {
     const float* sigma2_f;    // [F]     per-frame noise variance of this batch (may be null)
     const uint16_t* chk_order;  // [K*P] order of the check units in the fused check phase (may be null)
     const unsigned char* dft_tab = nullptr;   // DFT tables of the tensor-core channel node (null: trellis)
+    int var_reg = 1;          // 1: every variable has exactly dv edges; 0: var_edge rows end early with -1
 };
+
+// Edges of variable i: g.dv when the code is variable-regular, else the entries
+// of its var_edge row before the first -1 (rows are padded to the largest degree).
+__device__ __forceinline__ int var_degree(const Graph& g, int i)
+{
+    if (g.var_reg) return g.dv;
+    int d = 0;
+    while (d < g.dv && g.var_edge[i * g.dv + d] >= 0) ++d;
+    return d;
+}
 
 // 1 / sigma2 of frame f
 __device__ __forceinline__ float frame_inv_s2(const Graph& g, long f)
@@ -547,7 +558,8 @@ __device__ bool chan_trellis(const Graph& g, const float* msg_f, size_t ustride,
         float l[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) l[v] = SR::kLog ? 0.0f : 1.0f;
-        for (int d = 0; d < g.dv; ++d) {
+        const int deg = var_degree(g, i);
+        for (int d = 0; d < deg; ++d) {
             const float* m = edge_ptr(blk, g.var_edge[i * g.dv + d], cbs, Q);
 #pragma unroll
             for (int v = 0; v < V; ++v) {
@@ -789,7 +801,8 @@ __device__ bool chan_blocked(const Graph& g, const float* msg_f, size_t ustride,
         float l[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) l[v] = 1.0f;
-        for (int d = 0; d < g.dv; ++d) {
+        const int deg = var_degree(g, i);
+        for (int d = 0; d < deg; ++d) {
             const float* m = edge_ptr(blk, g.var_edge[i * g.dv + d], cbs, Q);
 #pragma unroll
             for (int v = 0; v < V; ++v) l[v] *= m[v * T + Lr.tl];
@@ -854,16 +867,17 @@ __device__ void chan_write_team(const Graph& g, float* msg_f, size_t ustride, in
             ch2v_f[((size_t)k * g.n + i) * Q + v * T + L.tl] = ch[v];
         }
         float cv[kMaxDv][V];
+        const int deg = var_degree(g, i);
 #pragma unroll
         for (int d = 0; d < kMaxDv; ++d)
-            if (d < g.dv) {
+            if (d < deg) {
                 const float* m = edge_ptr(blk, g.var_edge[i * g.dv + d], cbs, Q);
 #pragma unroll
                 for (int v = 0; v < V; ++v) cv[d][v] = m[v * T + L.tl];
             }
 #pragma unroll
         for (int d = 0; d < kMaxDv; ++d)
-            if (d < g.dv) {
+            if (d < deg) {
                 float l[V];
                 float lmx = kNegInf;
 #pragma unroll
@@ -871,7 +885,7 @@ __device__ void chan_write_team(const Graph& g, float* msg_f, size_t ustride, in
                     float s = ch[v];
 #pragma unroll
                     for (int d2 = 0; d2 < kMaxDv; ++d2)
-                        if (d2 < g.dv && d2 != d) s *= cv[d2][v];
+                        if (d2 < deg && d2 != d) s *= cv[d2][v];
                     l[v] = s;
                     lmx = fmaxf(lmx, s);
                 }
@@ -1058,7 +1072,8 @@ __device__ __forceinline__ void var_thread(const Graph& g, const float* ch2v_fk,
 {
     float b[Q];
     vload<Q>(ch2v_fk + (size_t)i * Q, b);
-    for (int d = 0; d < g.dv; ++d) {
+    const int deg = var_degree(g, i);
+    for (int d = 0; d < deg; ++d) {
         float t[Q];
         vload<Q>(edge_ptr(blk, g.var_edge[i * g.dv + d], cbs, Q), t);
 #pragma unroll
@@ -1090,7 +1105,8 @@ __device__ void var_team(const Graph& g, const float* ch2v_fk, const float* blk,
     float b[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) b[v] = ch2v_fk[(size_t)i * Q + v * T + L.tl];
-    for (int d = 0; d < g.dv; ++d) {
+    const int deg = var_degree(g, i);
+    for (int d = 0; d < deg; ++d) {
         const float* m = edge_ptr(blk, g.var_edge[i * g.dv + d], cbs, Q);
 #pragma unroll
         for (int v = 0; v < V; ++v) b[v] *= m[v * T + L.tl];

@@ -178,16 +178,16 @@ __device__ __forceinline__ void wht_lanes(float (&p)[StageShape<Q>::W], int l, u
     }
 }
 
-template <int Q>
+template <int Q, int DC>
 __device__ __forceinline__ void check_lanes_lin(float* blk, const uint8_t* coef, const uint8_t* gdiv, int l,
                                                 unsigned mask)
 {
     constexpr int LPC = StageShape<Q>::LPC, W = StageShape<Q>::W;
-    float P[kDC][W];
-    int basis[kDC][4];   // images of the low four basis vectors
-    int lane_off[kDC];   // image of 16 l
+    float P[DC][W];
+    int basis[DC][4];   // images of the low four basis vectors
+    int lane_off[DC];   // image of 16 l
 #pragma unroll
-    for (int d = 0; d < kDC; ++d) {
+    for (int d = 0; d < DC; ++d) {
         const uint8_t* dv = gdiv + coef[d] * Q;
 #pragma unroll
         for (int b = 0; b < 4; ++b) basis[d][b] = ((1 << b) < W) ? dv[1 << b] : 0;
@@ -202,20 +202,31 @@ __device__ __forceinline__ void check_lanes_lin(float* blk, const uint8_t* coef,
         }
     }
 #pragma unroll
-    for (int d = 0; d < kDC; ++d) wht_lanes<Q>(P[d], l, mask);
+    for (int d = 0; d < DC; ++d) wht_lanes<Q>(P[d], l, mask);
 #pragma unroll
-    for (int d = 0; d < kDC; ++d) {
+    for (int d = 0; d < DC; ++d) {
+        // leave-one-out product of the other DC - 1 transforms: for DC = 4 the
+        // pairing (P0 P1)(P2 P3) of check_thread, otherwise prefix times suffix
         float R[W];
 #pragma unroll
         for (int j = 0; j < W; ++j) {
-            const float l01 = P[0][j] * P[1][j], r23 = P[2][j] * P[3][j];
-            R[j] = d == 0 ? P[1][j] * r23 : d == 1 ? P[0][j] * r23 : d == 2 ? l01 * P[3][j] : l01 * P[2][j];
+            if constexpr (DC == 4) {
+                const float l01 = P[0][j] * P[1][j], r23 = P[2][j] * P[3][j];
+                R[j] = d == 0 ? P[1][j] * r23 : d == 1 ? P[0][j] * r23 : d == 2 ? l01 * P[3][j] : l01 * P[2][j];
+            } else {
+                float pre = 1.0f, suf = 1.0f;
+#pragma unroll
+                for (int e = 0; e < d; ++e) pre *= P[e][j];
+#pragma unroll
+                for (int e = DC - 1; e > d; --e) suf *= P[e][j];
+                R[j] = pre * suf;
+            }
         }
         wht_lanes<Q>(R, l, mask);
         float mx = vmax(R);
 #pragma unroll
         for (int o = 1; o < LPC; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(mask, mx, o, LPC));
-        const float fl = kRelFloor * mx, inv = 1.0f / mx;
+        const float fl = kRelFloor * mx, inv = __frcp_rn(mx);
 #pragma unroll
         for (int j = 0; j < W; ++j) {
             int o = lane_off[d];
@@ -227,11 +238,11 @@ __device__ __forceinline__ void check_lanes_lin(float* blk, const uint8_t* coef,
     }
 }
 
-template <int Q>
+template <int Q, int DC>
 __global__ void __launch_bounds__(kStageThreads, 3) k_check_staged(Graph g, long total, float* msg,
                                                                   const uint8_t* __restrict__ active)
 {
-    constexpr int CB = kDC * Q;   // floats per check block
+    constexpr int CB = DC * Q;   // floats per check block
     constexpr int LPC = StageShape<Q>::LPC, kStageChecks = kStageThreads / LPC;
     extern __shared__ __align__(128) float tiles[];   // [2][kStageChecks * CB]
     __shared__ __align__(8) uint64_t mbar_s[2];
@@ -291,7 +302,7 @@ __global__ void __launch_bounds__(kStageThreads, 3) k_check_staged(Graph g, long
         const unsigned mask = LPC == 1 ? 0xffffffffu : (((1u << LPC) - 1u) << ((threadIdx.x & 31) & ~(LPC - 1)));
         const long c = tile * kStageChecks + slot;
         if (c < total && (!active || active[c / per_frame]))
-            check_lanes_lin<Q>(buf + slot * CB, g.chk_coef + kDC * (int)(c % g.P), sdiv, l, mask);
+            check_lanes_lin<Q, DC>(buf + slot * CB, g.chk_coef + DC * (int)(c % g.P), sdiv, l, mask);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (threadIdx.x == 0) bulk_store(tile_ptr(tile), s_addr(buf), tile_bytes(tile));
@@ -529,7 +540,7 @@ cudaError_t channel_q(const Graph& g, const DeviceInfo& di, int F, const float* 
                       const uint8_t* active, cudaStream_t s)
 {
     if constexpr (Q <= 16) {
-        if (g.dv == 2) {
+        if (g.dv == 2 && g.var_reg) {
             switch (g.K) {
                 case 1: return channel_thread_q<Q, 1>(g, di, F, y, msg, ch2v, active, s);
                 case 2: return channel_thread_q<Q, 2>(g, di, F, y, msg, ch2v, active, s);
@@ -542,18 +553,31 @@ cudaError_t channel_q(const Graph& g, const DeviceInfo& di, int F, const float* 
     return channel_team_q<Q>(g, di, F, y, msg, ch2v, active, s);
 }
 
+template <int Q, int DC>
+cudaError_t check_qd(const Graph& g, const DeviceInfo& di, int F, float* msg, const uint8_t* active, cudaStream_t s)
+{
+    const long units = (long)F * g.K * g.P;
+    constexpr int checks_per_tile = kStageThreads / StageShape<Q>::LPC;
+    const size_t smem = 2ull * checks_per_tile * DC * Q * sizeof(float);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_check_staged<Q, DC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = persistent_grid(k_check_staged<Q, DC>, kStageThreads, smem, di, checks_per_tile, units);
+    k_check_staged<Q, DC><<<grid, kStageThreads, smem, s>>>(g, units, msg, active);
+    return cudaGetLastError();
+}
+
+// check degrees built: 3, 4 and 6 (codes of rate 1/3 with dv = 2, rate 1/2 with
+// (2, 4) and (3, 6), and any variable-degree profile with these check degrees)
 template <int Q>
 cudaError_t check_q(const Graph& g, const DeviceInfo& di, int F, float* msg, const uint8_t* active, cudaStream_t s)
 {
-    if (g.dc != kDC) return cudaErrorInvalidValue;
-    const long units = (long)F * g.K * g.P;
-    constexpr int checks_per_tile = kStageThreads / StageShape<Q>::LPC;
-    const size_t smem = 2ull * checks_per_tile * kDC * Q * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_check_staged<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int grid = persistent_grid(k_check_staged<Q>, kStageThreads, smem, di, checks_per_tile, units);
-    k_check_staged<Q><<<grid, kStageThreads, smem, s>>>(g, units, msg, active);
-    return cudaGetLastError();
+    switch (g.dc) {
+        case 3: return check_qd<Q, 3>(g, di, F, msg, active, s);
+        case 4: return check_qd<Q, 4>(g, di, F, msg, active, s);
+        case 6: return check_qd<Q, 6>(g, di, F, msg, active, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <int Q>
@@ -562,7 +586,7 @@ cudaError_t var_q(const Graph& g, const DeviceInfo& di, int F, const float* ch2v
 {
     constexpr int T = Shape<Q>::T;
     const long units = (long)F * g.K * g.n;
-    if (g.dv == 2) {
+    if (g.dv == 2 && g.var_reg) {
         if constexpr (Q <= 16) {
             const int grid = persistent_grid(k_var_thread<Q>, kStepThreads, 0, di, kStepThreads, units);
             k_var_thread<Q><<<grid, kStepThreads, 0, s>>>(g, F, ch2v, msg, post, hat, active);

@@ -121,6 +121,50 @@ def make_code(n: int, q: int, dv: int = 2, dc: int = 4, seed: int | None = None)
     return code
 
 
+def make_irregular_code(n: int, q: int, profile: dict, dc: int, seed: int | None = None) -> dict:
+    """GF(q) LDPC code with an irregular variable-degree profile and check degree dc.
+
+    profile maps a variable degree to the fraction of variables that have it
+    (e.g. {2: 0.5, 3: 0.3, 4: 0.2}).  The per-degree counts are the rounded
+    fractions, then variables move one degree down (from the largest degree
+    present) until the edge count is a multiple of dc; degrees are assigned to
+    variables by a seeded shuffle.  The sockets are then placed and repaired as in
+    make_code (no double edges, no 4-cycles); coefficients i.i.d. uniform on
+    {1, ..., q-1} (appendix "Construction of H": a sampled sparse support with
+    i.i.d. nonzero coefficients).  code["dv"] is the largest degree.
+    """
+    m = log2_exact(q)
+    rng = np.random.Generator(np.random.PCG64((code_seed(n, q) + 29) if seed is None else seed))
+    degs = sorted(profile)
+    counts = {d: int(round(profile[d] * n)) for d in degs}
+    counts[degs[0]] += n - sum(counts.values())
+    total = sum(d * c for d, c in counts.items())
+    while total % dc:
+        top = max(d for d in degs if counts[d] > 0 and d > 1)
+        counts[top] -= 1
+        counts[top - 1] = counts.get(top - 1, 0) + 1
+        total -= 1
+    deg = np.concatenate([np.full(c, d, dtype=np.int64) for d, c in sorted(counts.items()) if c > 0])
+    deg = deg[rng.permutation(n)]
+    P = int(deg.sum()) // dc
+    sockets = np.repeat(np.arange(n, dtype=np.int64), deg)
+    chk_var = sockets[rng.permutation(sockets.size)]
+    for _ in range(100000):
+        bad = _four_cycle_edges(chk_var, P, dc)
+        if bad.size == 0:
+            break
+        e1 = int(rng.choice(bad))
+        e2 = int(rng.integers(0, sockets.size))
+        chk_var[e1], chk_var[e2] = chk_var[e2], chk_var[e1]
+    else:
+        raise RuntimeError("could not remove 4-cycles")
+    chk_coef = rng.integers(1, q, size=P * dc)
+    code = {"n": n, "P": P, "q": q, "m": m, "dv": int(deg.max()), "dc": dc,
+            "chk_var": chk_var.astype(np.int32), "chk_coef": chk_coef.astype(np.uint8), "var_deg": deg.astype(np.int32)}
+    code.update(_encoder(code))
+    return code
+
+
 def make_peg_code(n: int, q: int, dv: int = 2, dc: int = 3, seed: int | None = None) -> dict:
     """Regular (dv, dc) GF(q) LDPC code by progressive edge growth.
 
@@ -223,7 +267,8 @@ def code_from_edges(n: int, q: int, dc: int, chk_var, chk_coef) -> dict:
     chk_coef = np.asarray(chk_coef, dtype=np.uint8).reshape(-1)
     if chk_var.size % dc:
         raise ValueError("edge count must be a multiple of dc")
-    code = {"n": n, "P": chk_var.size // dc, "q": q, "m": log2_exact(q), "dv": None, "dc": dc,
+    deg = np.bincount(chk_var, minlength=n)
+    code = {"n": n, "P": chk_var.size // dc, "q": q, "m": log2_exact(q), "dv": int(deg.max()), "dc": dc,
             "chk_var": chk_var, "chk_coef": chk_coef}
     code.update(_encoder(code))
     return code

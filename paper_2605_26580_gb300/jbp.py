@@ -240,7 +240,7 @@ class Decoder:
         self.K, self.n, self.q = int(K), int(code["n"]), int(code["q"])
         self._chk_var = np.ascontiguousarray(code["chk_var"], dtype=np.int32)
         self._chk_coef = np.ascontiguousarray(code["chk_coef"], dtype=np.uint8)
-        dv = code.get("dv") or int(self._chk_var.size // self.n)
+        dv = code.get("dv") or int(np.bincount(self._chk_var, minlength=self.n).max())   # largest degree
         c = Code(self.n, int(code["P"]), self.q, int(dv), int(code["dc"]),
                  self._chk_var.ctypes.data_as(C.POINTER(C.c_int32)),
                  self._chk_coef.ctypes.data_as(C.POINTER(C.c_uint8)))
@@ -342,7 +342,7 @@ class EvidenceDecoder:
         self._chk_coef = np.ascontiguousarray(code["chk_coef"], dtype=np.uint8)
         self._rows = np.ascontiguousarray(rows, dtype=np.int32)
         self.ns = int(self._rows.shape[1])
-        dv = code.get("dv") or int(self._chk_var.size // self.n)
+        dv = code.get("dv") or int(np.bincount(self._chk_var, minlength=self.n).max())   # largest degree
         c = Code(self.n, int(code["P"]), self.q, int(dv), int(code["dc"]),
                  self._chk_var.ctypes.data_as(C.POINTER(C.c_int32)),
                  self._chk_coef.ctypes.data_as(C.POINTER(C.c_uint8)))

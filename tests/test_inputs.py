@@ -126,3 +126,26 @@ def test_peg_codes_are_regular_with_larger_girth(L):
     assert I.girth(c) > I.girth(I.make_code(L, 64, dv=2, dc=3))
     again = I.make_peg_code(L, 64)
     assert np.array_equal(c["chk_var"], again["chk_var"]) and np.array_equal(c["chk_coef"], again["chk_coef"])
+
+
+def test_irregular_code_follows_its_profile(oracle):
+    """make_irregular_code: the variable degrees follow the profile (rounded, the
+    edge count made a multiple of dc), every check has dc distinct variables, no
+    two variables share two checks, and generated codewords satisfy H c = 0."""
+    import itertools
+    code = I.make_irregular_code(128, 16, {2: 0.5, 3: 0.3, 4: 0.2}, 4)
+    deg = np.bincount(code["chk_var"], minlength=128)
+    assert code["dv"] == deg.max() == 4
+    assert sum(deg) == code["P"] * 4
+    assert abs((deg == 2).sum() - 64) <= 1 and abs((deg == 3).sum() - 38) <= 3 and abs((deg == 4).sum() - 26) <= 3
+    rows = code["chk_var"].reshape(code["P"], 4)
+    assert all(len(set(r)) == 4 for r in rows)
+    pairs = set()
+    for r in rows:
+        for a, b in itertools.combinations(sorted(r), 2):
+            assert (a, b) not in pairs
+            pairs.add((a, b))
+    assert I.girth(code) >= 6
+    rng = np.random.default_rng(3)
+    c = I.encode(code, rng.integers(0, 16, size=(5, code["k"])))
+    assert (oracle.syndrome_ok(code, 5, c[None].astype(np.uint8)) == 1).all()   # the oracle's field, not the generator's

@@ -478,3 +478,42 @@ def test_single_steps_compose_to_the_decoder(oracle):
     assert np.abs(full["post"] - post).max() < 1e-12
     assert np.array_equal(full["hat"], hat)
     assert np.array_equal(full["ok"], oracle.syndrome_ok(code, K, hat))
+
+
+@pytest.mark.parametrize("q,dc,edges,n", [
+    # dc = 3: a chain of three checks; variables 2 and 4 of degree 2, the rest of degree 1
+    (4, 3, [0, 1, 2, 2, 3, 4, 4, 5, 6], 7),
+    # dc = 6: two checks sharing variable 5 (degree 2); variable 11 has no edge
+    (2, 6, [0, 1, 2, 3, 4, 5, 5, 6, 7, 8, 9, 10], 12),
+])
+def test_bp_is_exact_on_trees_of_other_degrees(oracle, q, dc, edges, n):
+    """Check degrees 3 and 6 with irregular variable degrees (0, 1 and 2) on a
+    cycle-free single-user graph: BP marginals equal the exact marginals
+    (codebook enumeration) -- the oracle's edge walk and check node for
+    degrees other than 4 and variable degrees other than 2."""
+    rng = np.random.default_rng(q * 31 + dc)
+    code = I.code_from_edges(n, q, dc, edges, rng.integers(1, q, len(edges)))
+    c = I.encode(code, rng.integers(0, q, size=(1, code["k"])))[0]
+    sigma2 = I.sigma2_from_snr(q, 3.0)
+    y = (2.0 * c - (q - 1) + rng.normal(size=n) * math.sqrt(sigma2)).astype(np.float32)
+    pe, pb, size, _ = _brute_vs_bp(oracle, code, 1, None, y, sigma2, iters=10)
+    assert size == q ** (n - len(edges) // dc)
+    assert np.abs(pe - pb).max() < 1e-10
+
+
+def test_bp_is_exact_on_cycle_free_joint_graph_dc3(oracle):
+    """Two users, one dc = 3 check each on positions 0..2, interleaved so that the
+    joint factor graph is a forest: BP = exact joint marginals."""
+    q, n = 4, 6
+    rng = np.random.default_rng(77)
+    code = I.code_from_edges(n, q, 3, [0, 1, 2], rng.integers(1, q, 3))
+    perm = np.stack([np.arange(n), (np.arange(n) + 3) % n]).astype(np.int32)
+    fr_c = I.encode(code, rng.integers(0, q, size=(2, code["k"])))
+    sigma2 = I.sigma2_from_snr(q, 4.0)
+    y = np.zeros(n)
+    for k in range(2):
+        y[perm[k]] += 2.0 * fr_c[k] - (q - 1)
+    y = (y + rng.normal(size=n) * math.sqrt(sigma2)).astype(np.float32)
+    pe, pb, size, _ = _brute_vs_bp(oracle, code, 2, perm, y, sigma2, iters=12)
+    assert size == q ** (n - 1)
+    assert np.abs(pe - pb).max() < 1e-10
