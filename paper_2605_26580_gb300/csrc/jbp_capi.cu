@@ -518,7 +518,10 @@ static std::vector<uint16_t> check_order(int K, int P, int E, const std::vector<
     std::vector<std::array<uint8_t, kDC>> col(N);
     for (int u = 0; u < N; ++u) {
         const int k = u / P, j = u % P;
-        for (int d = 0; d < kDC; ++d) col[u][d] = (uint8_t)((slot[(size_t)k * E + kDC * j + d] >> 1) & 31);
+        // bank of the edge's message: its position within the row, rotated by
+        // 16 for users 2 and 3 (pos_rot of the fused layout)
+        for (int d = 0; d < kDC; ++d)
+            col[u][d] = (uint8_t)(((slot[(size_t)k * E + kDC * j + d] >> 1) + ((k & 2) << 3)) & 31);
     }
     uint64_t x = 0x9e3779b97f4a7c15ull;
     auto rnd = [&]() {

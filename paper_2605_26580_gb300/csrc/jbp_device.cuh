@@ -1160,10 +1160,16 @@ struct PosW {
     static constexpr int W = 1;
 };
 
+// Users 2 and 3 rotate their rows' 32 positions by 16: the lane-pair shape has
+// lanes 2m and 2m+1 read users {0, 1} and {2, 3} at the same position, which
+// would otherwise fall on one bank.  Consecutive positions of a row still cover
+// all 32 banks.
+__host__ __device__ __forceinline__ int pos_rot(int k) { return (k & 2) << 3; }
+
 template <int Q>
-__device__ __forceinline__ int pos_vec(int row, int p)
+__device__ __forceinline__ int pos_vec(int row, int p, int k)
 {
-    return row * Q * kLanes + (p & (kLanes - 1)) * PosW<Q>::W;
+    return row * Q * kLanes + ((p + pos_rot(k)) & (kLanes - 1)) * PosW<Q>::W;
 }
 
 // offset of symbol a inside a position vector
@@ -1223,13 +1229,13 @@ __device__ __forceinline__ void chan_thread_pos(const Graph& g, float* msg_f, fl
     for (int k = 0; k < K; ++k) {
         const int row = (k * NB + (p >> 5)) * 2;
         float a0[Q], a1[Q];
-        sload<Q>(msg_f + pos_vec<Q>(row, p), a0);
-        sload<Q>(msg_f + pos_vec<Q>(row + 1, p), a1);
+        sload<Q>(msg_f + pos_vec<Q>(row, p, k), a0);
+        sload<Q>(msg_f + pos_vec<Q>(row + 1, p, k), a1);
 #pragma unroll
         for (int a = 0; a < Q; ++a) a0[a] *= a1[a];
         if (hat_f) {
             float b[Q];
-            sload<Q>(ch2v_f + pos_vec<Q>(k * NB + (p >> 5), p), b);
+            sload<Q>(ch2v_f + pos_vec<Q>(k * NB + (p >> 5), p, k), b);
 #pragma unroll
             for (int a = 0; a < Q; ++a) b[a] *= a0[a];
             hat_f[k * NB * 32 + p] = (uint8_t)vargmax<Q>(b);
@@ -1241,9 +1247,9 @@ __device__ __forceinline__ void chan_thread_pos(const Graph& g, float* msg_f, fl
     const GaussTerm gt = gauss_term(y, K, Q, inv_s2);
     chan_reg<K, Q>(mu, gt, g.log_fallbacks, [&](int k, const float (&o)[Q]) {
         const int row = (k * NB + (p >> 5)) * 2;
-        sstore<Q>(ch2v_f + pos_vec<Q>(k * NB + (p >> 5), p), o);
-        float* p0 = msg_f + pos_vec<Q>(row, p);
-        float* p1 = msg_f + pos_vec<Q>(row + 1, p);
+        sstore<Q>(ch2v_f + pos_vec<Q>(k * NB + (p >> 5), p, k), o);
+        float* p0 = msg_f + pos_vec<Q>(row, p, k);
+        float* p1 = msg_f + pos_vec<Q>(row + 1, p, k);
         float c0[Q], c1[Q];
         sload<Q>(p0, c0);
         sload<Q>(p1, c1);
@@ -1285,13 +1291,13 @@ __device__ __forceinline__ void chan_pair_pos(const Graph& g, float* msg_f, floa
         const int k = 2 * half + j;
         const int row = (k * NB + (p >> 5)) * 2;
         float a0[Q], a1[Q];
-        sload<Q>(msg_f + pos_vec<Q>(row, p), a0);
-        sload<Q>(msg_f + pos_vec<Q>(row + 1, p), a1);
+        sload<Q>(msg_f + pos_vec<Q>(row, p, k), a0);
+        sload<Q>(msg_f + pos_vec<Q>(row + 1, p, k), a1);
 #pragma unroll
         for (int a = 0; a < Q; ++a) a0[a] *= a1[a];
         if (hat_f) {
             float b[Q];
-            sload<Q>(ch2v_f + pos_vec<Q>(k * NB + (p >> 5), p), b);
+            sload<Q>(ch2v_f + pos_vec<Q>(k * NB + (p >> 5), p, k), b);
 #pragma unroll
             for (int a = 0; a < Q; ++a) b[a] *= a0[a];
             hat_f[k * NB * 32 + p] = (uint8_t)vargmax<Q>(b);
@@ -1311,54 +1317,47 @@ __device__ __forceinline__ void chan_pair_pos(const Graph& g, float* msg_f, floa
     const GaussTerm gt = gauss_term(y, K, Q, inv_s2);
     float H[NP];
     rcorr_g<NP, NP>(Po, H, gt);
-    float o[2][Q];
-    rcorr(mu[1], H, o[0]);   // message to user 2h
-    rcorr(mu[0], H, o[1]);   // message to user 2h+1
-    float mx[2];
-    bool bad = false;
+    // one user at a time (16 registers of output live, not 32): user 2h gets
+    // sum_b mu_{2h+1}(b) H(a+b), user 2h+1 gets sum_b mu_{2h}(b) H(a+b)
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-        mx[j] = vmax(o[j]);
-        bad = bad || !(mx[j] >= kFallbackMax);
-    }
-    // the log-space recomputation needs all four incoming messages: pair-uniform
-    const bool pair_bad = __shfl_xor_sync(mask, bad ? 1 : 0, 1) || bad;
-    if (pair_bad) {
-        float mu4[K][Q];
+        float o[Q];
+        rcorr(mu[1 - j], H, o);
+        float mx = vmax(o);
+        const bool bad = !(mx >= kFallbackMax);
+        // the log-space recomputation needs all four incoming messages: pair-uniform
+        if (__shfl_xor_sync(mask, bad ? 1 : 0, 1) || bad) {
+            float mu4[K][Q];
 #pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            const float x0 = __shfl_xor_sync(mask, mu[0][a], 1), x1 = __shfl_xor_sync(mask, mu[1][a], 1);
-            mu4[2 * half][a] = mu[0][a];
-            mu4[2 * half + 1][a] = mu[1][a];
-            mu4[2 * (1 - half)][a] = x0;
-            mu4[2 * (1 - half) + 1][a] = x1;
-        }
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-            if (!(mx[j] >= kFallbackMax)) {
-                if (g.log_fallbacks) atomicAdd(g.log_fallbacks, 1ull);
-                chan_user_log<K, Q>(mu4, 2 * half + j, gt, o[j]);
-                mx[j] = 1.0f;
+            for (int a = 0; a < Q; ++a) {
+                const float x0 = __shfl_xor_sync(mask, mu[0][a], 1), x1 = __shfl_xor_sync(mask, mu[1][a], 1);
+                mu4[2 * half][a] = mu[0][a];
+                mu4[2 * half + 1][a] = mu[1][a];
+                mu4[2 * (1 - half)][a] = x0;
+                mu4[2 * (1 - half) + 1][a] = x1;
             }
-    }
+            if (bad) {
+                if (g.log_fallbacks) atomicAdd(g.log_fallbacks, 1ull);
+                chan_user_log<K, Q>(mu4, 2 * half + j, gt, o);
+                mx = 1.0f;
+            }
+        }
+        const float inv = __frcp_rn(mx);
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const float inv = __frcp_rn(mx[j]);
-#pragma unroll
-        for (int a = 0; a < Q; ++a) o[j][a] = fmaxf(o[j][a] * inv, kRelFloor);
+        for (int a = 0; a < Q; ++a) o[a] = fmaxf(o[a] * inv, kRelFloor);
         const int k = 2 * half + j;
         const int row = (k * NB + (p >> 5)) * 2;
-        sstore<Q>(ch2v_f + pos_vec<Q>(k * NB + (p >> 5), p), o[j]);
-        float* p0 = msg_f + pos_vec<Q>(row, p);
-        float* p1 = msg_f + pos_vec<Q>(row + 1, p);
+        sstore<Q>(ch2v_f + pos_vec<Q>(k * NB + (p >> 5), p, k), o);
+        float* p0 = msg_f + pos_vec<Q>(row, p, k);
+        float* p1 = msg_f + pos_vec<Q>(row + 1, p, k);
         float c0[Q], c1[Q];
         sload<Q>(p0, c0);
         sload<Q>(p1, c1);
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
             const float t = c0[a];
-            c0[a] = o[j][a] * c1[a];
-            c1[a] = o[j][a] * t;
+            c0[a] = o[a] * c1[a];
+            c1[a] = o[a] * t;
         }
         const float i0 = __frcp_rn(vmax(c0)), i1 = __frcp_rn(vmax(c1));
 #pragma unroll
@@ -1402,7 +1401,7 @@ __device__ __forceinline__ CheckRec check_rec(const Graph& g, int NB, int k, int
 #pragma unroll
     for (int d = 0; d < kDC; ++d) {
         const int e = 4 * j + d, sl = g.slot[k * g.E + e], pp = sl >> 1, h = g.chk_coef[e];
-        o[d] = (unsigned)(pos_vec<Q>((k * NB + (pp >> 5)) * 2 + (sl & 1), pp)) | ((unsigned)h << 24);
+        o[d] = (unsigned)(pos_vec<Q>((k * NB + (pp >> 5)) * 2 + (sl & 1), pp, k)) | ((unsigned)h << 24);
         unsigned bb = 0;
         for (int t = 0; (1 << t) < Q; ++t) bb |= (unsigned)g.gf_div[h * Q + (1 << t)] << (4 * t);
         b[d] = bb;
@@ -1416,12 +1415,14 @@ __device__ __forceinline__ CheckRec check_rec(const Graph& g, int NB, int k, int
 __device__ __forceinline__ int rec_coef(unsigned o) { return (int)(o >> 24); }
 
 // position-order index of the edge's variable in the frame's decisions
-// (k*NB*32 + position): its message row is (k*NB + position/32)*2 + slot
+// (k*NB*32 + position): its message row is (k*NB + position/32)*2 + slot, and
+// its position within the row is rotated by pos_rot(k)
 template <int Q>
-__device__ __forceinline__ int rec_hat(unsigned o)
+__device__ __forceinline__ int rec_hat(unsigned o, int NB)
 {
     const unsigned v = o & 0xFFFFFFu, row = v / (Q * kLanes);
-    return (int)(((row >> 1) << 5) | (v & (kLanes - 1)));
+    const int k = (int)(row >> 1) / NB;
+    return (int)(((row >> 1) << 5) | ((v - pos_rot(k)) & (kLanes - 1)));
 }
 
 template <int Q>
@@ -1481,9 +1482,9 @@ __device__ __forceinline__ int var_thread_pos(const float* msg_f, const float* c
 {
     float b[Q], c0[Q], c1[Q];
     const int row = k * NB + (p >> 5);
-    sload<Q>(ch2v_f + pos_vec<Q>(row, p), b);
-    sload<Q>(msg_f + pos_vec<Q>(2 * row, p), c0);
-    sload<Q>(msg_f + pos_vec<Q>(2 * row + 1, p), c1);
+    sload<Q>(ch2v_f + pos_vec<Q>(row, p, k), b);
+    sload<Q>(msg_f + pos_vec<Q>(2 * row, p, k), c0);
+    sload<Q>(msg_f + pos_vec<Q>(2 * row + 1, p, k), c1);
 #pragma unroll
     for (int a = 0; a < Q; ++a) b[a] *= c0[a] * c1[a];
     const int bi = vargmax<Q>(b);

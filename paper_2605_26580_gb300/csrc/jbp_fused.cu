@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
             const unsigned o[kDC] = {r.x, r.y, r.z, r.w};
             int sy = 0;
 #pragma unroll
-            for (int d = 0; d < kDC; ++d) sy ^= s_mul[rec_coef(o[d]) * Q + hf[rec_hat<Q>(o[d])]];
+            for (int d = 0; d < kDC; ++d) sy ^= s_mul[rec_coef(o[d]) * Q + hf[rec_hat<Q>(o[d], NB)]];
             if (sy) s_unsat[gi * K + rec_user<Q>(o[0], NB)] = 1;
         };
         // per-frame stop after iteration t (syndromes already recorded); returns the frames still active
