@@ -251,7 +251,13 @@ int jbp_tune(jbp_h *h, const jbp_batch *batch, int32_t *threads, int32_t *frames
  * app_ldpc_v2c, app_ldpc_c2v, app_ldpc_marginal, app_ldpc_check_eq with early
  * exit); the paper has no serving counterpart: requests of any decoder of the
  * context are admitted into resident device pools as slots and memory free
- * up and re-batched every block of iterations.  Thread-safe.  Errors:
+ * up and re-batched every block of iterations.  A decoder that the fused
+ * position-major kernel serves (q <= 16, K <= 4, every variable of degree 2,
+ * FP32 check, trellis channel node) keeps its pool in that kernel's layout and
+ * runs each block as one launch of it (a slot's state goes to shared memory and
+ * back to HBM once per block): its served frames equal jbp_decode's fused form
+ * bit for bit.  Other decoders' pools run the step form and equal its results
+ * (under AUTO with the DFT node, see jbp_channel_node).  Thread-safe.  Errors:
  * JBP_EINVAL (NULL pointer, sigma2 not finite), JBP_ECLOSED (the context is
  * shutting down).  The queue is unbounded: a request waits on the host until a
  * pool slot frees up. */

@@ -172,6 +172,11 @@ struct ServePool {
     std::vector<Request> req;      // [cap] the request each used slot holds
     std::vector<uint8_t> used;     // [cap]
     std::vector<int> free_list;
+    // fused pool: slots keep the fused kernel's position-major state, and a
+    // block is one launch of that kernel (launch_fused_pool)
+    bool fused = false;
+    FusedPlan fplan{};
+    size_t fmsg = 0, fch2v = 0;    // floats of a slot's messages and channel messages
 };
 
 }  // namespace
@@ -1251,10 +1256,20 @@ extern "C" int jbp_step_syndrome(jbp_h* h, int32_t F, const uint8_t* hat, uint8_
 static constexpr int kPoolMinCap = 32;
 static constexpr int kPoolMaxCap = 1024;
 
-// device bytes of one frame slot of a pool
+// device bytes of one frame slot of a pool (the larger of the step form's state
+// and the fused form's, whose rows are padded to 32 positions)
 static int64_t pool_frame_bytes(const jbp_h* h)
 {
-    return state_bytes(h->graph()) + 8ll * h->n + 24 + 3ll * h->K + (int64_t)h->K * h->n;
+    const int64_t nb32 = (h->n + 31) / 32 * 32;
+    const int64_t state = std::max<int64_t>(state_bytes(h->graph()), 12ll * h->K * nb32 * h->Q);
+    return state + 8ll * h->n + 24 + 3ll * h->K + (int64_t)h->K * h->n;
+}
+
+// A decoder whose frames the fused position-major kernel runs (FP32 check, the
+// trellis channel node) keeps its serving pool in that kernel's layout.
+static bool pool_wants_fused(const jbp_ctx* ctx, const jbp_h* h)
+{
+    return h->fused_ok && ctx->opt.precision == JBP_PREC_FP32 && !h->d_dft_tab;
 }
 
 static PoolState pool_state(const ServePool& p)
@@ -1263,7 +1278,7 @@ static PoolState pool_state(const ServePool& p)
     PoolState st;
     st.n = h->n;
     st.K = h->K;
-    st.msg_floats = (long long)h->K * h->E * h->Q;
+    st.msg_floats = p.fused ? (long long)p.fmsg : (long long)h->K * h->E * h->Q;
     st.msg = P<float>(p.msg);
     st.y = P<float>(p.y);
     st.sig = P<float>(p.sig);
@@ -1308,11 +1323,16 @@ static int pool_create(jbp_ctx* ctx, jbp_h* h, int cap, ServePool** out)
     p->h = h;
     p->cap = cap;
     const size_t F = (size_t)cap, K = h->K, n = h->n, E = h->E, Q = h->Q;
+    if (pool_wants_fused(ctx, h)) {
+        p->fused = fused_pool_plan(h->graph(), ctx->di, cap, K == 4 ? 512 : 0, &p->fplan, &p->fmsg, &p->fch2v);
+        cudaGetLastError();
+    }
+    const size_t msg_floats = p->fused ? p->fmsg : K * E * Q, ch2v_floats = p->fused ? p->fch2v : K * n * Q;
     bool g = false;
     const int64_t before = ctx->used.load();
     int rc;
-    if ((rc = buf_ensure(ctx, p->msg, sizeof(float) * F * K * E * Q, &g)) ||
-        (rc = buf_ensure(ctx, p->ch2v, sizeof(float) * F * K * n * Q, &g)) ||
+    if ((rc = buf_ensure(ctx, p->msg, sizeof(float) * F * msg_floats, &g)) ||
+        (rc = buf_ensure(ctx, p->ch2v, sizeof(float) * F * ch2v_floats, &g)) ||
         (rc = buf_ensure(ctx, p->y, sizeof(float) * F * n, &g)) || (rc = buf_ensure(ctx, p->sig, sizeof(float) * F, &g)) ||
         (rc = buf_ensure(ctx, p->active, F, &g)) || (rc = buf_ensure(ctx, p->t, sizeof(int32_t) * F, &g)) ||
         (rc = buf_ensure(ctx, p->unsat, F * K, &g)) || (rc = buf_ensure(ctx, p->ok, F * K, &g)) ||
@@ -1476,7 +1496,20 @@ static int pool_launch(jbp_ctx* ctx, ServePool& p, std::vector<Request>& take)
     float* msg = P<float>(p.msg);
     float* ch2v = P<float>(p.ch2v);
     const uint8_t* act = P<uint8_t>(p.active);
-    for (int it = 0; it < ctx->opt.block_iters; ++it) {
+    if (p.fused) {
+        // one launch runs the block: every active slot up to block_iters more
+        // iterations in shared memory, its state back to HBM unless it finished
+        FusedPool fp;
+        fp.msg = msg;
+        fp.ch2v = ch2v;
+        fp.active = P<uint8_t>(p.active);
+        fp.fin = P<uint8_t>(p.fin);
+        fp.block = ctx->opt.block_iters;
+        JBP_CU(launch_fused_pool(g, p.fplan, F, P<float>(p.y), ctx->opt.iters, ctx->opt.early_stop,
+                                 P<uint8_t>(p.hat), P<int32_t>(p.t), P<uint8_t>(p.ok), fp, s),
+               "pool fused block");
+    }
+    for (int it = 0; it < (p.fused ? 0 : ctx->opt.block_iters); ++it) {
         JBP_CU(launch_channel(g, di, F, P<float>(p.y), msg, ch2v, act, s), "pool channel");
         JBP_CU(launch_check(g, di, F, msg, act, ctx->opt.precision, s), "pool check");
         JBP_CU(launch_var(g, di, F, ch2v, msg, nullptr, P<uint8_t>(p.hat), act, s), "pool var");

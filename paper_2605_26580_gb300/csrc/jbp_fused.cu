@@ -223,10 +223,14 @@ __host__ __device__ inline PosLayout pos_layout(const Graph& g, int G)
 template <int Q, int KC, bool PAIR>
 constexpr int pos_max_threads() { return PAIR ? 512 : kFusedMaxThreads; }
 
-template <int Q, int KC, bool PAIR = false>
+// POOL: serving-pool mode (FusedPool): G = 1, frame f0 is pool
+// slot f0, iterations t0 + 1 .. min(t0 + pool.block, T_it) with t0 = iters[f0],
+// state loaded from and stored to the pool, the unfolded phase order.
+template <int Q, int KC, bool PAIR = false, bool POOL = false>
 __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Graph g, int F, int G, const float* __restrict__ y,
                                                                 int T_it, int early_stop, uint8_t* hat,
-                                                                int32_t* iters, uint8_t* ok, float* logpost)
+                                                                int32_t* iters, uint8_t* ok, float* logpost,
+                                                                FusedPool pool)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     const PosLayout lay = pos_layout(g, G);
@@ -252,10 +256,35 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
         s_recb[i] = r.basis;
     }
 
+    constexpr bool in_pool = POOL;
+    // a pool slot's state between shared memory and HBM (16-byte words)
+    auto pool_state = [&](int f, bool load) {
+        float4* gm = reinterpret_cast<float4*>(pool.msg + (size_t)f * fs);
+        float4* gv = reinterpret_cast<float4*>(pool.ch2v + (size_t)f * vs);
+        float4* sm4 = reinterpret_cast<float4*>(s_msg);
+        float4* sv4 = reinterpret_cast<float4*>(s_ch2v);
+        for (size_t i = threadIdx.x; i < fs / 4; i += blockDim.x) {
+            if (load) sm4[i] = gm[i];
+            else gm[i] = sm4[i];
+        }
+        for (size_t i = threadIdx.x; i < vs / 4; i += blockDim.x) {
+            if (load) sv4[i] = gv[i];
+            else gv[i] = sv4[i];
+        }
+    };
+
     const int groups = (F + G - 1) / G;
     for (int grp = blockIdx.x; grp < groups; grp += gridDim.x) {
         const int f0 = grp * G, gc = min(G, F - f0);
-        for (size_t i = threadIdx.x; i < (size_t)gc * fs; i += blockDim.x) s_msg[i] = 1.0f;
+        int t0 = 0, t_end = T_it;
+        if constexpr (POOL) {
+            if (!pool.active[f0]) continue;   // uniform across the CTA
+            t0 = iters[f0];
+            t_end = min(T_it, t0 + pool.block);
+        }
+        if (POOL && t0 > 0) pool_state(f0, true);
+        else
+            for (size_t i = threadIdx.x; i < (size_t)gc * fs; i += blockDim.x) s_msg[i] = 1.0f;
         for (int i = threadIdx.x; i < gc * n; i += blockDim.x) s_y[(i / n) * NB * 32 + i % n] = y[(size_t)f0 * n + i];
         for (int i = threadIdx.x; i < gc * K; i += blockDim.x) s_unsat[i] = 0;
         for (int i = threadIdx.x; i < G; i += blockDim.x) s_active[i] = i < gc ? 1 : 0;
@@ -266,7 +295,7 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
         // messages), and its syndromes and stop test run between that channel
         // phase and the next check phase; a final pass decides after the last
         // iteration.
-        const bool fold = logpost == nullptr;
+        const bool fold = logpost == nullptr && !in_pool;
         auto phase_decide = [&]() {
             for (int unit = threadIdx.x; unit < gc * K * n; unit += blockDim.x) {
                 const int gi = unit / (K * n), rem = unit % (K * n), k = rem / n, p = rem % n;
@@ -315,7 +344,7 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
             return phase_finish(t);
         };
         bool all_stopped = false;
-        for (int t = 1; t <= T_it; ++t) {
+        for (int t = t0 + 1; t <= t_end; ++t) {
             // (A) channel nodes, v2c in place (and, folded, the decisions of iteration t - 1)
             const bool dec = fold && t > 1;
             if constexpr (PAIR && K == 4) {
@@ -367,6 +396,16 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
             __syncthreads();
             phase_stop(T_it);
         }
+        if (POOL && !all_stopped && t_end < T_it) {
+            // the slot goes on in a later block: keep its state
+            pool_state(f0, false);
+            __syncthreads();
+            continue;
+        }
+        if (POOL && threadIdx.x == 0) {
+            pool.active[f0] = 0;
+            pool.fin[f0] = 1;
+        }
         // decisions back to variable order
         for (int w = threadIdx.x; w < gc * K * n; w += blockDim.x) {
             const int gi = w / (K * n), rem = w % (K * n), k = rem / n, i = rem % n;
@@ -417,24 +456,35 @@ bool plan_pos(const Graph& g, const DeviceInfo& di, int F, int threads_hint, int
 
 template <int Q, int KC, bool PAIR>
 cudaError_t fused_pos_v(const Graph& g, const FusedPlan& p, int F, const float* y, int T_it, int early_stop,
-                        uint8_t* hat, int32_t* iters, uint8_t* ok, float* post, cudaStream_t s)
+                        uint8_t* hat, int32_t* iters, uint8_t* ok, float* post, cudaStream_t s,
+                        const FusedPool& pool = FusedPool())
 {
+    if (pool.msg) {
+        cudaError_t e = cudaFuncSetAttribute(k_fused_pos<Q, KC, PAIR, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem_bytes);
+        if (e != cudaSuccess) return e;
+        k_fused_pos<Q, KC, PAIR, true><<<p.grid, p.threads, p.smem_bytes, s>>>(g, F, 1, y, T_it, early_stop, hat,
+                                                                                iters, ok, nullptr, pool);
+        return cudaGetLastError();
+    }
     cudaError_t e =
         cudaFuncSetAttribute(k_fused_pos<Q, KC, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem_bytes);
     if (e != cudaSuccess) return e;
     k_fused_pos<Q, KC, PAIR><<<p.grid, p.threads, p.smem_bytes, s>>>(g, F, p.frames_per_cta, y, T_it, early_stop,
-                                                                      hat, iters, ok, post);
+                                                                      hat, iters, ok, post, pool);
     return cudaGetLastError();
 }
 
 template <int Q, int KC>
 cudaError_t fused_pos(const Graph& g, const FusedPlan& p, int F, const float* y, int T_it, int early_stop,
-                      uint8_t* hat, int32_t* iters, uint8_t* ok, float* post, cudaStream_t s)
+                      uint8_t* hat, int32_t* iters, uint8_t* ok, float* post, cudaStream_t s,
+                      const FusedPool& pool = FusedPool())
 {
     if constexpr (KC == 4) {
-        if (p.variant == 1) return fused_pos_v<Q, KC, true>(g, p, F, y, T_it, early_stop, hat, iters, ok, post, s);
+        if (p.variant == 1)
+            return fused_pos_v<Q, KC, true>(g, p, F, y, T_it, early_stop, hat, iters, ok, post, s, pool);
     }
-    return fused_pos_v<Q, KC, false>(g, p, F, y, T_it, early_stop, hat, iters, ok, post, s);
+    return fused_pos_v<Q, KC, false>(g, p, F, y, T_it, early_stop, hat, iters, ok, post, s, pool);
 }
 
 template <int Q, int KC>
@@ -533,6 +583,49 @@ cudaError_t launch_fused(const Graph& g, const FusedPlan& plan, int F, const flo
 {
     if (F <= 0) return cudaSuccess;
     JBP_FUSED_DISPATCH(fused_pos, fused_qk, g, plan, F, y, T_it, early_stop, hat, iters, ok, post, s);
+    return cudaErrorInvalidValue;
+}
+
+#define JBP_POS_DISPATCH(FN, ...)                                                    \
+    switch (g.Q * 8 + fused_kc(g)) {                                                 \
+        case 2 * 8 + 1: return FN<2, 1>(__VA_ARGS__);                                \
+        case 2 * 8 + 2: return FN<2, 2>(__VA_ARGS__);                                \
+        case 2 * 8 + 3: return FN<2, 3>(__VA_ARGS__);                                \
+        case 2 * 8 + 4: return FN<2, 4>(__VA_ARGS__);                                \
+        case 4 * 8 + 1: return FN<4, 1>(__VA_ARGS__);                                \
+        case 4 * 8 + 2: return FN<4, 2>(__VA_ARGS__);                                \
+        case 4 * 8 + 3: return FN<4, 3>(__VA_ARGS__);                                \
+        case 4 * 8 + 4: return FN<4, 4>(__VA_ARGS__);                                \
+        case 8 * 8 + 1: return FN<8, 1>(__VA_ARGS__);                                \
+        case 8 * 8 + 2: return FN<8, 2>(__VA_ARGS__);                                \
+        case 8 * 8 + 3: return FN<8, 3>(__VA_ARGS__);                                \
+        case 8 * 8 + 4: return FN<8, 4>(__VA_ARGS__);                                \
+        case 16 * 8 + 1: return FN<16, 1>(__VA_ARGS__);                              \
+        case 16 * 8 + 2: return FN<16, 2>(__VA_ARGS__);                              \
+        case 16 * 8 + 3: return FN<16, 3>(__VA_ARGS__);                              \
+        case 16 * 8 + 4: return FN<16, 4>(__VA_ARGS__);                              \
+        default: break;                                                              \
+    }
+
+bool fused_pool_plan(const Graph& g, const DeviceInfo& di, int cap, int threads_hint, FusedPlan* plan,
+                     size_t* msg_floats, size_t* ch2v_floats)
+{
+    if (g.dc != kDC || cap <= 0 || fused_kc(g) == 0) return false;
+    const size_t NB = (size_t)(g.n + 31) / 32;
+    *msg_floats = (size_t)g.K * NB * 2 * g.Q * 32;
+    *ch2v_floats = (size_t)g.K * NB * g.Q * 32;
+    JBP_POS_DISPATCH(plan_pos, g, di, cap, threads_hint, 1, plan);
+    return false;
+}
+
+cudaError_t launch_fused_pool(const Graph& g, const FusedPlan& plan, int F, const float* y, int T, int early_stop,
+                              uint8_t* hat, int32_t* t, uint8_t* ok, const FusedPool& pool, cudaStream_t s)
+{
+    if (F <= 0) return cudaSuccess;
+    if (plan.frames_per_cta != 1 || !pool.msg || pool.block < 1) return cudaErrorInvalidValue;
+    FusedPlan p = plan;
+    p.grid = std::min(plan.grid, F);
+    JBP_POS_DISPATCH(fused_pos, g, p, F, y, T, early_stop, hat, t, ok, nullptr, s, pool);
     return cudaErrorInvalidValue;
 }
 

@@ -141,6 +141,26 @@ cudaError_t launch_fused(const Graph& g, const FusedPlan& plan, int F, const flo
                          int early_stop, uint8_t* hat, int32_t* iters, uint8_t* ok, float* post,
                          cudaStream_t s);
 
+// A serving pool run by the fused position-major kernel: slot f's message state
+// (msg_floats + ch2v_floats floats, in the kernel's shared-memory layout) stays
+// in HBM between blocks; a launch runs up to `block` more iterations of every
+// active slot (one slot per CTA), loading its state into shared memory and
+// storing it back, and stops a slot at its early stop or at T (active = 0,
+// fin = 1, its decisions in hat).  t [F]: iterations run, updated.
+struct FusedPool {
+    float* msg = nullptr;    // [F][msg_floats]
+    float* ch2v = nullptr;   // [F][ch2v_floats]
+    uint8_t* active = nullptr;
+    uint8_t* fin = nullptr;
+    int block = 0;
+};
+// The fused pool's plan (one frame per CTA) and per-slot state sizes; false if
+// the position-major kernel does not serve this graph.
+bool fused_pool_plan(const Graph& g, const DeviceInfo& di, int cap, int threads_hint, FusedPlan* plan,
+                     size_t* msg_floats, size_t* ch2v_floats);
+cudaError_t launch_fused_pool(const Graph& g, const FusedPlan& plan, int F, const float* y, int T, int early_stop,
+                              uint8_t* hat, int32_t* t, uint8_t* ok, const FusedPool& pool, cudaStream_t s);
+
 // Evidence-interface path (jbp_ura.cu): slot-wise AMP detector and SIC row
 // decoder.  Device tables and scalars of one (code, detector) pair.
 struct UraDev {

@@ -396,8 +396,10 @@ def test_decode_many_graph_replay_matches_single_decodes(env):
 def test_serving_results_are_the_same_alone_and_in_the_mix(env):
     """Requests of two decoders submitted interleaved (resident pools re-batched
     every block of iterations, the two pools' blocks overlapping) give, frame by
-    frame, exactly the result of decoding that frame alone in the step form;
-    unknown or consumed tickets poll JBP_ECLOSED."""
+    frame, exactly the result of decoding that frame alone in the form its pool
+    runs -- the fused form here (GF(q <= 16), K <= 4, variable degree 2: the pool
+    keeps each slot's state in the fused kernel's layout); unknown or consumed
+    tickets poll JBP_ECLOSED."""
     jbp, O, torch = env
     ctx = jbp.Context(iters=10, early_stop=True)
     specs = [(64, 4, 2, 11.0, 24), (128, 16, 3, 13.0, 16)]
@@ -409,7 +411,7 @@ def test_serving_results_are_the_same_alone_and_in_the_mix(env):
             decs.append(jbp.Decoder(ctx, code, K, fr["sigma2"], fr["perm"]))
             frames.append(fr)
         sig = [np.full(fr["y"].shape[0], np.float32(fr["sigma2"]), np.float32) for fr in frames]
-        alone = [[d.decode(fr["y"][i:i + 1], form=jbp.FORM_STEP, sigma2=s[i:i + 1]) for i in range(fr["y"].shape[0])]
+        alone = [[d.decode(fr["y"][i:i + 1], form=jbp.FORM_FUSED, sigma2=s[i:i + 1]) for i in range(fr["y"].shape[0])]
                  for d, fr, s in zip(decs, frames, sig)]
         tickets = []
         for i in range(max(fr["y"].shape[0] for fr in frames)):
@@ -442,8 +444,9 @@ def test_serving_results_are_the_same_alone_and_in_the_mix(env):
 def test_serving_admits_frames_between_blocks(env):
     """Frames submitted while earlier frames of the same decoder are part-way
     through their iterations join the resident pool at the next block boundary;
-    every result equals the frame decoded alone (step form), and the iteration
-    counts show the early frames were not restarted."""
+    every result equals the frame decoded alone (fused form, which the pool of
+    this decoder runs, its slots' state stored between blocks of 2 iterations),
+    and the iteration counts show the early frames were not restarted."""
     import time
     jbp, O, torch = env
     ctx = jbp.Context(iters=30, early_stop=False, block_iters=2)
@@ -451,7 +454,7 @@ def test_serving_admits_frames_between_blocks(env):
     fr = I.make_frames(code, 4, 10.0, 48, seed=1234)
     dec = jbp.Decoder(ctx, code, 4, fr["sigma2"], fr["perm"])
     try:
-        alone = [dec.decode(fr["y"][i:i + 1], form=jbp.FORM_STEP) for i in range(48)]
+        alone = [dec.decode(fr["y"][i:i + 1], form=jbp.FORM_FUSED) for i in range(48)]
         first = [dec.submit(fr["y"][i]) for i in range(16)]
         time.sleep(0.002)
         second = [dec.submit(fr["y"][i]) for i in range(16, 48)]
@@ -504,7 +507,7 @@ def test_serving_destroy_with_frames_in_flight(env):
     dec_a = jbp.Decoder(ctx, code_a, 6, fr_a["sigma2"], fr_a["perm"])
     dec_b = jbp.Decoder(ctx, code_b, 2, fr_b["sigma2"], fr_b["perm"])
     try:
-        alone_b = [dec_b.decode(fr_b["y"][i:i + 1], form=jbp.FORM_STEP) for i in range(8)]
+        alone_b = [dec_b.decode(fr_b["y"][i:i + 1], form=jbp.FORM_FUSED) for i in range(8)]   # its pool's form
         ta = [dec_a.submit(fr_a["y"][i]) for i in range(64)]
         tb = [dec_b.submit(fr_b["y"][i]) for i in range(8)]
         dec_a.close()
@@ -660,3 +663,28 @@ def test_fused_many_groups_equal_small_batches(env, K, q, n, fpc):
         ctx.close()
     for key in ("hat", "iters", "ok"):
         assert np.array_equal(big[key], np.concatenate([s[key] for s in small])), key
+
+
+def test_serving_step_form_pools_match_frames_decoded_alone(env):
+    """Decoders outside the fused position-major form (variable degree 3 here)
+    keep step-form pools: each served frame equals the frame decoded alone in
+    the step form, early-stopping frames included."""
+    import time
+    jbp, O, torch = env
+    ctx = jbp.Context(iters=12, early_stop=True, block_iters=3)
+    code = I.make_code(64, 16, dv=3, dc=4)
+    fr = I.make_frames(code, 2, 14.0, 20, seed=3141)
+    dec = jbp.Decoder(ctx, code, 2, fr["sigma2"], fr["perm"])
+    try:
+        alone = [dec.decode(fr["y"][i:i + 1], form=jbp.FORM_STEP) for i in range(20)]
+        tickets = [dec.submit(fr["y"][i]) for i in range(20)]
+        for i, tk in enumerate(tickets):
+            deadline = time.time() + 60.0
+            while (res := ctx.poll(tk, 64, 2)) is None:
+                assert time.time() < deadline
+                time.sleep(1e-4)
+            assert np.array_equal(res["hat"], alone[i]["hat"][0]), i
+            assert res["iters"] == int(alone[i]["iters"][0]) and np.array_equal(res["ok"], alone[i]["ok"][0])
+    finally:
+        dec.close()
+        ctx.close()
