@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_channel_dft(Graph g, int F, 
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int ii = kg * 8 + i, uu = u_lo + ii;
-                e[i] = live ? (uu < U ? __expf(gt.expo(uu)) : 0.0f) : (ii == 0 ? 1.0f : 0.0f);
+                e[i] = live ? (uu < U ? gt.score(uu) : 0.0f) : (ii == 0 ? 1.0f : 0.0f);
             }
             *reinterpret_cast<uint4*>(AG + tc::tile_off(m, kg, W)) = pack8(e);
         }

@@ -218,17 +218,35 @@ __device__ __forceinline__ int vargmax(const float (&v)[N])
 // d = s* - s, -(y - L_s)^2/(2 sigma2) + (y - L_s*)^2/(2 sigma2) = -2 d (r + d)/sigma2,
 // which keeps its relative accuracy for every entry that matters.
 
+// 2^x by the special-function unit's approximation (PTX ex2.approx.ftz.f32;
+// relative error about 2^-22, results below 2^-126 flushed to zero)
+__device__ __forceinline__ float exp2_approx(float x)
+{
+    float e;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(x));
+    return e;
+}
+
 struct GaussTerm {
     int ss;          // nearest symbol sum s*
     float ssf;       // s* as a float (exact: a small integer)
     float r;         // y - (2 s* - K(q-1))
     float inv_s2;    // 1 / sigma2
+    float k2;        // -2 log2(e) / sigma2
+    // the exponent (natural log) of the score of sum value s
     __device__ __forceinline__ float expo(int s) const
     {
         // d = s* - s is exact in FP32 (small integers), so subtracting floats
         // gives the value an integer subtraction and conversion would
         const float d = ssf - (float)s;
         return -2.0f * d * (r + d) * inv_s2;
+    }
+    // the score itself, exp(expo(s)) = 2^(k2 d (r + d)): two additions, two
+    // products and one base-2 exponential
+    __device__ __forceinline__ float score(int s) const
+    {
+        const float d = ssf - (float)s;
+        return exp2_approx((d * k2) * (r + d));
     }
 };
 
@@ -242,6 +260,7 @@ __device__ __forceinline__ GaussTerm gauss_term(float y, int K, int Q, float inv
     t.ssf = sf;
     t.r = y - (float)(2 * t.ss - KD);
     t.inv_s2 = inv_s2;
+    t.k2 = -2.0f * 1.4426950408889634f * inv_s2;
     return t;
 }
 
@@ -290,7 +309,7 @@ __device__ __forceinline__ void rcorr_g2(const float (&P1)[NP1], float (&H1)[NH1
     for (int v = 0; v < NH2; ++v) H2[v] = 0.0f;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-        const float g = __expf(gt.expo(w));
+        const float g = gt.score(w);
 #pragma unroll
         for (int v = 0; v < NH1; ++v)
             if (w - v >= 0 && w - v < NP1) H1[v] = fmaf(P1[w - v], g, H1[v]);
@@ -307,7 +326,7 @@ __device__ __forceinline__ void rcorr_g(const float (&P)[NP], float (&H)[NH], co
     for (int v = 0; v < NH; ++v) H[v] = 0.0f;
 #pragma unroll
     for (int w = 0; w < NH + NP - 1; ++w) {
-        const float g = __expf(gt.expo(w));
+        const float g = gt.score(w);
 #pragma unroll
         for (int v = 0; v < NH; ++v)
             if (w - v >= 0 && w - v < NP) H[v] = fmaf(P[w - v], g, H[v]);
@@ -388,7 +407,7 @@ __device__ __forceinline__ void chan_reg(const float (&mu)[K][Q], const GaussTer
     if constexpr (K == 1) {
         float o[Q];
 #pragma unroll
-        for (int a = 0; a < Q; ++a) o[a] = __expf(gt.expo(a));
+        for (int a = 0; a < Q; ++a) o[a] = gt.score(a);
         chan_finish<K, Q>(mu, 0, gt, o, fb);
         emit(0, o);
     } else if constexpr (K == 2) {
@@ -576,7 +595,7 @@ __device__ bool chan_trellis(const Graph& g, const float* msg_f, size_t ustride,
     }
 
     const GaussTerm gt = gauss_term(y, K, Q, inv_s2);
-    for (int s = L.tl; s <= S; s += T) B[s] = SR::kLog ? gt.expo(s) : __expf(gt.expo(s));
+    for (int s = L.tl; s <= S; s += T) B[s] = SR::kLog ? gt.expo(s) : gt.score(s);
 
     for (int j = 1; j + 1 < K; ++j) {
         __syncwarp(L.mask);
@@ -820,7 +839,7 @@ __device__ bool chan_blocked(const Graph& g, const float* msg_f, size_t ustride,
         }
     }
     const GaussTerm gt = gauss_term(y, K, Q, inv_s2);
-    for (int s = Lr.tl; s <= S; s += T) B[s] = __expf(gt.expo(s));
+    for (int s = Lr.tl; s <= S; s += T) B[s] = gt.score(s);
     __syncwarp(Lr.mask);
     for (int j = 1; j + 1 < K; ++j) {
         const float m = team_corr<T, true, CorrBlock<Q>::BR>(Fb + blk_prefix_offset(j + 1, Q) + PL, (j + 1) * D + 1, mu + j * Q, Q,
