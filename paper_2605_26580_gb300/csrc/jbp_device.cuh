@@ -233,6 +233,7 @@ struct GaussTerm {
     float r;         // y - (2 s* - K(q-1))
     float inv_s2;    // 1 / sigma2
     float k2;        // -2 log2(e) / sigma2
+    float k2r;       // k2 r
     // the exponent (natural log) of the score of sum value s
     __device__ __forceinline__ float expo(int s) const
     {
@@ -241,12 +242,12 @@ struct GaussTerm {
         const float d = ssf - (float)s;
         return -2.0f * d * (r + d) * inv_s2;
     }
-    // the score itself, exp(expo(s)) = 2^(k2 d (r + d)): two additions, two
-    // products and one base-2 exponential
+    // the score itself, exp(expo(s)) = 2^(d (k2 d + k2 r)): one addition, one
+    // multiply-add, one product and one base-2 exponential
     __device__ __forceinline__ float score(int s) const
     {
         const float d = ssf - (float)s;
-        return exp2_approx((d * k2) * (r + d));
+        return exp2_approx(d * fmaf(k2, d, k2r));
     }
 };
 
@@ -261,6 +262,7 @@ __device__ __forceinline__ GaussTerm gauss_term(float y, int K, int Q, float inv
     t.r = y - (float)(2 * t.ss - KD);
     t.inv_s2 = inv_s2;
     t.k2 = -2.0f * 1.4426950408889634f * inv_s2;
+    t.k2r = t.k2 * t.r;
     return t;
 }
 

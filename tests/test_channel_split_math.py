@@ -9,7 +9,7 @@ without division by splitting the users into two halves (reading R11):
   * K = 4: P_23 = mu_2 (*) mu_3, H_23(v) = sum_s P_23(s) G(v + s), users 0 and 1
     correlate mu_1 and mu_0 with H_23; users 2 and 3 use P_01 and H_01.
 G(u) is the Gaussian score of the sum value u, computed relative to the nearest
-symbol sum s* (reading R10): exp(-2 d (r + d) / sigma2) = 2^((d k2) (r + d)) with
+symbol sum s* (reading R10): exp(-2 d (r + d) / sigma2) = 2^(d (k2 d + k2 r)) with
 d = s* - u, r = y - (2 s* - K(q-1)) and k2 = -2 log2(e) / sigma2, which differs from exp(-(y - (2u - K(q-1)))^2 / (2 sigma2))
 only by the factor exp(-r^2 / (2 sigma2)) common to every u.
 Run in FP64 this must equal the oracle's trellis to rounding; run in FP32 (the
@@ -31,13 +31,16 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def gauss(K, q, sigma2, y, dt):
-    """G(u) as the kernels form it: 2^((d k2) (r + d)) with k2 = -2 log2(e) / sigma2."""
+    """G(u) as the kernels form it: 2^(d (k2 d + k2 r)) with k2 = -2 log2(e) / sigma2,
+    the inner sum one fused multiply-add (emulated: the FP32 product is exact in FP64)."""
     KD = K * (q - 1)
     ss = int(min(max(np.rint((y + KD) * 0.5), 0), KD))
     r = dt(y - (2 * ss - KD))
     d = (ss - np.arange(KD + 1)).astype(dt)
     k2 = dt(dt(-2.0 * math.log2(math.e)) * dt(1.0 / sigma2))
-    return np.exp2(((d * k2).astype(dt) * (r + d)).astype(dt)).astype(dt)
+    k2r = dt(k2 * r)
+    t = (k2.astype(np.float64) * d.astype(np.float64) + np.float64(k2r)).astype(dt)
+    return np.exp2((d * t).astype(dt)).astype(dt)
 
 
 def corr(P, X, nh, dt):

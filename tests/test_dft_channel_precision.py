@@ -2,7 +2,7 @@
 
 `test_dft_channel_math.py` shows that the DFT formulation equals the trellis in
 FP64.  This test runs the same recipe with the arithmetic of the GPU kernel:
-  * mu_j (FP32, max 1) and the Gaussian window (FP32, as 2^((d k2)(r + d))) rounded to one FP16
+  * mu_j (FP32, max 1) and the Gaussian window (FP32, as 2^(d (k2 d + k2 r))) rounded to one FP16
     term each;
   * the forward and inverse DFT matrices as the library's own FP16 hi + lo tables
     (`jbp_dft_tables`);
@@ -87,7 +87,9 @@ def dft_node_fp16(tabs, K, q, sigma2, y, mu, round16=_f16):
     u = u_lo[:, None] + np.arange(W)[None, :]
     d = (ss[:, None] - u).astype(np.float32)
     k2 = np.float32(np.float32(-2.0 * math.log2(math.e)) * inv_s2)
-    e = np.exp2(((d * k2).astype(np.float32) * (r[:, None] + d)).astype(np.float32))
+    k2r = (k2 * r).astype(np.float32)
+    t = (np.float64(k2) * d.astype(np.float64) + k2r[:, None].astype(np.float64)).astype(np.float32)
+    e = np.exp2((d * t).astype(np.float32))
     g16 = round16(np.where(u < U, e, 0.0))
     mu16 = round16(mu)
     # forward products, FP32 sums of exact FP16 products
