@@ -150,7 +150,9 @@ typedef struct {
  * iteration run; logpost [F*K*n*q] optional (may be NULL) max-normalised
  * log-posterior of the last iteration run.
  * on_device = 0: host pointers; the call copies in and out and returns when
- * the outputs are written.  on_device = 1: device pointers; the work is
+ * the outputs are written (a batch of 8,192 frames or more goes in eight parts
+ * whose copies overlap the other parts' decodes; the outputs are those of one
+ * launch).  on_device = 1: device pointers; the work is
  * enqueued on `stream` (a cudaStream_t, NULL = the handle's own stream) and the
  * call returns without waiting; outputs are valid once that stream reaches
  * this point.  form: jbp_form.  sigma2 [F]: optional (NULL = the handle's

@@ -186,6 +186,7 @@ struct jbp_ctx {
     int device = 0;
     DeviceInfo di{};
     cudaStream_t stream = nullptr;
+    cudaStream_t io_in = nullptr, io_out = nullptr;   // host-buffer decodes: copies beside the compute stream
     int64_t budget = 0;
     std::atomic<int64_t> used{0};
 
@@ -467,7 +468,11 @@ extern "C" int jbp_context_create(const jbp_options* opt, jbp_ctx** out)
     cudaError_t e;
     if ((e = cudaDeviceGetAttribute(&ctx->di.sm_count, cudaDevAttrMultiProcessorCount, ctx->device)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&ctx->di.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device)) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        (e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&ctx->io_in, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&ctx->io_out, cudaStreamNonBlocking)) != cudaSuccess) {
+        for (cudaStream_t st : {ctx->stream, ctx->io_in, ctx->io_out})
+            if (st) cudaStreamDestroy(st);
         delete ctx;
         return cuda_fail(e, "context setup");
     }
@@ -502,6 +507,8 @@ extern "C" int jbp_context_destroy(jbp_ctx* ctx)
     if (ctx->many_in) cudaEventDestroy(ctx->many_in);
     if (ctx->many_out) cudaEventDestroy(ctx->many_out);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->io_in) cudaStreamDestroy(ctx->io_in);
+    if (ctx->io_out) cudaStreamDestroy(ctx->io_out);
     delete ctx;
     return JBP_OK;
 }
@@ -1030,6 +1037,11 @@ extern "C" int jbp_stats(jbp_h* h, uint64_t* log_fallbacks, int32_t* tc_timeouts
 // decode
 // ---------------------------------------------------------------------------
 
+// host-buffer decodes of at least kPipeMinFrames frames run as kPipeChunks parts
+// whose copies overlap the other parts' decodes
+static constexpr int kPipeChunks = 8;
+static constexpr int kPipeMinFrames = 8192;
+
 extern "C" int jbp_decode(jbp_h* h, jbp_batch* b)
 {
     if (!h || !b) return fail(JBP_EINVAL, "jbp_decode: NULL argument");
@@ -1050,23 +1062,82 @@ extern "C" int jbp_decode(jbp_h* h, jbp_batch* b)
     Workspace& w = h->ws;
     int rc = ws_io(ctx, h, w, F, b->logpost != nullptr);
     if (rc) return rc;
-    const size_t vs = (size_t)h->K * h->n * h->Q;
+    const size_t vs = (size_t)h->K * h->n * h->Q, KN = (size_t)h->K * h->n;
     float* dy = P<float>(w.y);
     float* dsig = P<float>(w.sig);
     float* dpost = P<float>(w.post);
     uint8_t* dhat = P<uint8_t>(w.hat);
     int32_t* dit = P<int32_t>(w.iters);
     uint8_t* dok = P<uint8_t>(w.ok);
-    JBP_CU(cudaMemcpyAsync(dy, b->y, sizeof(float) * (size_t)F * h->n, cudaMemcpyHostToDevice, s), "copy y");
-    if (b->sigma2) JBP_CU(cudaMemcpyAsync(dsig, b->sigma2, sizeof(float) * F, cudaMemcpyHostToDevice, s), "copy sigma2");
-    rc = decode_device(h, w, b->form, F, dy, dhat, dit, dok, b->logpost ? dpost : nullptr, b->sigma2 ? dsig : nullptr, s);
+    // A large batch goes in kPipeChunks parts: part c's inputs travel on io_in, its
+    // decode runs on the compute stream once they are in (parts in order, so the
+    // step form's workspace is reused safely), and its results travel back on
+    // io_out once it is decoded, so copies overlap the other parts' decodes.
+    // Every frame is decoded as it would be in one launch.
+    const int parts = F >= kPipeMinFrames ? kPipeChunks : 1;
+    cudaEvent_t ev_in[kPipeChunks] = {}, ev_done[kPipeChunks] = {};
+    cudaStream_t sin = parts > 1 ? ctx->io_in : s, sout = parts > 1 ? ctx->io_out : s;
+    auto cleanup = [&]() {
+        for (int c = 0; c < kPipeChunks; ++c) {
+            if (ev_in[c]) cudaEventDestroy(ev_in[c]);
+            if (ev_done[c]) cudaEventDestroy(ev_done[c]);
+        }
+    };
+    for (int c = 0; c < parts; ++c)
+        if (parts > 1 && (cudaEventCreateWithFlags(&ev_in[c], cudaEventDisableTiming) != cudaSuccess ||
+                          cudaEventCreateWithFlags(&ev_done[c], cudaEventDisableTiming) != cudaSuccess)) {
+            cleanup();
+            cudaGetLastError();
+            return fail(JBP_ECUDA, "jbp_decode: event creation failed");
+        }
+    auto part = [&](int c, int& f0, int& nf) {   // the first parts are the larger ones (workspaces only grow)
+        const int base = F / parts, rem = F % parts;
+        f0 = c * base + std::min(c, rem);
+        nf = base + (c < rem ? 1 : 0);
+    };
+    auto fetch = [&](int c) {   // results of part c back to the caller's buffers
+        int f0, nf;
+        part(c, f0, nf);
+        cudaError_t e;
+        if ((parts > 1 && (e = cudaStreamWaitEvent(sout, ev_done[c], 0)) != cudaSuccess) ||
+            (e = cudaMemcpyAsync(b->hat + KN * f0, dhat + KN * f0, KN * nf, cudaMemcpyDeviceToHost, sout)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(b->iters + f0, dit + f0, sizeof(int32_t) * nf, cudaMemcpyDeviceToHost, sout)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(b->ok + (size_t)h->K * f0, dok + (size_t)h->K * f0, (size_t)h->K * nf,
+                                 cudaMemcpyDeviceToHost, sout)) != cudaSuccess ||
+            (b->logpost && (e = cudaMemcpyAsync(b->logpost + vs * f0, dpost + vs * f0, sizeof(float) * vs * nf,
+                                                cudaMemcpyDeviceToHost, sout)) != cudaSuccess))
+            return cuda_fail(e, "jbp_decode: copy results");
+        return (int)JBP_OK;
+    };
+    for (int c = 0; c < parts && rc == JBP_OK; ++c) {
+        int f0, nf;
+        part(c, f0, nf);
+        cudaError_t e = cudaMemcpyAsync(dy + (size_t)h->n * f0, b->y + (size_t)h->n * f0, sizeof(float) * h->n * nf,
+                                        cudaMemcpyHostToDevice, sin);
+        if (e == cudaSuccess && b->sigma2)
+            e = cudaMemcpyAsync(dsig + f0, b->sigma2 + f0, sizeof(float) * nf, cudaMemcpyHostToDevice, sin);
+        if (e == cudaSuccess && parts > 1 && (e = cudaEventRecord(ev_in[c], sin)) == cudaSuccess)
+            e = cudaStreamWaitEvent(s, ev_in[c], 0);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "jbp_decode: copy inputs");
+            break;
+        }
+        rc = decode_device(h, w, b->form, nf, dy + (size_t)h->n * f0, dhat + KN * f0, dit + f0, dok + (size_t)h->K * f0,
+                           b->logpost ? dpost + vs * f0 : nullptr, b->sigma2 ? dsig + f0 : nullptr, s);
+        if (rc) break;
+        if (parts > 1 && (e = cudaEventRecord(ev_done[c], s)) != cudaSuccess) {
+            rc = cuda_fail(e, "jbp_decode: event");
+            break;
+        }
+        // the previous part's results (a copy to pageable memory returns when it is done,
+        // by which time this part's decode is queued behind it)
+        if (parts > 1 && c > 0) rc = fetch(c - 1);
+    }
+    if (rc == JBP_OK) rc = fetch(parts - 1);
+    const cudaError_t e1 = cudaStreamSynchronize(s), e2 = cudaStreamSynchronize(sin), e3 = cudaStreamSynchronize(sout);
+    cleanup();
     if (rc) return rc;
-    JBP_CU(cudaMemcpyAsync(b->hat, dhat, (size_t)F * h->K * h->n, cudaMemcpyDeviceToHost, s), "copy hat");
-    JBP_CU(cudaMemcpyAsync(b->iters, dit, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s), "copy iters");
-    JBP_CU(cudaMemcpyAsync(b->ok, dok, (size_t)F * h->K, cudaMemcpyDeviceToHost, s), "copy ok");
-    if (b->logpost)
-        JBP_CU(cudaMemcpyAsync(b->logpost, dpost, sizeof(float) * vs * F, cudaMemcpyDeviceToHost, s), "copy post");
-    JBP_CU(cudaStreamSynchronize(s), "jbp_decode");
+    JBP_CU(e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3, "jbp_decode");
     {
         // bounded device waits (tensor-core completions, staged check tiles) record expiry here
         int err = 0;

@@ -688,3 +688,46 @@ def test_serving_step_form_pools_match_frames_decoded_alone(env):
     finally:
         dec.close()
         ctx.close()
+
+
+@pytest.mark.parametrize("form,want_post,per_frame_sigma", [("FORM_FUSED", False, False), ("FORM_STEP", True, True),
+                                                            ("FORM_AUTO", False, True)])
+def test_host_decode_in_parts_equals_device_decode(env, form, want_post, per_frame_sigma):
+    """A host-buffer decode of a large batch runs in parts whose copies overlap the
+    other parts' decodes (9,001 frames: eight parts of unequal size).  Every output
+    must equal the one-launch decode of the same frames on device buffers, bit for
+    bit, and the decisions the oracle's on a sample above the margin."""
+    jbp, O, torch = env
+    K, q, n, F, T = 2, 4, 64, 9001, 12
+    code = I.make_code(n, q)
+    fr = I.make_frames(code, K, 10.0, F, seed=88_000 + len(form))
+    sig = (fr["sigma2"] * (1.0 + 0.25 * np.random.default_rng(5).random(F))).astype(np.float32) \
+        if per_frame_sigma else None
+    ctx, dec = _decoder(jbp, code, K, fr["sigma2"], fr["perm"], iters=T, early_stop=True)
+    f = getattr(jbp, form)
+    try:
+        host = dec.decode(fr["y"], form=f, want_post=want_post, sigma2=sig)
+        dev = torch.device("cuda", 0)
+        y_d = torch.from_numpy(fr["y"]).to(dev)
+        hat = torch.full((F, K, n), 255, dtype=torch.uint8, device=dev)
+        it = torch.zeros((F,), dtype=torch.int32, device=dev)
+        ok = torch.full((F, K), 7, dtype=torch.uint8, device=dev)
+        post = torch.empty((F, K, n, q), dtype=torch.float32, device=dev) if want_post else None
+        sig_d = torch.from_numpy(sig).to(dev) if sig is not None else None
+        torch.cuda.synchronize()
+        dec.decode_device(y_d, hat, it, ok, post=post, form=f, sigma2=sig_d)
+        torch.cuda.synchronize()
+        ref = {"hat": hat.cpu().numpy(), "iters": it.cpu().numpy(), "ok": ok.cpu().numpy()}
+        if want_post:
+            ref["post"] = post.cpu().numpy()
+    finally:
+        dec.close()
+        ctx.close()
+    for key in ref:
+        assert np.array_equal(host[key], ref[key]), key
+    for f in [0, 1125, 1126, 4500, F - 1]:   # both sides of the first part boundary, the ends
+        s2 = fr["sigma2"] if sig is None else float(sig[f])
+        o = O.decode(code, K, s2, fr["perm"], fr["y"][f:f + 1], T, early_stop=True, want_margin=True)
+        bad, _ = _margin_mismatch({"hat": host["hat"][f:f + 1]}, o)
+        assert bad == 0, f
+        assert host["iters"][f] == o["iters"][0], f
