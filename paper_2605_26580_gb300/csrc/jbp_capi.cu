@@ -564,9 +564,10 @@ static std::vector<uint32_t> check_order(int K, int P, int E, const std::vector<
         const long iters = 2500l * N;
         for (long it = 0; it < iters; ++it) {
             int i1 = (int)(rnd() % (uint64_t)N);
-            const int i2 = (int)(rnd() % (uint64_t)N);
+            int i2 = (int)(rnd() % (uint64_t)N);
             if (it & 1) {
-                // every other move takes its first unit from an overfull bank of a random run
+                // every other move takes its first unit from an overfull bank of a random run,
+                // and its second from a run where that bank is short
                 const int r = (int)(rnd() % (uint64_t)R), m = std::min(32, N - 32 * r);
                 const int fair = (kDC * m + 31) / 32;
                 int b0 = -1;
@@ -581,6 +582,13 @@ static std::vector<uint32_t> check_order(int K, int P, int E, const std::vector<
                         break;
                     }
                 }
+                if (b0 >= 0)
+                    for (int t = 0, s2 = (int)(rnd() % (uint64_t)R); t < R; ++t) {
+                        const int r2 = (t + s2) % R, m2 = std::min(32, N - 32 * r2);
+                        if (r2 == r || cnt[r2][b0] * 32 >= kDC * m2) continue;
+                        i2 = 32 * r2 + (int)(rnd() % (uint64_t)m2);
+                        break;
+                    }
             }
             const int r1 = i1 / 32, r2 = i2 / 32;
             if (r1 == r2) continue;
