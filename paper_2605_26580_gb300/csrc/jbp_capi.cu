@@ -240,7 +240,7 @@ struct jbp_h {
     int32_t* d_pos_of = nullptr;
     int* d_tc_error = nullptr;
     uint16_t* d_slot = nullptr;
-    uint32_t* d_chk_order = nullptr;   // [K*P] unit | slot permutation << 16 (check_order)
+    uint16_t* d_chk_order = nullptr;
     unsigned char* d_dft_tab = nullptr;   // tables of the tensor-core channel node (null: trellis)
     size_t dft_bytes = 0;
     int64_t table_bytes = 0;
@@ -517,31 +517,21 @@ extern "C" int jbp_context_destroy(jbp_ctx* ctx)
 // handles
 // ---------------------------------------------------------------------------
 
-// Order of the K*P check units (k, j) in the fused kernel's check phase, and of
-// the four edges within each unit.  A warp runs 32 consecutive units, and a
-// unit's edge message lives in shared-memory bank (position mod 32, rotated by
-// 16 for users 2 and 3) at every symbol, so the warp's loads of edge slot d cost
-// as many wavefronts as the largest number of its lanes whose slot-d edge shares
-// a bank.  The check node treats its edges alike, so each unit may put its edges
-// in any slots:
-//   1. annealed pairwise swaps of units between runs of 32, on the sum over runs
-//      and banks of the squared number of the run's edges on the bank (all slots
-//      together; balanced runs carry four edges per bank);
-//   2. in each run, the units' edges are given slots by colouring the edges of the
-//      bipartite multigraph units x banks with four colours (alternating-path
-//      recolouring; any bipartite graph of largest degree 4 has such a colouring):
-//      no two lanes of a slot then share a bank, except for the edges past the
-//      fourth on one bank, which take their unit's free slots.
-// Entry i: bits 0..15 the unit, bits 16..23 its slot permutation (2 bits per slot:
-// the unit's edge in slot c).  Deterministic (fixed-seed xorshift).  The slot
-// order changes the association of the check node's leave-one-out products,
-// and so the rounding of its outputs, and nothing else.
-static std::vector<uint32_t> check_order(int K, int P, int E, const std::vector<uint16_t>& slot)
+// Order of the K*P check units (k, j) in the fused kernel's check phase.  A
+// warp runs 32 consecutive units, and the d-th edge message of unit (k, j) lives
+// in shared-memory bank (position mod 32) of that edge, so the d-th loads of a
+// warp cost as many wavefronts as the largest number of its units sharing that
+// bank.  Greedy fill of each run of 32 with units whose banks are still free,
+// then annealed pairwise swaps between runs.  Deterministic (fixed-seed
+// xorshift); the order does not change any result.
+static std::vector<uint16_t> check_order(int K, int P, int E, const std::vector<uint16_t>& slot)
 {
     const int N = K * P, R = (N + 31) / 32;
     std::vector<std::array<uint8_t, kDC>> col(N);
     for (int u = 0; u < N; ++u) {
         const int k = u / P, j = u % P;
+        // bank of the edge's message: its position within the row, rotated by
+        // 16 for users 2 and 3 (pos_rot of the fused layout)
         for (int d = 0; d < kDC; ++d)
             col[u][d] = (uint8_t)(((slot[(size_t)k * E + kDC * j + d] >> 1) + ((k & 2) << 3)) & 31);
     }
@@ -552,64 +542,47 @@ static std::vector<uint32_t> check_order(int K, int P, int E, const std::vector<
         x ^= x << 17;
         return x;
     };
-    std::vector<int> order(N);
-    for (int u = 0; u < N; ++u) order[u] = u;
-    for (int i = N - 1; i > 0; --i) std::swap(order[i], order[rnd() % (uint64_t)(i + 1)]);
-    std::vector<std::array<int, 32>> cnt(R);
-    for (auto& c : cnt) c.fill(0);
-    for (int i = 0; i < N; ++i)
-        for (int d = 0; d < kDC; ++d) cnt[i / 32][col[order[i]][d]]++;
-    // 1. runs with balanced banks
-    if (R > 1) {
-        const long iters = 2500l * N;
-        for (long it = 0; it < iters; ++it) {
-            int i1 = (int)(rnd() % (uint64_t)N);
-            int i2 = (int)(rnd() % (uint64_t)N);
-            if (it & 1) {
-                // every other move takes its first unit from an overfull bank of a random run,
-                // and its second from a run where that bank is short
-                const int r = (int)(rnd() % (uint64_t)R), m = std::min(32, N - 32 * r);
-                const int fair = (kDC * m + 31) / 32;
-                int b0 = -1;
-                for (int b = 0, s0 = (int)(rnd() & 31); b < 32 && b0 < 0; ++b)
-                    if (cnt[r][(b + s0) & 31] > fair) b0 = (b + s0) & 31;
-                for (int t = 0, s1 = (int)(rnd() % (uint64_t)m); b0 >= 0 && t < m; ++t) {
-                    const int ii = 32 * r + (t + s1) % m;
-                    bool has = false;
-                    for (int d = 0; d < kDC; ++d) has = has || col[order[ii]][d] == b0;
-                    if (has) {
-                        i1 = ii;
-                        break;
-                    }
+    std::vector<int> rem(N);
+    for (int u = 0; u < N; ++u) rem[u] = u;
+    for (int i = N - 1; i > 0; --i) std::swap(rem[i], rem[rnd() % (uint64_t)(i + 1)]);
+    std::vector<int> order;
+    order.reserve(N);
+    std::vector<std::array<std::array<int, 32>, kDC>> cnt(R);
+    for (int r = 0; r < R; ++r) {
+        for (auto& a : cnt[r]) a.fill(0);
+        const int want = std::min(32, N - r * 32);
+        int got = 0;
+        for (int pass = 0; pass < 2 && got < want; ++pass)
+            for (size_t i = 0; i < rem.size() && got < want;) {
+                const int u = rem[i];
+                bool free_all = true;
+                for (int d = 0; d < kDC; ++d) free_all = free_all && cnt[r][d][col[u][d]] == 0;
+                if (pass == 1 || free_all) {
+                    for (int d = 0; d < kDC; ++d) cnt[r][d][col[u][d]]++;
+                    order.push_back(u);
+                    rem.erase(rem.begin() + i);
+                    ++got;
+                } else {
+                    ++i;
                 }
-                if (b0 >= 0)
-                    for (int t = 0, s2 = (int)(rnd() % (uint64_t)R); t < R; ++t) {
-                        const int r2 = (t + s2) % R, m2 = std::min(32, N - 32 * r2);
-                        if (r2 == r || cnt[r2][b0] * 32 >= kDC * m2) continue;
-                        i2 = 32 * r2 + (int)(rnd() % (uint64_t)m2);
-                        break;
-                    }
             }
+    }
+    // Annealed pairwise swaps between runs on the sum of squared bank counts
+    // (every collision costs, so the search has a gradient that the largest count
+    // alone lacks); the cost of a swap changes only in the two runs' counts.
+    if (R > 1) {
+        const long iters = 800l * N;
+        for (long it = 0; it < iters; ++it) {
+            const int i1 = (int)(rnd() % (uint64_t)N), i2 = (int)(rnd() % (uint64_t)N);
             const int r1 = i1 / 32, r2 = i2 / 32;
             if (r1 == r2) continue;
             const int u1 = order[i1], u2 = order[i2];
-            // cost change sum_b (c + v)^2 - c^2 = 2 c v + v^2 over the banks the swap touches,
-            // v = the entering unit's edges on b minus the leaving unit's
             int delta = 0;
-            for (int side = 0; side < 2; ++side) {
-                const int r = side ? r2 : r1, uin = side ? u1 : u2, uout = side ? u2 : u1;
-                int bk[2 * kDC], nb = 0;
-                for (int d = 0; d < 2 * kDC; ++d) {
-                    const int b = d < kDC ? col[uin][d] : col[uout][d - kDC];
-                    bool seen = false;
-                    for (int t = 0; t < nb; ++t) seen = seen || bk[t] == b;
-                    if (!seen) bk[nb++] = b;
-                }
-                for (int t = 0; t < nb; ++t) {
-                    int v = 0;
-                    for (int d = 0; d < kDC; ++d) v += (col[uin][d] == bk[t]) - (col[uout][d] == bk[t]);
-                    delta += 2 * cnt[r][bk[t]] * v + v * v;
-                }
+            for (int d = 0; d < kDC; ++d) {
+                const int a = col[u1][d], b = col[u2][d];
+                if (a == b) continue;
+                // u1 (bank a) leaves r1 for r2, u2 (bank b) leaves r2 for r1
+                delta += 2 * (cnt[r1][d][b] - cnt[r1][d][a] + 1) + 2 * (cnt[r2][d][a] - cnt[r2][d][b] + 1);
             }
             // temperature falls linearly from 2 to 0; uniform in [0, 1) from 53 random bits
             const double temp = 2.0 * (1.0 - (double)it / (double)iters);
@@ -617,103 +590,14 @@ static std::vector<uint32_t> check_order(int K, int P, int E, const std::vector<
             if (delta <= 0 || (temp > 0.0 && u01 < std::exp(-delta / temp))) {
                 std::swap(order[i1], order[i2]);
                 for (int d = 0; d < kDC; ++d) {
-                    cnt[r1][col[u1][d]]--; cnt[r1][col[u2][d]]++;
-                    cnt[r2][col[u2][d]]--; cnt[r2][col[u1][d]]++;
+                    cnt[r1][d][col[u1][d]]--; cnt[r1][d][col[u2][d]]++;
+                    cnt[r2][d][col[u2][d]]--; cnt[r2][d][col[u1][d]]++;
                 }
             }
         }
     }
-    // 2. slots by edge colouring, run by run
-    std::vector<uint32_t> out(N);
-    for (int r = 0; r < R; ++r) {
-        const int base = 32 * r, m = std::min(32, N - base);
-        int color[32][kDC], at_unit[32][kDC], at_bank[32][kDC], deg[32];
-        for (int i = 0; i < 32; ++i)
-            for (int c = 0; c < kDC; ++c) color[i][c] = at_unit[i][c] = at_bank[i][c] = -1;
-        std::fill(deg, deg + 32, 0);
-        // Swap colours c1 <-> c2 on the maximal path that leaves vertex `from` (a bank
-        // if on_bank, else a unit) by its c1 edge and alternates c1, c2.  With
-        // keep_units, a path that would end at a unit is left as it is (false).
-        auto flip = [&](int from, bool on_bank, int c1, int c2, bool keep_units) {
-            int path[2 * 32 * kDC], len = 0, at = from, want = c1;
-            while (len < 2 * 32 * kDC) {
-                const int e = on_bank ? at_bank[at][want] : at_unit[at][want];
-                if (e < 0) break;
-                const int eu = on_bank ? e / kDC : at, ed = on_bank ? e % kDC : e;
-                path[len++] = eu * kDC + ed;
-                at = on_bank ? eu : col[order[base + eu]][ed];
-                on_bank = !on_bank;
-                want = want == c1 ? c2 : c1;
-            }
-            if (keep_units && !on_bank) return false;
-            for (int t = 0; t < len; ++t) {   // clear, then set with swapped colours
-                const int eu = path[t] / kDC, ed = path[t] % kDC, eb = col[order[base + eu]][ed];
-                at_unit[eu][color[eu][ed]] = -1;
-                at_bank[eb][color[eu][ed]] = -1;
-            }
-            for (int t = 0; t < len; ++t) {
-                const int eu = path[t] / kDC, ed = path[t] % kDC, eb = col[order[base + eu]][ed];
-                color[eu][ed] = color[eu][ed] == c1 ? c2 : c1;
-                at_unit[eu][color[eu][ed]] = ed;
-                at_bank[eb][color[eu][ed]] = eu * kDC + ed;
-            }
-            return true;
-        };
-        for (int lu = 0; lu < m; ++lu)
-            for (int d = 0; d < kDC; ++d) {
-                const int b = col[order[base + lu]][d];
-                if (deg[b] == kDC) continue;   // past the fourth edge on this bank: later
-                deg[b]++;
-                int cu = 0, cb = 0;
-                while (at_unit[lu][cu] >= 0) ++cu;   // free at the unit: it has kDC slots
-                while (at_bank[b][cb] >= 0) ++cb;    // free at the bank: fewer than kDC coloured
-                int c = cu;
-                if (at_bank[b][cu] >= 0) {
-                    if (at_unit[lu][cb] < 0) {
-                        c = cb;
-                    } else {
-                        // flip cu <-> cb along the path from b: bank -(cu)- unit -(cb)- bank ...
-                        // (it cannot reach unit lu, where cu is free)
-                        flip(b, true, cu, cb, false);
-                    }
-                }
-                color[lu][d] = c;
-                at_unit[lu][c] = d;
-                at_bank[b][c] = lu * kDC + d;
-            }
-        // the edges past the fourth on a bank collide in whatever slot they take: gather
-        // them in one slot (the units' most common free colour), so that one load of the
-        // run pays for them.  A unit's free colour c becomes tgt by swapping tgt <-> c on
-        // the path that leaves it by its tgt edge; such a path ends at a bank, or at a
-        // unit whose free colour is tgt (a gathered one), which the swap would undo, so
-        // those paths are left alone.
-        int nfree[kDC] = {0, 0, 0, 0};
-        for (int lu = 0; lu < m; ++lu)
-            for (int d = 0; d < kDC; ++d)
-                if (color[lu][d] < 0)
-                    for (int c = 0; c < kDC; ++c) nfree[c] += at_unit[lu][c] < 0;
-        const int tgt = (int)(std::max_element(nfree, nfree + kDC) - nfree);
-        for (int lu = 0; lu < m; ++lu) {
-            bool over = false;
-            for (int d = 0; d < kDC; ++d) over = over || color[lu][d] < 0;
-            if (!over || at_unit[lu][tgt] < 0) continue;
-            int c = 0;
-            while (at_unit[lu][c] >= 0) ++c;
-            flip(lu, false, tgt, c, true);
-        }
-        for (int lu = 0; lu < m; ++lu) {
-            for (int d = 0; d < kDC; ++d)
-                if (color[lu][d] < 0) {   // an edge past the fourth on its bank: a free slot of the unit
-                    int c = 0;
-                    while (at_unit[lu][c] >= 0) ++c;
-                    color[lu][d] = c;
-                    at_unit[lu][c] = d;
-                }
-            uint32_t perm = 0;
-            for (int c = 0; c < kDC; ++c) perm |= (uint32_t)at_unit[lu][c] << (2 * c);
-            out[base + lu] = (uint32_t)order[base + lu] | (perm << 16);
-        }
-    }
+    std::vector<uint16_t> out(N);
+    for (int i = 0; i < N; ++i) out[i] = (uint16_t)order[i];
     return out;
 }
 
@@ -779,7 +663,7 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
     // frame's state in shared memory)
     const bool want_order = want_slot && dc == kDC && K <= 4 && q <= 16 &&
                             4ll * K * (E + n) * q <= (int64_t)ctx->di.smem_optin;
-    std::vector<uint32_t> chk_order;
+    std::vector<uint16_t> chk_order;
     if (want_order) chk_order = check_order(K, P, E, slot);
     const DftShape dsh = dft_shape(K, q);
     // AUTO: the transform except where the register-resident trellis (thread shape) applies
@@ -836,7 +720,7 @@ extern "C" int jbp_create(jbp_ctx* ctx, const jbp_code* code, int32_t K, int32_t
         (e = cudaMemcpy(h->d_pos_of, pos_of.data(), sizeof(int32_t) * pos_of.size(), cudaMemcpyHostToDevice)) ||
         (want_slot &&
          (e = cudaMemcpy(h->d_slot, slot.data(), sizeof(uint16_t) * slot.size(), cudaMemcpyHostToDevice))) ||
-        (want_order && (e = cudaMemcpy(h->d_chk_order, chk_order.data(), sizeof(uint32_t) * chk_order.size(),
+        (want_order && (e = cudaMemcpy(h->d_chk_order, chk_order.data(), sizeof(uint16_t) * chk_order.size(),
                                        cudaMemcpyHostToDevice))) ||
         (want_dft && (e = cudaMemcpy(h->d_dft_tab, dft_tab.data(), dft_tab.size(), cudaMemcpyHostToDevice)))) {
         jbp_destroy(h);
@@ -978,7 +862,7 @@ extern "C" int jbp_destroy(jbp_h* h)
     dev_free(ctx, h->d_dft_tab, h->dft_bytes);
     dev_free(ctx, h->d_tc_error, sizeof(int));
     if (h->d_slot) dev_free(ctx, h->d_slot, sizeof(uint16_t) * (size_t)h->K * h->E);
-    if (h->d_chk_order) dev_free(ctx, h->d_chk_order, sizeof(uint32_t) * (size_t)h->K * h->P);
+    if (h->d_chk_order) dev_free(ctx, h->d_chk_order, sizeof(uint16_t) * (size_t)h->K * h->P);
     delete h;
     return JBP_OK;
 }

@@ -49,7 +49,7 @@ struct Graph {
     const uint16_t* slot;     // [K*E]   pi_k(var of e)*2 + (e's rank in its var) (fused layout)
     int* tc_error;            // set to 1 if a tensor-core wait expired (may be null: FP32 only)
     const float* sigma2_f;    // [F]     per-frame noise variance of this batch (may be null)
-    const uint32_t* chk_order;  // [K*P] fused check phase: unit (bits 0..15) and its edge slots (16..23); may be null
+    const uint16_t* chk_order;  // [K*P] order of the check units in the fused check phase (may be null)
     const unsigned char* dft_tab = nullptr;   // DFT tables of the tensor-core channel node (null: trellis)
     int var_reg = 1;          // 1: every variable has exactly dv edges; 0: var_edge rows end early with -1
 };
@@ -1416,14 +1416,12 @@ struct CheckRec {
 };
 
 template <int Q>
-__device__ __forceinline__ CheckRec check_rec(const Graph& g, int NB, int k, int j, unsigned perm = 0xE4u)
+__device__ __forceinline__ CheckRec check_rec(const Graph& g, int NB, int k, int j)
 {
     unsigned o[kDC], b[kDC];
 #pragma unroll
     for (int d = 0; d < kDC; ++d) {
-        // slot d holds the unit's edge (perm >> 2d) & 3
-        const int e = 4 * j + (int)((perm >> (2 * d)) & 3u), sl = g.slot[k * g.E + e], pp = sl >> 1,
-                  h = g.chk_coef[e];
+        const int e = 4 * j + d, sl = g.slot[k * g.E + e], pp = sl >> 1, h = g.chk_coef[e];
         o[d] = (unsigned)(pos_vec<Q>((k * NB + (pp >> 5)) * 2 + (sl & 1), pp, k)) | ((unsigned)h << 24);
         unsigned bb = 0;
         for (int t = 0; (1 << t) < Q; ++t) bb |= (unsigned)g.gf_div[h * Q + (1 << t)] << (4 * t);

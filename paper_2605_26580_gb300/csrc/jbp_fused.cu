@@ -250,9 +250,8 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
     const size_t fs = (size_t)K * NB * 2 * Q * 32, vs = (size_t)K * NB * Q * 32, hs = (size_t)K * NB * 32;
     for (int i = threadIdx.x; i < Q * Q; i += blockDim.x) s_mul[i] = g.gf_mul[i];
     for (int i = threadIdx.x; i < K * P; i += blockDim.x) {
-        const uint32_t w = g.chk_order ? g.chk_order[i] : (uint32_t)i | (0xE4u << 16);
-        const int u = (int)(w & 0xFFFFu);
-        const CheckRec r = check_rec<Q>(g, NB, u / P, u % P, (w >> 16) & 0xFFu);
+        const int u = g.chk_order ? g.chk_order[i] : i;
+        const CheckRec r = check_rec<Q>(g, NB, u / P, u % P);
         s_rec[i] = r.off;
         s_recb[i] = r.basis;
     }
