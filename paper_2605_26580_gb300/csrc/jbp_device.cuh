@@ -1441,15 +1441,18 @@ __device__ __forceinline__ int rec_coef(unsigned o) { return (int)(o >> 24); }
 template <int Q>
 __device__ __forceinline__ int rec_hat(unsigned o, int NB)
 {
-    const unsigned v = o & 0xFFFFFFu, row = v / (Q * kLanes);
-    const int k = (int)(row >> 1) / NB;
-    return (int)(((row >> 1) << 5) | ((v - pos_rot(k)) & (kLanes - 1)));
+    // rk = k NB + position / 32; users k >= 2 (rk >= 2 NB, K <= 4) rotate by pos_rot = 16
+    const unsigned v = o & 0xFFFFFFu, rk = (v / (Q * kLanes)) >> 1;
+    const unsigned rot = rk >= 2u * (unsigned)NB ? (unsigned)pos_rot(2) : 0u;
+    return (int)((rk << 5) | ((v - rot) & (kLanes - 1)));
 }
 
+// user k of the record's unit, from rk = k NB + position / 32 (K <= 4: three comparisons)
 template <int Q>
 __device__ __forceinline__ int rec_user(unsigned o, int NB)
 {
-    return (int)(((o & 0xFFFFFFu) / (Q * kLanes)) >> 1) / NB;
+    const unsigned rk = ((o & 0xFFFFFFu) / (Q * kLanes)) >> 1, nb = (unsigned)NB;
+    return (int)(rk >= nb) + (int)(rk >= 2u * nb) + (int)(rk >= 3u * nb);
 }
 
 // Check node of one unit (check j of user k), thread shape, position-major

@@ -335,11 +335,23 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
             __syncthreads();
             return s_nactive;
         };
+        // A thread's units are u, u + step, ... over gc frames of `per` units each:
+        // (frame, index) pairs formed and advanced by subtraction (a thread's first
+        // unit lies in the first frame or close to it), not by a division per unit.
+        auto advance = [](int step, int per, int& gi, int& i) {
+            i += step;
+            while (i >= per) {
+                i -= per;
+                ++gi;
+            }
+        };
+        const int KP = K * P;
         auto phase_stop = [&](int t) {
-            for (int w = threadIdx.x; w < gc * K * P; w += blockDim.x) {
-                const int gi = w / (K * P);
+            int gi0 = 0, i0 = 0;
+            advance(threadIdx.x, KP, gi0, i0);
+            for (int gi = gi0, i = i0; gi < gc; advance(blockDim.x, KP, gi, i)) {
                 if (!s_active[gi]) continue;
-                unit_syndrome(gi, s_rec[w % (K * P)]);
+                unit_syndrome(gi, s_rec[i]);
             }
             return phase_finish(t);
         };
@@ -350,15 +362,17 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
             if constexpr (PAIR && K == 4) {
                 const int half = threadIdx.x & 1;
                 const unsigned pmask = 3u << (threadIdx.x & 30);
-                for (int unit = threadIdx.x >> 1; unit < gc * n; unit += blockDim.x >> 1) {
-                    const int gi = unit / n, p = unit % n;
+                int gi0 = 0, p0 = 0;
+                advance(threadIdx.x >> 1, n, gi0, p0);
+                for (int gi = gi0, p = p0; gi < gc; advance(blockDim.x >> 1, n, gi, p)) {
                     if (!s_active[gi]) continue;
                     chan_pair_pos<Q>(g, s_msg + gi * fs, s_ch2v + gi * vs, NB, s_y[gi * NB * 32 + p],
                                      frame_inv_s2(g, f0 + gi), p, half, pmask, dec ? s_hat + gi * hs : nullptr);
                 }
             } else {
-                for (int unit = threadIdx.x; unit < gc * n; unit += blockDim.x) {
-                    const int gi = unit / n, p = unit % n;
+                int gi0 = 0, p0 = 0;
+                advance(threadIdx.x, n, gi0, p0);
+                for (int gi = gi0, p = p0; gi < gc; advance(blockDim.x, n, gi, p)) {
                     if (!s_active[gi]) continue;
                     chan_thread_pos<K, Q>(g, s_msg + gi * fs, s_ch2v + gi * vs, NB, s_y[gi * NB * 32 + p],
                                           frame_inv_s2(g, f0 + gi), p, dec ? s_hat + gi * hs : nullptr);
@@ -368,8 +382,9 @@ __global__ void __launch_bounds__(pos_max_threads<Q, KC, PAIR>()) k_fused_pos(Gr
             // (B) check nodes, in the bank-spreading order of chk_order; folded, each
             // unit also tests its check against the decisions of iteration t - 1
             const bool syn = fold && t > 1;
-            for (int unit = threadIdx.x; unit < gc * K * P; unit += blockDim.x) {
-                const int gi = unit / (K * P), i = unit % (K * P);
+            int cg0 = 0, ci0 = 0;
+            advance(threadIdx.x, KP, cg0, ci0);
+            for (int gi = cg0, i = ci0; gi < gc; advance(blockDim.x, KP, gi, i)) {
                 if (!s_active[gi]) continue;
                 const uint4 r = s_rec[i];
                 if (syn) unit_syndrome(gi, r);
