@@ -373,11 +373,11 @@ def main() -> None:
     achieved = flops / (total_ms / 1e3) / 1e12 / world
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 # DRAM bytes per 65,536-frame launch: ncu capture of k_fused_pos<16,4> in its lane-pair
-                # shape (the autotuner's choice) on 1,216 frames (1.351 MB read + 4.6 KB written),
+                # shape (the autotuner's choice) on 1,216 frames (1.349 MB read + 14.1 KB written),
                 # scaled by frames; state stays in shared memory, so this is y in (and decisions out
                 # through L2), not message traffic.  Only valid at the default workload size and for
                 # this kernel version.
-                "traffic": (1.3555e6 * 65536 / 1216) if args.frames == FRAMES else None,
+                "traffic": (1.3635e6 * 65536 / 1216) if args.frames == FRAMES else None,
                 "traffic_note": "per launch, from profiles/k_fused_pos_q16_k4_n256_small_full.md scaled by frames",
                 "kernel": "k_fused_pos<16,4>",
                 "peak_note": ("of measured: FP32 multiply-add peak measured in this run by jbp_fp32_peak "
