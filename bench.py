@@ -817,6 +817,22 @@ def wl_uneven(args):
     return out
 
 
+def steady_rate(done_t, t_first, n_req):
+    """Saturated serving throughput.  done_t: completion times (s) of the requests
+    that finished after the first poll sweep at t_first (the sweep that collects,
+    at one time stamp, what finished while requests were still being submitted).
+    Under overload the queue still holds most requests then: the completion rate
+    from t_first until 90 % of all n_req requests are done is the engine's
+    saturated throughput, without the drain at the end (pools emptying).  None
+    when fewer than half the requests were still queued, or fewer than 100
+    completions fall in that window.  Returns (frames/s, [t_first, t90])."""
+    n90 = int(0.9 * n_req) - (n_req - len(done_t))
+    if len(done_t) < n_req // 2 or n90 < 100:
+        return None
+    t90 = sorted(done_t)[n90 - 1]
+    return n90 / max(1e-9, t90 - t_first), [t_first, t90]
+
+
 def wl_serve(args):
     """Serving: Poisson arrivals of single frames drawn from the uneven-batch size
     distribution, continuous batching over concurrent launches with admission by
@@ -878,14 +894,9 @@ def wl_serve(args):
                "frames_per_s": n_req / wall, "p50_ms": stats["p50_us"] / 1e3,
                "p99_ms": stats["p99_us"] / 1e3, "ser": ser_num / max(1, ser_den),
                "completed": stats["completed"]}
-        # under overload the queue still holds most requests after submission ends:
-        # the completion rate from then until 90 % of all requests are done is the
-        # saturated throughput, without the drain at the end (pools emptying)
-        n90 = int(0.9 * n_req) - (n_req - len(done_t))
-        if len(done_t) >= n_req // 2 and n90 >= 100:
-            t90 = sorted(done_t)[n90 - 1]
-            row["steady_frames_per_s"] = n90 / max(1e-9, t90 - t_first)
-            row["steady_window_s"] = [t_first, t90]
+        st = steady_rate(done_t, t_first, n_req)
+        if st is not None:
+            row["steady_frames_per_s"], row["steady_window_s"] = st
         results.append(row)
         for p in parts:
             p["dec"].close()

@@ -75,6 +75,25 @@ def test_uneven_classes_cover_every_frame():
     assert ((8.0 <= snr) & (snr <= 16.0)).all()
 
 
+def test_serving_steady_rate_counts_the_saturated_window_only():
+    """The serving workload's steady throughput: completions after the first poll
+    sweep, up to 90 % of all requests, over that window; the drain after it and
+    the completions folded into the first sweep do not count."""
+    sys.path.insert(0, ROOT)
+    import bench
+    # 1,000 requests: 200 done by the first sweep at t = 1 s, then 4,000 frames/s
+    # until 900 are done (t = 1.175 s), then a slow drain of the last 100 over 1 s
+    done = [1.0 + (i + 1) / 4000.0 for i in range(700)] + [1.175 + (i + 1) / 100.0 for i in range(100)]
+    rate, win = bench.steady_rate(done, 1.0, 1000)
+    assert abs(rate - 4000.0) < 1e-6 and win == [1.0, 1.175]
+    # the whole run counted as frames over wall time would be far lower
+    assert 1000 / max(done) < 0.25 * rate
+    # most requests already done at the first sweep (no queue): no steady figure
+    assert bench.steady_rate(done[:300], 1.0, 1000) is None
+    # too few completions in the window
+    assert bench.steady_rate([1.0 + i / 10.0 for i in range(60)], 1.0, 100) is None
+
+
 def test_profile_commands_run_committed_files_with_valid_flags():
     """Every command a profile summary quotes runs a committed file (bench.py)
     with flags the benchmark still accepts."""
